@@ -1,0 +1,303 @@
+"""FP64 CPU oracle for Iterative Least Squares (ILS) smoothing.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  The product library never does, and this module imports nothing from
+the product package: the two share no kernels, tables, helpers or constants.
+
+Everything here follows Liu et al., "Real-time Image Smoothing via Iterative
+Least Squares" (arXiv 2003.07504).  Equations are numbered in the order the
+paper's LaTeX source numbers them:
+
+  Eq. 1  objective  E(u,f) = sum_s (u_s-f_s)^2 + lam * sum_{*=x,y} phi_p(grad_* u_s)   (Sec. 3)
+  Eq. 2  generalized Charbonnier penalty  phi_p(x) = (x^2+eps)^(p/2)                  (Sec. 3)
+  Eq. 7  half-quadratic auxiliary update  mu = c*grad u - phi_p'(grad u)              (Sec. 3.1)
+  Eq. 8  the per-iteration least-squares problem (ILS)                                (Sec. 3.2)
+  Eq. 9  its periodic-boundary FFT solution                                           (Sec. 3.2)
+  Eq. 11 c >= c0 = p*eps^(p/2-1), with c = c0 used throughout                         (Sec. 3.3, App. B)
+  Algorithm 1: u^0 = f; for n = 0..N-1: mu^n from u^n (Eq. 7), u^{n+1} from Eq. 9.
+  Sec. 3.4: colour images are smoothed one RGB channel at a time.
+
+Arithmetic is float64 throughout.  The 2-D DFT is the naive separable DFT: an
+explicit n x n DFT matrix applied along rows and then columns (a matrix product
+is the only library primitive used).  No blocking, fusion or reordering beyond
+what the equations state.
+
+Readings of points the paper leaves open (each is also listed with the design
+notes of the repository):
+  * gradients are forward differences with periodic wrap,
+      (grad_x u)[y,x] = u[y,(x+1)%W] - u[y,x],  (grad_y u)[y,x] = u[(y+1)%H,x] - u[y,x];
+    the "inverse direction" derivative of Sec. 3.2 is the transpose,
+      (grad_x^T m)[y,x] = m[y,(x-1)%W] - m[y,x]   (likewise for y);
+  * forward DFT uses exp(-2*pi*i*jk/n), the inverse exp(+...)/n; the real part of
+    the inverse is the result (the exact result is real);
+  * u^0 = f unless a warm start u0 is given; no clipping of u;
+  * c = c0 exactly.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+__all__ = [
+    "c0", "phi_p", "dphi_p", "d2phi_p", "g2", "mu_update",
+    "grad_x", "grad_y", "grad_x_T", "grad_y_T",
+    "dft_matrix", "dft2", "idft2", "gradient_transfer_functions", "denominator",
+    "solve_eq9", "ils_iteration", "ils_smooth", "ils_channel", "energy", "ils_backward",
+    "conv3x3", "warmstart_cnn_forward",
+]
+
+
+# ----------------------------------------------------------------------------
+# Penalty and half-quadratic pieces (Eq. 2, Eq. 7, Eq. 11, Appendix B)
+# ----------------------------------------------------------------------------
+
+def c0(p: float, eps: float) -> float:
+    """Smallest constant keeping g(x) = c/2 x^2 - phi_p(x) convex: c0 = p*eps^(p/2-1).
+
+    Eq. 11 (Sec. 3.3) and Appendix B (h(0) = p*eps^(p/2-1)).
+    """
+    return float(p) * float(eps) ** (float(p) / 2.0 - 1.0)
+
+
+def phi_p(x, p, eps):
+    """Generalized Charbonnier penalty, Eq. 2: (x^2 + eps)^(p/2)."""
+    x = np.asarray(x, dtype=np.float64)
+    return (x * x + eps) ** (p / 2.0)
+
+
+def dphi_p(x, p, eps):
+    """phi_p'(x) = p * x * (x^2 + eps)^(p/2 - 1), the derivative written out in Eq. 7."""
+    x = np.asarray(x, dtype=np.float64)
+    return p * x * (x * x + eps) ** (p / 2.0 - 1.0)
+
+
+def d2phi_p(x, p, eps):
+    """phi_p''(x) = p (x^2+eps)^(p/2-2) [(p-1) x^2 + eps]: the h(x) of Appendix B."""
+    x = np.asarray(x, dtype=np.float64)
+    return p * (x * x + eps) ** (p / 2.0 - 2.0) * ((p - 1.0) * x * x + eps)
+
+
+def g2(x, p, eps, c):
+    """g''(x) = c - p (x^2+eps)^(p/2-2) [(p-1) x^2 + eps]  (Appendix B).
+
+    This is also d mu / d x for the mu of Eq. 7, which the adjoint needs.
+    """
+    return c - d2phi_p(x, p, eps)
+
+
+def mu_update(x, p, eps, c):
+    """Eq. 7: mu = c*x - p*x*(x^2+eps)^(p/2-1), elementwise on a gradient field x."""
+    x = np.asarray(x, dtype=np.float64)
+    return c * x - p * x * (x * x + eps) ** (p / 2.0 - 1.0)
+
+
+# ----------------------------------------------------------------------------
+# Discrete differential operators (Sec. 3: [1,-1] and [1,-1]^T; Sec. 3.2: the
+# inverse-direction derivative).  Periodic boundary, as the FFT solve assumes.
+# ----------------------------------------------------------------------------
+
+def grad_x(u):
+    """(grad_x u)[y,x] = u[y,x+1] - u[y,x], periodic in x."""
+    return np.roll(u, -1, axis=-1) - u
+
+
+def grad_y(u):
+    """(grad_y u)[y,x] = u[y+1,x] - u[y,x], periodic in y."""
+    return np.roll(u, -1, axis=-2) - u
+
+
+def grad_x_T(m):
+    """Transpose of grad_x (the 'inverse direction' derivative of Sec. 3.2)."""
+    return np.roll(m, 1, axis=-1) - m
+
+
+def grad_y_T(m):
+    """Transpose of grad_y."""
+    return np.roll(m, 1, axis=-2) - m
+
+
+# ----------------------------------------------------------------------------
+# Naive separable DFT (the F and F^{-1} of Eq. 9)
+# ----------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=16)
+def dft_matrix(n: int, sign: int = -1) -> np.ndarray:
+    """Explicit n x n DFT matrix  F[j,k] = exp(sign * 2*pi*i * j*k / n).
+
+    The product j*k is reduced mod n before the angle is formed so the twiddle
+    keeps full float64 accuracy for large n.
+    """
+    j = np.arange(n, dtype=np.int64)
+    m = np.outer(j, j) % n
+    F = np.exp(sign * 2j * np.pi * m.astype(np.float64) / n)
+    F.setflags(write=False)
+    return F
+
+
+def dft2(x: np.ndarray) -> np.ndarray:
+    """Forward 2-D DFT of an H x W array: the row DFT, then the column DFT."""
+    H, W = x.shape
+    rows = np.asarray(x, dtype=np.complex128) @ dft_matrix(W, -1)   # DFT along x (F symmetric)
+    return dft_matrix(H, -1) @ rows                                 # DFT along y
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """Inverse 2-D DFT (sign +, scaled by 1/(H*W))."""
+    H, W = X.shape
+    rows = np.asarray(X, dtype=np.complex128) @ dft_matrix(W, +1)
+    return (dft_matrix(H, +1) @ rows) / (H * W)
+
+
+def gradient_transfer_functions(H: int, W: int):
+    """F(grad_x) and F(grad_y): the DFT of the impulse responses of the two
+    difference operators, as Eq. 9 writes them.
+
+    grad_x u = u (*) h_x (circular convolution) with h_x[0,0] = -1, h_x[0,-1] = +1;
+    grad_y likewise along y.
+    """
+    hx = np.zeros((H, W))
+    hx[0, 0] = -1.0
+    hx[0, (W - 1) % W] += 1.0
+    hy = np.zeros((H, W))
+    hy[0, 0] = -1.0
+    hy[(H - 1) % H, 0] += 1.0
+    return dft2(hx), dft2(hy)
+
+
+def denominator(H: int, W: int, lam: float, c: float, Fdx=None, Fdy=None) -> np.ndarray:
+    """Eq. 9 denominator: F(1) + (c/2) lam (conj(F grad_x) F grad_x + conj(F grad_y) F grad_y).
+
+    F(1) is the DFT of the unit impulse, i.e. all ones.
+    """
+    if Fdx is None or Fdy is None:
+        Fdx, Fdy = gradient_transfer_functions(H, W)
+    delta = np.zeros((H, W))
+    delta[0, 0] = 1.0
+    F1 = dft2(delta)
+    return F1 + (c / 2.0) * lam * (np.conj(Fdx) * Fdx + np.conj(Fdy) * Fdy)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1
+# ----------------------------------------------------------------------------
+
+def solve_eq9(Ff, mu_x, mu_y, lam, den, Fdx, Fdy):
+    """Eq. 9: F^{-1}[(F(f) + lam/2 (conj(F grad_x) F(mu_x) + conj(F grad_y) F(mu_y))) / den],
+    the minimizer of the Eq. 8 least-squares problem for fixed mu (real part taken)."""
+    num = Ff + (lam / 2.0) * (np.conj(Fdx) * dft2(mu_x) + np.conj(Fdy) * dft2(mu_y))
+    return np.real(idft2(num / den))
+
+
+def ils_iteration(u, f, lam, p, eps, c, Ff, den, Fdx, Fdy):
+    """One pass of Algorithm 1's loop body on one channel.
+
+    Step 1: mu^n_* from grad_* u^n by Eq. 7.
+    Step 2: u^{n+1} by Eq. 9 (solve_eq9).
+    """
+    mu_x = mu_update(grad_x(u), p, eps, c)
+    mu_y = mu_update(grad_y(u), p, eps, c)
+    return solve_eq9(Ff, mu_x, mu_y, lam, den, Fdx, Fdy)
+
+
+def ils_channel(f, lam, p, eps, N, u0=None, c=None, return_iterates=False):
+    """Algorithm 1 on one H x W channel (float64).  Returns u^N (and u^0..u^N)."""
+    f = np.asarray(f, dtype=np.float64)
+    H, W = f.shape
+    if c is None:
+        c = c0(p, eps)
+    Fdx, Fdy = gradient_transfer_functions(H, W)
+    den = denominator(H, W, lam, c, Fdx, Fdy)   # pre-computed once (Algorithm 1, input line)
+    Ff = dft2(f)                                 # pre-computed once
+    u = f.copy() if u0 is None else np.asarray(u0, dtype=np.float64).copy()
+    iterates = [u.copy()]
+    for _ in range(int(N)):
+        u = ils_iteration(u, f, lam, p, eps, c, Ff, den, Fdx, Fdy)
+        if return_iterates:
+            iterates.append(u.copy())
+    return (u, iterates) if return_iterates else u
+
+
+def ils_smooth(f, lam=1.0, p=0.8, eps=1e-4, N=4, u0=None, c=None):
+    """ILS on a C x H x W (or H x W) image, channels independent (Sec. 3.4)."""
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 2:
+        return ils_channel(f, lam, p, eps, N, u0, c)
+    out = np.empty_like(f)
+    for ch in range(f.shape[0]):
+        out[ch] = ils_channel(f[ch], lam, p, eps, N, None if u0 is None else u0[ch], c)
+    return out
+
+
+def energy(u, f, lam, p, eps):
+    """Eq. 1 with the penalty of Eq. 2, periodic forward differences."""
+    u = np.asarray(u, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    return float(np.sum((u - f) ** 2)
+                 + lam * np.sum(phi_p(grad_x(u), p, eps))
+                 + lam * np.sum(phi_p(grad_y(u), p, eps)))
+
+
+# ----------------------------------------------------------------------------
+# Adjoint of Algorithm 1 with respect to f
+# ----------------------------------------------------------------------------
+
+def ils_backward(f, grad_u, lam, p, eps, N, c=None):
+    """Gradient of <grad_u, u^N(f)> with respect to f, on one H x W channel (float64).
+
+    The paper has no adjoint; this is the chain rule through Algorithm 1.
+    Write A for the Eq. 9 operator (I + (lam c/2)(grad_x^T grad_x + grad_y^T grad_y)),
+    diagonal in Fourier space with the real, even eigenvalues `den`, hence symmetric.
+    u^{n+1} = A^{-1} (f + lam/2 sum_* grad_*^T mu(grad_* u^n)), u^0 = f, so with
+    g = dL/du^{n+1}:
+        r = A^{-1} g;   dL/df += r;   dL/du^n = lam/2 sum_* grad_*^T [ g''(grad_* u^n) * grad_* r ],
+    where g'' = d mu / dx is the Appendix B second derivative.  Finally dL/df += dL/du^0.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    H, W = f.shape
+    if c is None:
+        c = c0(p, eps)
+    _, iterates = ils_channel(f, lam, p, eps, N, c=c, return_iterates=True)
+    den = denominator(H, W, lam, c)
+    g = np.asarray(grad_u, dtype=np.float64).copy()
+    gf = np.zeros_like(f)
+    for n in range(int(N) - 1, -1, -1):
+        r = np.real(idft2(dft2(g) / den))
+        gf += r
+        un = iterates[n]
+        g = (lam / 2.0) * (grad_x_T(g2(grad_x(un), p, eps, c) * grad_x(r))
+                           + grad_y_T(g2(grad_y(un), p, eps, c) * grad_y(r)))
+    return gf + g
+
+
+# ----------------------------------------------------------------------------
+# Warm-start network (not in the paper): 3x3 convolutions, ReLU, residual output.
+# ----------------------------------------------------------------------------
+
+def conv3x3(x, w, b):
+    """Zero-padded 3x3 cross-correlation, NCHW: out[o] = b[o] + sum_{i,dy,dx} w[o,i,dy,dx] x[i, y+dy-1, x+dx-1].
+
+    Plain torch.nn.functional.conv2d in float64 (a library primitive).
+    """
+    import torch
+    xt = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    wt = torch.as_tensor(np.asarray(w, dtype=np.float64))
+    bt = torch.as_tensor(np.asarray(b, dtype=np.float64))
+    squeeze = xt.ndim == 3
+    if squeeze:
+        xt = xt[None]
+    y = torch.nn.functional.conv2d(xt, wt, bt, padding=1)
+    return (y[0] if squeeze else y).numpy()
+
+
+def warmstart_cnn_forward(f, weights, biases):
+    """u0 = f + net(f): conv3x3 layers with ReLU between them, none after the last."""
+    x = np.asarray(f, dtype=np.float64)
+    h = x
+    L = len(weights)
+    for i, (w, b) in enumerate(zip(weights, biases)):
+        h = conv3x3(h, w, b)
+        if i < L - 1:
+            h = np.maximum(h, 0.0)
+    return x + h

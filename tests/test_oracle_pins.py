@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by the mathematics.
+
+Nothing here re-types the oracle's formulas: each check reaches the same
+quantity another way (brute force, dense linear algebra on the Eq. 8 normal
+equations, finite differences of Eq. 1/Eq. 2, invariants, closed forms).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_07504_gb300 import synth
+
+
+# ---------------------------------------------------------------- helpers (dense, from definitions)
+
+def dense_forward_difference(H, W, axis):
+    """Matrix of the periodic forward difference on row-major H*W vectors."""
+    n = H * W
+    D = np.zeros((n, n))
+    for y in range(H):
+        for x in range(W):
+            i = y * W + x
+            j = y * W + (x + 1) % W if axis == "x" else ((y + 1) % H) * W + x
+            D[i, j] += 1.0
+            D[i, i] -= 1.0
+    return D
+
+
+def dense_backward_difference(H, W, axis):
+    n = H * W
+    D = np.zeros((n, n))
+    for y in range(H):
+        for x in range(W):
+            i = y * W + x
+            j = y * W + (x - 1) % W if axis == "x" else ((y - 1) % H) * W + x
+            D[i, i] += 1.0
+            D[i, j] -= 1.0
+    return D
+
+
+def fd_dphi(x, p, eps, h=1e-6):
+    """Central finite difference of Eq. 2's penalty (second-order accurate)."""
+    return (O.phi_p(x + h, p, eps) - O.phi_p(x - h, p, eps)) / (2 * h)
+
+
+def dense_ils(f, lam, p, eps, N, Dx, Dy):
+    """Algorithm 1 with every operator a dense matrix and phi' by finite differences.
+
+    mu = c*g - phi'(g) is the optimum condition of Eq. 3 (Appendix A); u^{n+1}
+    solves the normal equations of Eq. 8: (2I + lam c (Dx^T Dx + Dy^T Dy)) u = 2f + lam (Dx^T mu_x + Dy^T mu_y).
+    """
+    c = p * eps ** (p / 2 - 1)
+    n = f.size
+    fv = f.reshape(-1)
+    A = 2 * np.eye(n) + lam * c * (Dx.T @ Dx + Dy.T @ Dy)
+    u = fv.copy()
+    for _ in range(N):
+        gx, gy = Dx @ u, Dy @ u
+        mx = c * gx - fd_dphi(gx, p, eps)
+        my = c * gy - fd_dphi(gy, p, eps)
+        u = np.linalg.solve(A, 2 * fv + lam * (Dx.T @ mx + Dy.T @ my))
+    return u.reshape(f.shape)
+
+
+def small_image(H, W, seed):
+    return synth.voronoi_texture(H, W, 1, K=4, A=0.05, Tmin=3, Tmax=5, sigma=0.02, seed=seed)[0].astype(np.float64)
+
+
+# ---------------------------------------------------------------- DFT
+
+def test_dft2_matches_bruteforce_quadruple_sum():
+    rng = np.random.default_rng(1)
+    H, W = 6, 10
+    x = rng.normal(size=(H, W))
+    X = np.zeros((H, W), dtype=complex)
+    for l in range(H):
+        for k in range(W):
+            s = 0j
+            for y in range(H):
+                for xx in range(W):
+                    s += x[y, xx] * np.exp(-2j * np.pi * (l * y / H + k * xx / W))
+            X[l, k] = s
+    np.testing.assert_allclose(O.dft2(x), X, atol=1e-11)
+    np.testing.assert_allclose(O.idft2(X).real, x, atol=1e-12)
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (15, 12), (27, 40)])
+def test_dft2_matches_numpy_fft(H, W):
+    rng = np.random.default_rng(H * 100 + W)
+    x = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+    np.testing.assert_allclose(O.dft2(x), np.fft.fft2(x), atol=1e-10)
+    np.testing.assert_allclose(O.idft2(x), np.fft.ifft2(x), atol=1e-12)
+
+
+def test_denominator_closed_form():
+    # |F grad|^2 for the periodic [1,-1] operator is 4 sin^2(pi k / n).
+    H, W, lam, c = 9, 14, 1.3, 7.0
+    den = O.denominator(H, W, lam, c)
+    l = np.arange(H)[:, None]
+    k = np.arange(W)[None, :]
+    want = 1 + (lam * c / 2) * (4 * np.sin(np.pi * k / W) ** 2 + 4 * np.sin(np.pi * l / H) ** 2)
+    np.testing.assert_allclose(den.real, want, rtol=1e-13, atol=1e-12)
+    assert np.abs(den.imag).max() < 1e-12
+
+
+# ---------------------------------------------------------------- pieces
+
+def test_c0_is_the_convexity_threshold():
+    # Appendix B: at c = c0, g'' >= 0 everywhere; any smaller c makes g'' negative at 0.
+    x = np.linspace(-2, 2, 400001)
+    for p in (0.2, 0.5, 0.8, 1.0):
+        eps = 1e-4
+        c = O.c0(p, eps)
+        assert np.min(O.g2(x, p, eps, c)) >= -1e-9 * c
+        assert np.min(O.g2(x, p, eps, 0.9 * c)) < 0
+        # numerical second derivative of g = c/2 x^2 - phi at a few points agrees with g''
+        h = 1e-4
+        xs = np.array([-0.3, -0.02, 0.004, 0.05, 0.7])
+        g = lambda t: c / 2 * t * t - O.phi_p(t, p, eps)
+        num = (g(xs + h) - 2 * g(xs) + g(xs - h)) / h ** 2
+        np.testing.assert_allclose(O.g2(xs, p, eps, c), num, rtol=2e-4, atol=1e-3)
+    assert O.c0(0.8, 1e-4) == pytest.approx(0.8 * 10 ** 2.4, rel=1e-14)
+
+
+def test_mu_is_c_x_minus_numerical_derivative_of_penalty():
+    x = np.concatenate([np.linspace(-1, 1, 201), [1e-5, -3e-3, 0.011]])
+    for p in (0.5, 0.8, 1.0):
+        eps = 1e-4
+        c = O.c0(p, eps)
+        np.testing.assert_allclose(O.mu_update(x, p, eps, c), c * x - fd_dphi(x, p, eps),
+                                   rtol=1e-7, atol=1e-8)
+
+
+def test_mu_is_the_argmin_of_the_half_quadratic_bound():
+    # Eq. 3 / Appendix A: phi(t) <= 1/2 (sqrt(c) t - mu/sqrt(c))^2 + psi(mu) with equality at the
+    # optimum mu = mu(x0) when t = x0.  So for that fixed mu, t -> 1/2 (sqrt(c) t - mu/sqrt(c))^2 - phi(t)
+    # (which equals -psi(mu) at t = x0 and is >= -psi(mu) elsewhere) is minimal at t = x0.
+    p, eps = 0.8, 1e-4
+    c = O.c0(p, eps)
+    for x0 in (-0.4, -0.01, 0.003, 0.2):
+        mu = O.mu_update(x0, p, eps, c)
+        t = x0 + np.linspace(-0.05, 0.05, 20001)
+        val = 0.5 * (np.sqrt(c) * t - mu / np.sqrt(c)) ** 2 - O.phi_p(t, p, eps)
+        assert abs(t[np.argmin(val)] - x0) <= 1e-5
+
+
+# ---------------------------------------------------------------- the Eq. 9 solve
+
+@pytest.mark.parametrize("H,W,lam,p", [(8, 8, 1.0, 0.8), (8, 8, 3.5, 0.5), (6, 10, 0.4, 1.0), (5, 7, 2.0, 0.8)])
+def test_eq9_solves_the_eq8_least_squares_problem(H, W, lam, p):
+    rng = np.random.default_rng(H * W)
+    eps = 1e-4
+    c = O.c0(p, eps)
+    f = rng.uniform(size=(H, W))
+    mx = rng.normal(size=(H, W)) * 5
+    my = rng.normal(size=(H, W)) * 5
+    Fdx, Fdy = O.gradient_transfer_functions(H, W)
+    den = O.denominator(H, W, lam, c, Fdx, Fdy)
+    u = O.solve_eq9(O.dft2(f), mx, my, lam, den, Fdx, Fdy)
+    # Dense minimization of the Eq. 8 objective for these mu.
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    n = H * W
+    A = 2 * np.eye(n) + lam * c * (Dx.T @ Dx + Dy.T @ Dy)
+    b = 2 * f.reshape(-1) + lam * (Dx.T @ mx.reshape(-1) + Dy.T @ my.reshape(-1))
+    u_dense = np.linalg.solve(A, b).reshape(H, W)
+    np.testing.assert_allclose(u, u_dense, atol=1e-12 * max(1, np.abs(u_dense).max()))
+
+    def J(v):
+        v = v.reshape(-1)
+        return (np.sum((v - f.reshape(-1)) ** 2)
+                + lam * 0.5 * np.sum((np.sqrt(c) * (Dx @ v) - mx.reshape(-1) / np.sqrt(c)) ** 2)
+                + lam * 0.5 * np.sum((np.sqrt(c) * (Dy @ v) - my.reshape(-1) / np.sqrt(c)) ** 2))
+    j0 = J(u)
+    for s in range(5):
+        d = rng.normal(size=(H, W)) * 1e-3
+        assert J(u + d) > j0
+
+
+@pytest.mark.parametrize("H,W,lam,p,N", [(8, 8, 1.0, 0.8, 4), (4, 6, 2.0, 0.5, 3), (6, 5, 0.7, 1.0, 2)])
+def test_full_algorithm_matches_dense_bruteforce(H, W, lam, p, N):
+    eps = 1e-4
+    f = small_image(H, W, seed=H + W)
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    want = dense_ils(f, lam, p, eps, N, Dx, Dy)
+    got = O.ils_channel(f, lam, p, eps, N)
+    np.testing.assert_allclose(got, want, atol=1e-7)   # the finite-difference phi' limits this
+
+
+def test_backward_difference_reading_gives_the_same_result():
+    # Sec. 3 only names the [1,-1] filter; periodic forward and backward differences give one result.
+    H, W, lam, p, eps, N = 6, 8, 1.0, 0.8, 1e-4, 3
+    f = small_image(H, W, seed=3)
+    Bx, By = dense_backward_difference(H, W, "x"), dense_backward_difference(H, W, "y")
+    np.testing.assert_allclose(O.ils_channel(f, lam, p, eps, N), dense_ils(f, lam, p, eps, N, Bx, By), atol=1e-7)
+
+
+def test_p2_reduces_to_tikhonov():
+    # p = 2 (outside the paper's range but the formulas hold): c0 = 2, mu == 0, so one
+    # iteration is the closed-form quadratic smoother (I + lam (Dx^T Dx + Dy^T Dy))^{-1} f.
+    H, W, lam = 7, 9, 1.7
+    f = small_image(H, W, seed=5)
+    assert O.c0(2.0, 1e-4) == pytest.approx(2.0)
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    want = np.linalg.solve(np.eye(H * W) + lam * (Dx.T @ Dx + Dy.T @ Dy), f.reshape(-1)).reshape(H, W)
+    np.testing.assert_allclose(O.ils_channel(f, lam, 2.0, 1e-4, 1), want, atol=1e-12)
+    np.testing.assert_allclose(O.ils_channel(f, lam, 2.0, 1e-4, 3), want, atol=1e-12)
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_lambda_zero_returns_f():
+    f = small_image(12, 10, seed=7)
+    np.testing.assert_allclose(O.ils_channel(f, 0.0, 0.8, 1e-4, 4), f, atol=1e-13)
+
+
+def test_constant_image_is_a_fixed_point():
+    f = np.full((9, 12), 0.37)
+    np.testing.assert_allclose(O.ils_channel(f, 2.0, 0.8, 1e-4, 4), f, atol=1e-13)
+
+
+def test_mean_is_preserved():
+    f = small_image(16, 20, seed=11)
+    u = O.ils_channel(f, 1.0, 0.8, 1e-4, 4)
+    assert abs(u.mean() - f.mean()) < 1e-13
+
+
+def test_energy_is_non_increasing():
+    # The half-quadratic majorization (Eq. 3-6, Appendix A) makes Eq. 1 monotone along the iterates.
+    for p, lam in ((0.8, 1.0), (0.5, 3.0), (1.0, 0.5)):
+        f = small_image(24, 20, seed=int(10 * p + lam))
+        _, its = O.ils_channel(f, lam, p, 1e-4, 12, return_iterates=True)
+        E = [O.energy(u, f, lam, p, 1e-4) for u in its]
+        assert all(E[i + 1] <= E[i] * (1 + 1e-12) for i in range(len(E) - 1)), E
+        assert E[-1] < E[0]
+
+
+def test_fixed_point_is_a_stationary_point_of_eq1():
+    # A limit of the iteration makes the gradient of Eq. 1 vanish; checked with a finite-difference
+    # gradient of the energy itself.
+    H, W, lam, p, eps = 6, 6, 0.5, 1.0, 1e-2
+    f = small_image(H, W, seed=13)
+    u = O.ils_channel(f, lam, p, eps, 3000)
+    h = 1e-6
+    grad = np.zeros_like(u)
+    for i in range(H):
+        for j in range(W):
+            e = np.zeros_like(u)
+            e[i, j] = h
+            grad[i, j] = (O.energy(u + e, f, lam, p, eps) - O.energy(u - e, f, lam, p, eps)) / (2 * h)
+    assert np.abs(grad).max() < 1e-6
+
+
+def test_shift_and_transpose_equivariance():
+    f = small_image(12, 16, seed=17)
+    u = O.ils_channel(f, 1.0, 0.8, 1e-4, 4)
+    us = O.ils_channel(np.roll(f, (3, -5), axis=(0, 1)), 1.0, 0.8, 1e-4, 4)
+    np.testing.assert_allclose(us, np.roll(u, (3, -5), axis=(0, 1)), atol=1e-12)
+    ut = O.ils_channel(f.T.copy(), 1.0, 0.8, 1e-4, 4)
+    np.testing.assert_allclose(ut, u.T, atol=1e-12)
+
+
+def test_colour_channels_are_independent():
+    f = synth.voronoi_texture(10, 12, 3, K=3, seed=19).astype(np.float64)
+    u = O.ils_smooth(f, 1.0, 0.8, 1e-4, 2)
+    for ch in range(3):
+        np.testing.assert_array_equal(u[ch], O.ils_channel(f[ch], 1.0, 0.8, 1e-4, 2))
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_adjoint_matches_directional_finite_differences():
+    H, W, lam, p, eps, N = 8, 10, 1.0, 0.8, 1e-4, 4
+    f = small_image(H, W, seed=23)
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=(H, W))
+    g = O.ils_backward(f, w, lam, p, eps, N)
+    for trial in range(3):
+        v = rng.normal(size=(H, W))
+        h = 1e-6
+        Lp = np.sum(w * O.ils_channel(f + h * v, lam, p, eps, N))
+        Lm = np.sum(w * O.ils_channel(f - h * v, lam, p, eps, N))
+        fd = (Lp - Lm) / (2 * h)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_adjoint_per_pixel_finite_differences_on_a_crop():
+    H, W, lam, p, eps, N = 6, 6, 2.0, 0.5, 1e-4, 3
+    f = small_image(H, W, seed=29)
+    w = np.random.default_rng(1).normal(size=(H, W))
+    g = O.ils_backward(f, w, lam, p, eps, N)
+    h = 1e-6
+    for i in range(H):
+        for j in range(W):
+            e = np.zeros((H, W))
+            e[i, j] = h
+            fd = (np.sum(w * O.ils_channel(f + e, lam, p, eps, N)) - np.sum(w * O.ils_channel(f - e, lam, p, eps, N))) / (2 * h)
+            assert g[i, j] == pytest.approx(fd, rel=1e-5, abs=1e-6)
+
+
+# ---------------------------------------------------------------- warm-start network helpers
+
+def test_conv3x3_matches_loops():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(2, 5, 7))
+    w = rng.normal(size=(3, 2, 3, 3))
+    b = rng.normal(size=3)
+    want = np.zeros((3, 5, 7))
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)))
+    for o in range(3):
+        for y in range(5):
+            for xx in range(7):
+                want[o, y, xx] = b[o] + np.sum(w[o] * xp[:, y:y + 3, xx:xx + 3])
+    np.testing.assert_allclose(O.conv3x3(x, w, b), want, atol=1e-12)
+
+
+def test_golden_regression_vector():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "ils_12x10_lam1_p08_N4.txt")
+    rows = [l for l in open(path) if not l.startswith("#")]
+    f = np.array([float(v) for v in rows[0].split()]).reshape(12, 10)
+    u = np.array([float(v) for v in rows[1].split()]).reshape(12, 10)
+    np.testing.assert_allclose(O.ils_channel(f, 1.0, 0.8, 1e-4, 4), u, atol=1e-12)
