@@ -1,0 +1,131 @@
+/*
+ * ils.h - C ABI of libils.so: Iterative Least Squares (ILS) edge-preserving
+ * smoothing on one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * Method: Liu, Zhang, Huang, Yang, Shen, Reid, "Real-time Image Smoothing via
+ * Iterative Least Squares" (arXiv 2003.07504).  Equation numbers follow the
+ * paper's LaTeX order:
+ *   Eq. 1  E(u,f) = sum_s (u_s-f_s)^2 + lambda sum_{*=x,y} phi_p(grad_* u_s)      (Sec. 3)
+ *   Eq. 2  phi_p(x) = (x^2 + eps)^(p/2)                                          (Sec. 3)
+ *   Eq. 7  mu_* = c grad_* u - p grad_* u (grad_* u^2 + eps)^(p/2-1)             (Sec. 3.1)
+ *   Eq. 9  u^{n+1} = F^-1[(F f + lambda/2 sum_* conj(F grad_*) F mu_*) /
+ *                         (F 1 + c lambda/2 sum_* |F grad_*|^2)]                 (Sec. 3.2)
+ *   Eq. 11 c = c0 = p eps^(p/2-1)                                                 (Sec. 3.3, App. B)
+ *   Algorithm 1: u^0 = f; N times: mu from u (Eq. 7), u from Eq. 9.
+ *   Sec. 3.4: colour channels are smoothed independently.
+ *
+ * Conventions shared by every entry point
+ *   - Images are planar C x H x W float32, row-major, contiguous (x fastest),
+ *     caller-owned.  Gradients are periodic forward differences
+ *     (grad_x u)[y,x] = u[y,(x+1)%W] - u[y,x], likewise in y (the periodic
+ *     boundary that Eq. 9 assumes).
+ *   - "Device pointer" means memory the CUDA device can address (cudaMalloc,
+ *     torch CUDA tensors).  All calls that take a stream are stream-ordered and
+ *     asynchronous: they enqueue work on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and return; the caller synchronizes.
+ *   - Every call returns an ils_status.  Nothing aborts or throws across the
+ *     ABI.  On ILS_ERR_CUDA the text of the CUDA error is available from
+ *     ils_last_error() on the calling thread.
+ *   - Supported sizes: 2 <= H, W <= 8192, W even, and both H and W of the form
+ *     2^a 3^b 5^c (the radices of the hand-written FFT).  Other sizes return
+ *     ILS_ERR_UNSUPPORTED_SIZE.
+ *   - A plan owns device workspace; it is not safe to use one plan from two
+ *     streams or threads at the same time.
+ */
+#ifndef ILS_H_
+#define ILS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ils_plan ils_plan; /* opaque */
+
+typedef enum {
+  ILS_OK = 0,
+  ILS_ERR_INVALID_ARG = 1,      /* null pointer, bad parameter, aliasing, wrong state */
+  ILS_ERR_UNSUPPORTED_SIZE = 2, /* H or W outside the supported set above */
+  ILS_ERR_OOM = 3,              /* a device or host allocation failed */
+  ILS_ERR_CUDA = 4,             /* a CUDA runtime call failed; see ils_last_error() */
+  ILS_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up (status word set by a kernel) */
+} ils_status;
+
+/* Human-readable name of a status code (static storage). */
+const char* ils_status_string(ils_status s);
+
+/* Text of the last CUDA error seen by an ILS call on this thread ("" if none). */
+const char* ils_last_error(void);
+
+/*
+ * ils_plan_create - validate parameters and build a plan for C x H x W images.
+ *   lambda >= 0 : smoothing strength (Eq. 1).  lambda = 0 returns f.
+ *   0 < p <= 1  : penalty power (Eq. 2; the paper's range, Sec. 3).  p = 2 is
+ *                 also accepted: c0 = 2 and mu = 0, i.e. one quadratic solve.
+ *   eps > 0     : Charbonnier constant (Eq. 2; the paper fixes 1e-4).
+ *   N >= 0      : iterations of Algorithm 1 (the paper fixes 4). N = 0 copies f.
+ *   c = c0 = p eps^(p/2-1) (Eq. 11) is used; ils_plan_c() returns it.
+ * Allocates device workspace of 2*C*H*W floats plus small tables on the current
+ * device.  *out receives the plan (NULL on failure).
+ */
+ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps, int N,
+                           ils_plan** out);
+
+/* Free a plan and its device memory.  NULL is accepted.  Synchronizes the device. */
+ils_status ils_plan_destroy(ils_plan* plan);
+
+/* The constant c the plan uses (Eq. 11).  Returns -1 for NULL. */
+float ils_plan_c(const ils_plan* plan);
+
+/*
+ * ils_smooth - Algorithm 1 with u^0 = f.
+ *   f : device pointer, C x H x W float32 input (read only).
+ *   u : device pointer, C x H x W float32 output; must not overlap f.
+ * If checkpointing is on (ils_set_checkpointing), also stores u^0..u^{N-1}
+ * inside the plan for ils_backward.
+ */
+ils_status ils_smooth(ils_plan* plan, const float* f, float* u, void* stream);
+
+/*
+ * ils_smooth_from - Algorithm 1 started from a given u^0 instead of f (warm start).
+ *   u0 : device pointer, C x H x W float32 (read only); may equal f.
+ *   u  : device pointer output; must overlap neither f nor u0.
+ */
+ils_status ils_smooth_from(ils_plan* plan, const float* f, const float* u0, float* u, void* stream);
+
+/*
+ * ils_smooth_host - ils_smooth on HOST buffers: copies f to the device, runs
+ * Algorithm 1, copies u back and synchronizes `stream` before returning.
+ *   f_host, u_host : host pointers to C x H x W float32 (page-locked memory
+ *                    gives full copy bandwidth; pageable memory also works).
+ * Uses device staging buffers owned by the plan (allocated on first use).
+ */
+ils_status ils_smooth_host(ils_plan* plan, const float* f_host, float* u_host, void* stream);
+
+/*
+ * Per-kernel timing, for measurement tools.  Kernel kinds of one ils_smooth call:
+ *   ILS_KERNEL_ROW_FIRST   - first fused row pass (reads f or u0; stencil; forward row FFT)
+ *   ILS_KERNEL_ROW         - later fused row passes (inverse row FFT of u^n; stencil; forward row FFT)
+ *   ILS_KERNEL_COLUMN      - column FFT, Eq. 9 division, inverse column FFT
+ *   ILS_KERNEL_ROW_INVERSE - final inverse row FFT writing u^N
+ * ils_set_profiling(plan, 1) creates CUDA events and clears the totals; while
+ * on, each smoothing call records an event on its stream before every launch
+ * and after the last, then waits for its own last event and adds the elapsed
+ * times per kind (so profiled calls are synchronous).  ils_set_profiling(plan, 0)
+ * turns it off and frees the events.  ils_get_profile copies the totals into
+ * ms[ILS_KERNEL_KINDS] and launches[ILS_KERNEL_KINDS] (host arrays).
+ */
+#define ILS_KERNEL_ROW_FIRST 0
+#define ILS_KERNEL_ROW 1
+#define ILS_KERNEL_COLUMN 2
+#define ILS_KERNEL_ROW_INVERSE 3
+#define ILS_KERNEL_KINDS 4
+ils_status ils_set_profiling(ils_plan* plan, int on);
+ils_status ils_get_profile(const ils_plan* plan, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ILS_H_ */

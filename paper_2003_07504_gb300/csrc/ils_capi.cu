@@ -1,0 +1,319 @@
+// C ABI of libils.so (declared in include/ils.h): plans, validation, tables and
+// the iteration driver of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ils.h"
+#include "ils_internal.h"
+
+using namespace ils;
+
+struct ils_plan {
+  int H, W, C, N;
+  float lambda, p, eps, c;
+  int device;
+  ImageDesc desc;
+  Geometry geo;
+  Tables tab;
+  MuParams mp;
+  float2* spec[2];     // ping-pong row-spectrum workspaces, C*H*(W/2) complex each
+  float* ckpt;         // N*C*H*W floats when checkpointing is on
+  float* stage_f;      // device staging for ils_smooth_host
+  float* stage_u;
+  // optional per-kernel event timing (ils_set_profiling)
+  bool profiling;
+  std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
+  std::vector<int> ev_kind;     // kind of the launch that starts at event i
+  double prof_ms[ILS_KERNEL_KINDS];
+  long long prof_launches[ILS_KERNEL_KINDS];
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ils_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return ILS_ERR_CUDA;
+}
+
+// Test hook: ILS_TEST_FAIL_ALLOC=k makes the k-th device allocation (1-based)
+// of an ils_plan_create call report out-of-memory.
+thread_local int g_alloc_count = 0;
+
+ils_status dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  const char* env = std::getenv("ILS_TEST_FAIL_ALLOC");
+  ++g_alloc_count;
+  if (env != nullptr && std::atoi(env) == g_alloc_count) {
+    g_last_error = "injected allocation failure";
+    return ILS_ERR_OOM;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    g_last_error = "cudaMalloc: out of memory";
+    *p = nullptr;
+    return ILS_ERR_OOM;
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  return ILS_OK;
+}
+
+bool smooth_235(int n) {
+  if (n < 1) return false;
+  for (int r : {2, 3, 5})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+void destroy_events(ils_plan* pl) {
+  for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  pl->ev.clear();
+  pl->ev_kind.clear();
+}
+
+void free_plan_memory(ils_plan* pl) {
+  destroy_events(pl);
+  cudaFree(pl->spec[0]);
+  cudaFree(pl->spec[1]);
+  cudaFree(pl->ckpt);
+  cudaFree(pl->stage_f);
+  cudaFree(pl->stage_u);
+  cudaFree(pl->tab.twW);
+  cudaFree(pl->tab.twH);
+  cudaFree(pl->tab.ax);
+  cudaFree(pl->tab.by);
+}
+
+// exp(-2 pi i t / L) for t = 0..L-1, double precision, reduced argument.
+std::vector<float2> roots(int L) {
+  std::vector<float2> v(L);
+  for (int t = 0; t < L; ++t) {
+    const double a = -2.0 * M_PI * (double)t / (double)L;
+    v[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return v;
+}
+
+// With profiling on, records an event before launch number `slot` of this call.
+cudaError_t mark(ils_plan* pl, int slot, int kind, cudaStream_t st) {
+  if (!pl->profiling) return cudaSuccess;
+  pl->ev_kind[slot] = kind;
+  return cudaEventRecord(pl->ev[slot], st);
+}
+
+ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, cudaStream_t st) {
+  const size_t n = (size_t)pl->C * pl->H * pl->W;
+  const size_t bytes = n * sizeof(float);
+  cudaError_t e;
+  if (pl->N == 0) {
+    e = cudaMemcpyAsync(u, u0 ? u0 : f, bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
+  }
+  int slot = 0;
+  for (int it = 0; it < pl->N; ++it) {
+    float2* out = pl->spec[it & 1];
+    const float2* in = it == 0 ? nullptr : pl->spec[(it - 1) & 1];
+    float* ck = pl->ckpt ? pl->ckpt + (size_t)it * n : nullptr;
+    if ((e = mark(pl, slot++, it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW, st))) return cuda_fail(e, "event");
+    if ((e = launch_row_forward(pl->desc, pl->geo, pl->tab, pl->mp, f, it == 0 ? u0 : nullptr, in, out, ck, st)))
+      return cuda_fail(e, "row pass launch");
+    if ((e = mark(pl, slot++, ILS_KERNEL_COLUMN, st))) return cuda_fail(e, "event");
+    if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, out, st))) return cuda_fail(e, "column pass launch");
+  }
+  if ((e = mark(pl, slot++, ILS_KERNEL_ROW_INVERSE, st))) return cuda_fail(e, "event");
+  if ((e = launch_row_inverse(pl->desc, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st)))
+    return cuda_fail(e, "inverse row pass launch");
+  if ((e = mark(pl, slot, -1, st))) return cuda_fail(e, "event");
+  if (pl->profiling) {
+    // accumulate this call's launch durations (waits for the call to finish)
+    if ((e = cudaEventSynchronize(pl->ev[slot]))) return cuda_fail(e, "cudaEventSynchronize");
+    for (int i = 0; i < slot; ++i) {
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, pl->ev[i], pl->ev[i + 1]))) return cuda_fail(e, "cudaEventElapsedTime");
+      pl->prof_ms[pl->ev_kind[i]] += ms;
+      pl->prof_launches[pl->ev_kind[i]] += 1;
+    }
+  }
+  return ILS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ils_status_string(ils_status s) {
+  switch (s) {
+    case ILS_OK: return "ILS_OK";
+    case ILS_ERR_INVALID_ARG: return "ILS_ERR_INVALID_ARG";
+    case ILS_ERR_UNSUPPORTED_SIZE: return "ILS_ERR_UNSUPPORTED_SIZE";
+    case ILS_ERR_OOM: return "ILS_ERR_OOM";
+    case ILS_ERR_CUDA: return "ILS_ERR_CUDA";
+    case ILS_ERR_TIMEOUT: return "ILS_ERR_TIMEOUT";
+  }
+  return "ILS_ERR_UNKNOWN";
+}
+
+const char* ils_last_error(void) { return g_last_error.c_str(); }
+
+ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps, int N, ils_plan** out) {
+  if (out == nullptr) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (C < 1 || N < 0 || !(lambda >= 0.0f) || !std::isfinite(lambda) || !(eps > 0.0f) || !std::isfinite(eps) ||
+      !((p > 0.0f && p <= 1.0f) || p == 2.0f))
+    return ILS_ERR_INVALID_ARG;
+  if (H < 2 || W < 2 || H > 8192 || W > 8192 || (W & 1) || !smooth_235(H) || !smooth_235(W))
+    return ILS_ERR_UNSUPPORTED_SIZE;
+  const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);
+  if (!std::isfinite(c) || (size_t)C * H * W > (size_t)1 << 31) return ILS_ERR_UNSUPPORTED_SIZE;
+
+  ils_plan* pl = new (std::nothrow) ils_plan();
+  if (pl == nullptr) return ILS_ERR_OOM;
+  g_alloc_count = 0;
+  pl->H = H; pl->W = W; pl->C = C; pl->N = N;
+  pl->lambda = lambda; pl->p = p; pl->eps = eps; pl->c = (float)c;
+  pl->desc.H = H; pl->desc.W = W; pl->desc.C = C;
+  const int M = W / 2;
+  if (!make_fft_plan(M, &pl->desc.planM) || !make_fft_plan(H, &pl->desc.planH) || !pick_geometry(H, W, &pl->geo)) {
+    delete pl;
+    return ILS_ERR_UNSUPPORTED_SIZE;
+  }
+  pl->mp.c = (float)c;
+  pl->mp.p = p;
+  pl->mp.eps = eps;
+  pl->mp.a = p / 2.0f - 1.0f;
+  pl->mp.half_lambda = 0.5f * lambda;
+
+  cudaError_t e;
+  if ((e = cudaGetDevice(&pl->device))) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
+  if ((e = set_kernel_attributes())) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute"); }
+
+  const size_t plane = (size_t)C * H * M;
+  ils_status s;
+  if ((s = dev_alloc((void**)&pl->spec[0], plane * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->spec[1], plane * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.twW, (size_t)W * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.twH, (size_t)H * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.ax, (size_t)(M + 1) * sizeof(float))) ||
+      (s = dev_alloc((void**)&pl->tab.by, (size_t)H * sizeof(float)))) {
+    free_plan_memory(pl);
+    delete pl;
+    return s;
+  }
+  // Eq. 9 denominator, separable: 1 + (lambda c / 2)(|F grad_x|^2 + |F grad_y|^2) with
+  // |F grad|^2 = 4 sin^2(pi k / n); stored as ax[k] + by[l], each lambda c * 2 sin^2.
+  std::vector<float> ax(M + 1), by(H);
+  for (int k = 0; k <= M; ++k) {
+    const double s1 = std::sin(M_PI * (double)k / (double)W);
+    ax[k] = (float)(2.0 * (double)lambda * c * s1 * s1);
+  }
+  for (int l = 0; l < H; ++l) {
+    const double s1 = std::sin(M_PI * (double)l / (double)H);
+    by[l] = (float)(2.0 * (double)lambda * c * s1 * s1);
+  }
+  std::vector<float2> tw = roots(W), th = roots(H);
+  if ((e = cudaMemcpy(pl->tab.twW, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(pl->tab.twH, th.data(), th.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(pl->tab.ax, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(pl->tab.by, by.data(), by.size() * sizeof(float), cudaMemcpyHostToDevice))) {
+    free_plan_memory(pl);
+    delete pl;
+    return cuda_fail(e, "cudaMemcpy tables");
+  }
+  *out = pl;
+  return ILS_OK;
+}
+
+ils_status ils_plan_destroy(ils_plan* pl) {
+  if (pl == nullptr) return ILS_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan_memory(pl);
+  delete pl;
+  return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaDeviceSynchronize");
+}
+
+float ils_plan_c(const ils_plan* pl) { return pl ? pl->c : -1.0f; }
+
+ils_status ils_set_profiling(ils_plan* pl, int on) {
+  if (pl == nullptr) return ILS_ERR_INVALID_ARG;
+  for (int k = 0; k < ILS_KERNEL_KINDS; ++k) {
+    pl->prof_ms[k] = 0.0;
+    pl->prof_launches[k] = 0;
+  }
+  if (!on) {
+    destroy_events(pl);
+    pl->profiling = false;
+    return ILS_OK;
+  }
+  if (pl->ev.empty()) {
+    const int slots = 2 * pl->N + 2;
+    pl->ev.assign(slots, nullptr);
+    pl->ev_kind.assign(slots, -1);
+    for (int i = 0; i < slots; ++i) {
+      cudaError_t e = cudaEventCreate(&pl->ev[i]);
+      if (e != cudaSuccess) {
+        destroy_events(pl);
+        return cuda_fail(e, "cudaEventCreate");
+      }
+    }
+  }
+  pl->profiling = true;
+  return ILS_OK;
+}
+
+ils_status ils_get_profile(const ils_plan* pl, double* ms, long long* launches) {
+  if (pl == nullptr || ms == nullptr || launches == nullptr) return ILS_ERR_INVALID_ARG;
+  for (int k = 0; k < ILS_KERNEL_KINDS; ++k) {
+    ms[k] = pl->prof_ms[k];
+    launches[k] = pl->prof_launches[k];
+  }
+  return ILS_OK;
+}
+
+ils_status ils_smooth_from(ils_plan* pl, const float* f, const float* u0, float* u, void* stream) {
+  if (pl == nullptr || f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  if (overlaps(f, u, bytes) || (u0 != nullptr && overlaps(u0, u, bytes))) return ILS_ERR_INVALID_ARG;
+  return run_ils(pl, f, u0, u, static_cast<cudaStream_t>(stream));
+}
+
+ils_status ils_smooth(ils_plan* pl, const float* f, float* u, void* stream) {
+  if (pl == nullptr || f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
+  return ils_smooth_from(pl, f, nullptr, u, stream);
+}
+
+ils_status ils_smooth_host(ils_plan* pl, const float* f_host, float* u_host, void* stream) {
+  if (pl == nullptr || f_host == nullptr || u_host == nullptr) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  ils_status s;
+  if (pl->stage_f == nullptr) {
+    if ((s = dev_alloc((void**)&pl->stage_f, bytes))) return s;
+  }
+  if (pl->stage_u == nullptr) {
+    if ((s = dev_alloc((void**)&pl->stage_u, bytes))) return s;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(pl->stage_f, f_host, bytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D copy");
+  if ((s = run_ils(pl, pl->stage_f, nullptr, pl->stage_u, st))) return s;
+  if ((e = cudaMemcpyAsync(u_host, pl->stage_u, bytes, cudaMemcpyDeviceToHost, st))) return cuda_fail(e, "D2H copy");
+  if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "cudaStreamSynchronize");
+  return ILS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+declared entry point, and rejects bad arguments before touching a GPU."""
+import ctypes
+
+import pytest
+
+from tests._util import declared_symbols
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2003_07504_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert "ils_plan_create" in names and "ils_smooth" in names
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_2003_07504_gb300 import _lib
+    assert set(declared_symbols()) <= set(_lib.SIGNATURES), set(declared_symbols()) - set(_lib.SIGNATURES)
+
+
+def test_status_strings(L):
+    for code, name in ((0, b"ILS_OK"), (1, b"ILS_ERR_INVALID_ARG"), (2, b"ILS_ERR_UNSUPPORTED_SIZE"),
+                       (3, b"ILS_ERR_OOM"), (4, b"ILS_ERR_CUDA"), (5, b"ILS_ERR_TIMEOUT")):
+        assert L.ils_status_string(code) == name
+
+
+def _create(L, H, W, C=1, lam=1.0, p=0.8, eps=1e-4, N=4):
+    h = ctypes.c_void_p()
+    return L.ils_plan_create(H, W, C, lam, p, eps, N, ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("args", [
+    dict(C=0), dict(N=-1), dict(lam=-1.0), dict(lam=float("nan")), dict(eps=0.0), dict(eps=-1e-4),
+    dict(p=0.0), dict(p=1.5), dict(p=-0.5), dict(lam=float("inf")),
+])
+def test_bad_parameters_are_rejected(L, args):
+    kw = dict(H=16, W=16)
+    kw.update(args)
+    st, h = _create(L, **kw)
+    assert st == 1 and not h.value
+
+
+@pytest.mark.parametrize("H,W", [(7, 16), (16, 14), (16, 15), (1, 16), (16, 0), (16384, 16), (16, 16384), (22, 16)])
+def test_unsupported_sizes_are_rejected(L, H, W):
+    st, h = _create(L, H, W)
+    assert st == 2 and not h.value
+
+
+def test_null_arguments(L):
+    assert L.ils_plan_create(16, 16, 1, 1.0, 0.8, 1e-4, 4, None) == 1
+    assert L.ils_smooth(None, None, None, None) == 1
+    assert L.ils_smooth_from(None, None, None, None, None) == 1
+    assert L.ils_smooth_host(None, None, None, None) == 1
+    assert L.ils_plan_destroy(None) == 0
+    assert L.ils_plan_c(None) == -1.0
