@@ -59,7 +59,7 @@ def voronoi_texture(H: int, W: int, C: int = 1, *, K: int = 12, A: float = 0.05,
     tex = A * np.sin(2 * np.pi * (xx * np.cos(th[lab]) + yy * np.sin(th[lab])) / T[lab] + ph[lab])
     img = val[:, lab] + tex[None]
     img += rng.normal(0.0, sigma, (C, H, W))
-    return np.clip(img, 0.0, 1.0).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img, 0.0, 1.0), dtype=np.float32)
 
 
 def preset_image(H: int, W: int, C: int, preset: str, seed: int) -> np.ndarray:
