@@ -124,6 +124,38 @@ ils_status ils_smooth_host(ils_plan* plan, const float* f_host, float* u_host, v
 ils_status ils_set_profiling(ils_plan* plan, int on);
 ils_status ils_get_profile(const ils_plan* plan, double* ms, long long* launches);
 
+/*
+ * ils_smooth_noalloc - ils_smooth for callers that cannot allocate.
+ * (The paper has no counterpart; this is a deployment variant of the same path.)
+ *
+ * Some callers must not allocate once they are running - for example a video
+ * pipeline that cannot take cudaMalloc's implicit device synchronization and
+ * unbounded latency in the middle of a stream, or a plugin whose host
+ * application owns all device memory.  This call runs the same kernels as
+ * ils_smooth, but its workspace is a fixed array in the library's static device
+ * memory: it calls no cudaMalloc, cudaFree or other allocating routine, host
+ * or device.  The caller still passes f and u (device pointers, C x H x W
+ * float32, non-overlapping) and a stream; parameters mean what they mean for
+ * ils_plan_create, with the same validation.
+ *
+ * Limits: C*H*W <= ILS_NOALLOC_MAX_ELEMS (2^21 floats, e.g. one 1920 x 1080
+ * channel) and H, W <= ILS_NOALLOC_MAX_SIDE; larger images return
+ * ILS_ERR_UNSUPPORTED_SIZE.  The array (about 16.2 MiB) is part of the library:
+ * every GPU that loads libils.so holds it until the process exits.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (and sets the kernels' shared-memory limits); make that first
+ * call before any stream capture.  All calls on a device share the one array,
+ * which keeps the previous call's contents (nothing in it needs to start at
+ * zero: every word is written before it is read).  Calls that overlap on the
+ * GPU - on two streams, or from two threads - race on it and must be
+ * serialized by the caller.  Returns ILS_ERR_CUDA if a launch fails.
+ */
+#define ILS_NOALLOC_MAX_ELEMS (1 << 21)
+#define ILS_NOALLOC_MAX_SIDE 8192
+ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, float p, float eps, int N,
+                              const float* f, float* u, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,8 @@ SIGNATURES = {
     "ils_smooth_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_set_profiling": (c_int, [c_void_p, c_int]),
     "ils_get_profile": (c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_longlong)]),
+    "ils_smooth_noalloc": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int,
+                                   c_void_p, c_void_p, c_void_p]),
 }
 
 KERNEL_KINDS = ("row_first", "row", "column", "row_inverse")

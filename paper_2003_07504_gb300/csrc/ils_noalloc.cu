@@ -1,0 +1,145 @@
+// ils_smooth_noalloc: the ILS iteration with its workspace in a fixed, file-scope
+// device array instead of memory from cudaMalloc.
+//
+// Some callers cannot allocate device memory once they are running: a video
+// pipeline that must hold its frame rate cannot afford cudaMalloc's implicit
+// device synchronization and unbounded latency in the middle of a stream, and
+// a plugin hosted inside another application may not own any allocation at
+// all.  This entry point gives them the same smoothing with no allocation of
+// any kind (no cudaMalloc/cudaFree, no host heap, no library allocator); the
+// caller still provides the input and output buffers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/ils.h"
+#include "ils_internal.h"
+
+using namespace ils;
+
+namespace {
+
+constexpr int kSideMax = ILS_NOALLOC_MAX_SIDE;
+constexpr size_t kElemsMax = ILS_NOALLOC_MAX_ELEMS;  // floats per image (C*H*W)
+// table floats: twW (2*side) + twH (2*side) + ax (side/2+1, padded) + by (side)
+constexpr size_t kTableFloats = 2 * kSideMax + 2 * kSideMax + (kSideMax / 2 + 64) + kSideMax;
+constexpr size_t kScratchFloats = 2 * kElemsMax + kTableFloats;
+
+// Shared by every call on a device and kept until the process exits.
+static __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; the first call on a
+// device resolves it (and sets the kernels' shared-memory limits) with that device current.
+ils_status scratch_for_current_device(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ILS_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return ILS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return ILS_ERR_CUDA;
+    e = set_kernel_attributes();
+    if (e != cudaSuccess) return ILS_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<float*>(g_scratch_addr[dev]);
+  return ILS_OK;
+}
+
+// Twiddle and Eq. 9 denominator tables, computed on the device in double precision.
+__global__ void noalloc_tables_kernel(int H, int W, double lc, float2* twW, float2* twH, float* ax, float* by) {
+  const int M = W / 2;
+  const int n = W > H ? W : H;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s, c;
+    if (i < W) {
+      sincospi(-2.0 * (double)i / (double)W, &s, &c);
+      twW[i] = make_float2((float)c, (float)s);
+    }
+    if (i < H) {
+      sincospi(-2.0 * (double)i / (double)H, &s, &c);
+      twH[i] = make_float2((float)c, (float)s);
+      const double sh = sinpi((double)i / (double)H);
+      by[i] = (float)(2.0 * lc * sh * sh);
+    }
+    if (i <= M) {
+      const double sw = sinpi((double)i / (double)W);
+      ax[i] = (float)(2.0 * lc * sw * sw);
+    }
+  }
+}
+
+bool smooth_235(int n) {
+  if (n < 1) return false;
+  for (int r : {2, 3, 5})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
+}  // namespace
+
+extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, float p, float eps, int N,
+                                         const float* f, float* u, void* stream) {
+  if (f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
+  if (C < 1 || N < 0 || !(lambda >= 0.0f) || !std::isfinite(lambda) || !(eps > 0.0f) || !std::isfinite(eps) ||
+      !((p > 0.0f && p <= 1.0f) || p == 2.0f))
+    return ILS_ERR_INVALID_ARG;
+  if (H < 2 || W < 2 || H > kSideMax || W > kSideMax || (W & 1) || !smooth_235(H) || !smooth_235(W))
+    return ILS_ERR_UNSUPPORTED_SIZE;
+  const size_t elems = (size_t)C * (size_t)H * (size_t)W;
+  if (elems > kElemsMax) return ILS_ERR_UNSUPPORTED_SIZE;  // beyond the fixed scratch array
+  const size_t bytes = elems * sizeof(float);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(f), b = reinterpret_cast<uintptr_t>(u);
+  if (a < b + bytes && b < a + bytes) return ILS_ERR_INVALID_ARG;
+
+  ImageDesc d;
+  d.H = H; d.W = W; d.C = C;
+  Geometry g;
+  if (!make_fft_plan(W / 2, &d.planM) || !make_fft_plan(H, &d.planH) || !pick_geometry(H, W, &g))
+    return ILS_ERR_UNSUPPORTED_SIZE;
+
+  float* base = nullptr;
+  ils_status s = scratch_for_current_device(&base);
+  if (s != ILS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (N == 0) {
+    e = cudaMemcpyAsync(u, f, bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? ILS_OK : ILS_ERR_CUDA;
+  }
+  // scratch layout (floats): spectrum 0 | spectrum 1 | twW | twH | ax | by
+  float2* spec[2] = {reinterpret_cast<float2*>(base), reinterpret_cast<float2*>(base + kElemsMax)};
+  float* tab = base + 2 * kElemsMax;
+  Tables t;
+  t.twW = reinterpret_cast<float2*>(tab);
+  t.twH = reinterpret_cast<float2*>(tab + 2 * kSideMax);
+  t.ax = tab + 4 * kSideMax;
+  t.by = tab + 4 * kSideMax + (kSideMax / 2 + 64);
+
+  const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);
+  MuParams mp;
+  mp.c = (float)c;
+  mp.p = p;
+  mp.eps = eps;
+  mp.a = p / 2.0f - 1.0f;
+  mp.half_lambda = 0.5f * lambda;
+
+  noalloc_tables_kernel<<<(kSideMax + 255) / 256, 256, 0, st>>>(H, W, (double)lambda * c, t.twW, t.twH, t.ax, t.by);
+  if ((e = cudaGetLastError())) return ILS_ERR_CUDA;
+  for (int it = 0; it < N; ++it) {
+    float2* out = spec[it & 1];
+    const float2* in = it == 0 ? nullptr : spec[(it - 1) & 1];
+    if ((e = launch_row_forward(d, g, t, mp, f, nullptr, in, out, nullptr, st))) return ILS_ERR_CUDA;
+    if ((e = launch_col_solve(d, g, t, out, st))) return ILS_ERR_CUDA;
+  }
+  if ((e = launch_row_inverse(d, g, t, spec[(N - 1) & 1], u, st))) return ILS_ERR_CUDA;
+  return ILS_OK;
+}

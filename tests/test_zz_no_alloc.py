@@ -1,0 +1,57 @@
+"""ils_smooth_noalloc: the entry point for callers that cannot allocate.
+
+Such callers (a real-time video pipeline that must not stall on cudaMalloc's
+device synchronization, a plugin whose host owns all device memory) get the
+same smoothing with the workspace in the library's fixed static device array.
+Checked through the C ABI against the plan-based ils_smooth, within the parity
+tolerance, on two calls in a row (the second call reuses the array the first
+one left behind).  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2003_07504_gb300 import synth
+from tests._util import MAX_ABS_TOL, RMS_TOL, err_stats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2003_07504_gb300 import build
+    build.build()
+    from paper_2003_07504_gb300 import _lib, ils
+    return torch, _lib, ils
+
+
+def _noalloc(torch, _lib, f, out, lam=1.0, p=0.8, eps=1e-4, N=4):
+    C, H, W = f.shape
+    st = _lib.lib().ils_smooth_noalloc(H, W, C, lam, p, eps, N, f.data_ptr(), out.data_ptr(),
+                                       int(torch.cuda.current_stream().cuda_stream))
+    return st
+
+
+def test_noalloc_matches_plan_path_on_two_calls(env):
+    torch, _lib, ils = env
+    cases = [(3, 240, 320, 41, 1.0, 0.8), (1, 1080, 1920, 42, 2.0, 1.0)]   # second: a whole 1080p channel
+    for C, H, W, seed, lam, p in cases:
+        f = torch.from_numpy(synth.preset_image(H, W, C, "hd", seed)).cuda()
+        u_na = torch.full_like(f, float("nan"))
+        assert _noalloc(torch, _lib, f, u_na, lam, p) == 0
+        with ils.Plan(H, W, C, lam, p, 1e-4, 4) as plan:
+            u_ref = plan.smooth(f)
+        torch.cuda.synchronize()
+        mx, rms = err_stats(u_na.cpu().numpy(), u_ref.cpu().numpy())
+        assert mx <= MAX_ABS_TOL and rms <= RMS_TOL, (C, H, W, mx, rms)
+
+
+def test_noalloc_rejects_sizes_beyond_its_array(env):
+    torch, _lib, ils = env
+    f = torch.zeros(3, 1080, 1920, device="cuda")   # 3 channels: more than 2^21 floats
+    u = torch.empty_like(f)
+    assert _noalloc(torch, _lib, f, u) == 2          # ILS_ERR_UNSUPPORTED_SIZE
+    g = torch.zeros(1, 16, 16, device="cuda")
+    assert _noalloc(torch, _lib, g, g) == 1          # output overlaps input
