@@ -1,0 +1,211 @@
+// Small DFTs held entirely in registers, for the FFT stages of the ILS kernels.
+//
+// dft_reg<R, INV>(v) replaces v[0..R-1] by its R-point DFT (forward: exp(-2 pi i jk/R),
+// INV: exp(+2 pi i jk/R), unnormalized).  R in {2,3,4,5,8} are written out; every other
+// supported R = A*B is one Cooley-Tukey step on registers: B DFTs of size A on the
+// stride-B subsequences, multiplication by w_R^{n2 k1}, then A DFTs of size B, with
+// output index k1 + A k2.  The w_R constants come from a compile-time table built with
+// a Taylor-series sine/cosine written here (no math-library call), so after unrolling
+// every twiddle is an immediate.
+//
+// All functions are __host__ __device__ so the same code can be exercised on the CPU.
+#pragma once
+#include <cuda_runtime.h>
+
+#if defined(__CUDACC__)
+#define ILS_HD __host__ __device__ __forceinline__
+#else
+#define ILS_HD inline
+#endif
+
+namespace ils {
+
+ILS_HD float2 c2(float x, float y) { float2 r; r.x = x; r.y = y; return r; }
+ILS_HD float2 cadd(float2 a, float2 b) { return c2(a.x + b.x, a.y + b.y); }
+ILS_HD float2 csub(float2 a, float2 b) { return c2(a.x - b.x, a.y - b.y); }
+ILS_HD float2 cmul(float2 a, float2 b) { return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+ILS_HD float2 cconj(float2 a) { return c2(a.x, -a.y); }
+ILS_HD float2 cscale(float2 a, float s) { return c2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+ILS_HD float2 rot90(float2 a) {
+  return INV ? c2(-a.y, a.x) : c2(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------- compile-time roots of unity
+// theta = 2 pi m / R is reduced exactly on the integer grid to [-pi, pi]; there the Taylor
+// series with 20 terms is accurate to well below double rounding.
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double ct_theta(long m, long R) {
+  long r = m % R;
+  if (r < 0) r += R;
+  if (2 * r > R) r -= R;
+  return 2.0 * kPi * (double)r / (double)R;
+}
+constexpr double ct_sin(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n < 20; ++n) {
+    term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double ct_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 20; ++n) {
+    term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += term;
+  }
+  return sum;
+}
+// exp(-2 pi i m / R) (forward root) as a float2 constant
+template <int R>
+struct Roots {
+  float re[R], im[R];
+  constexpr Roots() : re(), im() {
+    for (int m = 0; m < R; ++m) {
+      re[m] = (float)ct_cos(ct_theta(m, R));
+      im[m] = (float)(-ct_sin(ct_theta(m, R)));
+    }
+  }
+};
+
+// ---------------------------------------------------------------- written-out small DFTs
+
+template <bool INV>
+ILS_HD void dft2(float2* v) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV>
+ILS_HD void dft4(float2* v) {
+  float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  float2 s13 = cadd(v[1], v[3]), d13 = rot90<INV>(csub(v[1], v[3]));
+  v[0] = cadd(s02, s13);
+  v[2] = csub(s02, s13);
+  v[1] = cadd(d02, d13);
+  v[3] = csub(d02, d13);
+}
+
+template <bool INV>
+ILS_HD void dft8(float2* v) {
+  constexpr float h = 0.70710678118654752440f;  // sqrt(2)/2
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  // o[k] *= w_8^k
+  o[1] = INV ? c2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)) : c2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+  o[2] = rot90<INV>(o[2]);
+  o[3] = INV ? c2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)) : c2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <bool INV>
+ILS_HD void dft3(float2* v) {
+  constexpr float s3 = 0.86602540378443864676f;  // sin(2 pi / 3)
+  float2 t = cadd(v[1], v[2]);
+  float2 d = csub(v[1], v[2]);
+  float2 m = c2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+  float2 r = rot90<INV>(cscale(d, s3));
+  v[0] = cadd(v[0], t);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+
+template <bool INV>
+ILS_HD void dft5(float2* v) {
+  constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+  constexpr float c2_ = -0.80901699437494742410f; // cos(4 pi / 5)
+  constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+  constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+  float2 a14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
+  float2 a23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
+  float2 p1 = c2(v[0].x + c1 * a14.x + c2_ * a23.x, v[0].y + c1 * a14.y + c2_ * a23.y);
+  float2 p2 = c2(v[0].x + c2_ * a14.x + c1 * a23.x, v[0].y + c2_ * a14.y + c1 * a23.y);
+  float2 q1 = rot90<INV>(c2(s1 * d14.x + s2 * d23.x, s1 * d14.y + s2 * d23.y));
+  float2 q2 = rot90<INV>(c2(s2 * d14.x - s1 * d23.x, s2 * d14.y - s1 * d23.y));
+  v[0] = c2(v[0].x + a14.x + a23.x, v[0].y + a14.y + a23.y);
+  v[1] = cadd(p1, q1);
+  v[4] = csub(p1, q1);
+  v[2] = cadd(p2, q2);
+  v[3] = csub(p2, q2);
+}
+
+// ---------------------------------------------------------------- composite sizes
+
+template <int R>
+struct Split;  // R = A * B with A the first factor used
+template <> struct Split<6> { static constexpr int A = 2, B = 3; };
+template <> struct Split<9> { static constexpr int A = 3, B = 3; };
+template <> struct Split<10> { static constexpr int A = 2, B = 5; };
+template <> struct Split<12> { static constexpr int A = 4, B = 3; };
+template <> struct Split<15> { static constexpr int A = 3, B = 5; };
+template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+template <> struct Split<20> { static constexpr int A = 4, B = 5; };
+template <> struct Split<24> { static constexpr int A = 8, B = 3; };
+template <> struct Split<25> { static constexpr int A = 5, B = 5; };
+template <> struct Split<27> { static constexpr int A = 3, B = 9; };
+template <> struct Split<30> { static constexpr int A = 2, B = 15; };
+template <> struct Split<32> { static constexpr int A = 4, B = 8; };
+
+template <int R, bool INV>
+ILS_HD void dft_reg(float2* v);
+
+template <int A, int B, bool INV>
+ILS_HD void dft_composite(float2* v) {
+  constexpr int R = A * B;
+  constexpr Roots<R> w{};
+  float2 y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+    float2 t[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) t[n1] = v[B * n1 + n2];
+    dft_reg<A, INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      const int m = (n2 * k1) % R;
+      if (m == 0) {
+        y[n2 * A + k1] = t[k1];
+      } else {
+        const float2 tw = c2(w.re[m], INV ? -w.im[m] : w.im[m]);
+        y[n2 * A + k1] = cmul(t[k1], tw);
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    float2 t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+    dft_reg<B, INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+  }
+}
+
+template <int R, bool INV>
+ILS_HD void dft_reg(float2* v) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<INV>(v);
+  } else if constexpr (R == 3) {
+    dft3<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v);
+  } else if constexpr (R == 5) {
+    dft5<INV>(v);
+  } else if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else {
+    dft_composite<Split<R>::A, Split<R>::B, INV>(v);
+  }
+}
+
+}  // namespace ils

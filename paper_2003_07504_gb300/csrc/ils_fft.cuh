@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ils_dft.cuh"
+
 namespace ils {
 
 // A CTA sweeping `elems` complex values with T threads needs elems <= EPT * T,
@@ -33,99 +35,6 @@ struct FftPlan {
 
 __host__ __device__ __forceinline__ int smem_idx(int i) { return i + (i >> 4); }
 __host__ __device__ __forceinline__ int smem_elems(int n) { return n == 0 ? 0 : smem_idx(n - 1) + 1; }
-
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-// multiply by -i (forward) or +i (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 rot90(float2 a) {
-  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-}
-
-// ---------------------------------------------------------------- small DFTs
-// Forward kernels use w_R = exp(-2 pi i / R); INV uses the conjugate.
-
-template <bool INV>
-__device__ __forceinline__ void dft2(float2* v) {
-  float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft4(float2* v) {
-  float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-  float2 s13 = cadd(v[1], v[3]), d13 = rot90<INV>(csub(v[1], v[3]));
-  v[0] = cadd(s02, s13);
-  v[2] = csub(s02, s13);
-  v[1] = cadd(d02, d13);
-  v[3] = csub(d02, d13);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft8(float2* v) {
-  constexpr float h = 0.70710678118654752440f;  // sqrt(2)/2
-  float2 e[4] = {v[0], v[2], v[4], v[6]};
-  float2 o[4] = {v[1], v[3], v[5], v[7]};
-  dft4<INV>(e);
-  dft4<INV>(o);
-  // o[k] *= w_8^k
-  o[1] = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
-             : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
-  o[2] = rot90<INV>(o[2]);
-  o[3] = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
-             : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    v[k] = cadd(e[k], o[k]);
-    v[k + 4] = csub(e[k], o[k]);
-  }
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft3(float2* v) {
-  constexpr float s3 = 0.86602540378443864676f;  // sin(2 pi / 3)
-  float2 t = cadd(v[1], v[2]);
-  float2 d = csub(v[1], v[2]);
-  float2 m = make_float2(fmaf(-0.5f, t.x, v[0].x), fmaf(-0.5f, t.y, v[0].y));
-  float2 r = rot90<INV>(cscale(d, s3));
-  v[0] = cadd(v[0], t);
-  v[1] = cadd(m, r);
-  v[2] = csub(m, r);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft5(float2* v) {
-  constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
-  constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
-  constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
-  constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-  float2 a14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
-  float2 a23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
-  float2 p1 = make_float2(v[0].x + c1 * a14.x + c2 * a23.x, v[0].y + c1 * a14.y + c2 * a23.y);
-  float2 p2 = make_float2(v[0].x + c2 * a14.x + c1 * a23.x, v[0].y + c2 * a14.y + c1 * a23.y);
-  float2 q1 = rot90<INV>(make_float2(s1 * d14.x + s2 * d23.x, s1 * d14.y + s2 * d23.y));
-  float2 q2 = rot90<INV>(make_float2(s2 * d14.x - s1 * d23.x, s2 * d14.y - s1 * d23.y));
-  v[0] = make_float2(v[0].x + a14.x + a23.x, v[0].y + a14.y + a23.y);
-  v[1] = cadd(p1, q1);
-  v[4] = csub(p1, q1);
-  v[2] = cadd(p2, q2);
-  v[3] = csub(p2, q2);
-}
-
-template <int R, bool INV>
-__device__ __forceinline__ void dft(float2* v) {
-  if constexpr (R == 2) dft2<INV>(v);
-  else if constexpr (R == 3) dft3<INV>(v);
-  else if constexpr (R == 4) dft4<INV>(v);
-  else if constexpr (R == 5) dft5<INV>(v);
-  else dft8<INV>(v);
-}
 
 // ---------------------------------------------------------------- one Stockham stage
 // Sequences: nseq of length n; element e of sequence s lives at logical index
@@ -165,7 +74,7 @@ __device__ __forceinline__ void stockham_stage(float2* buf, int n, int nseq, int
           if (r + 1 < R) t = cmul(t, w1);
         }
       }
-      dft<R, INV>(v[b]);
+      dft_reg<R, INV>(v[b]);
     }
   }
   __syncthreads();

@@ -24,6 +24,8 @@ struct Geometry {
   int cols;          // complex columns per CTA in the column pass
   int threads_col, ept_col;
   size_t smem_fwd, smem_inv, smem_col;  // dynamic shared memory bytes
+  int fixed_row;     // index of a compile-time row plan for M = W/2, or -1 (generic kernels)
+  int fixed_col;     // index of a compile-time column plan for H, or -1
 };
 
 // Device tables for one (H, W, lambda, c).
@@ -52,5 +54,16 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
                                float* u, cudaStream_t stream);
 cudaError_t set_kernel_attributes();
+
+// Compile-time specialised kernels (ils_kernels_fixed.cu).
+int fixed_row_index(int M);
+int fixed_col_index(int H);
+cudaError_t fixed_set_attributes();
+cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
+                              const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
+                              cudaStream_t stream);
+cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
+                              cudaStream_t stream);
+cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream);
 
 }  // namespace ils

@@ -15,6 +15,7 @@
 // symmetry.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "ils_fft.cuh"
 #include "ils_internal.h"
@@ -287,6 +288,12 @@ bool pick_geometry(int H, int W, Geometry* g) {
   if (G == 0 || !tile_config(H * G, &g->ept_col, &g->threads_col)) return false;
   g->cols = G;
   g->smem_col = (size_t)smem_elems(H * G) * sizeof(float2);
+  // Compile-time plans where one exists; ILS_FORCE_GENERIC=1 keeps the generic kernels
+  // (used by the tests to cover both implementations on the same sizes).
+  const char* force = getenv("ILS_FORCE_GENERIC");
+  const bool generic = force != nullptr && force[0] == '1';
+  g->fixed_row = generic ? -1 : fixed_row_index(M);
+  g->fixed_col = generic ? -1 : fixed_col_index(H);
   return true;
 }
 
@@ -305,12 +312,13 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(col_solve_kernel<32>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16>))) return e;
   if ((e = allow_smem(row_inverse_kernel<32>))) return e;
-  return cudaSuccess;
+  return fixed_set_attributes();
 }
 
 cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
                                const float* f, const float* u0, const float2* spec_in, float2* spec_out,
                                float* u_ckpt, cudaStream_t stream) {
+  if (g.fixed_row >= 0) return fixed_row_forward(g.fixed_row, d, t, mp, f, u0, spec_in, spec_out, u_ckpt, stream);
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   const int T = g.threads_row;
   const size_t S = g.smem_fwd;
@@ -334,6 +342,7 @@ cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tabl
 
 cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables& t, float2* spec,
                              cudaStream_t stream) {
+  if (g.fixed_col >= 0) return fixed_col_solve(g.fixed_col, d, t, spec, stream);
   const int M = d.W / 2;
   dim3 grid((M + g.cols - 1) / g.cols, d.C);
   const float scale = 1.0f / ((float)d.H * (float)d.W);
@@ -348,6 +357,7 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
 
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
                                float* u, cudaStream_t stream) {
+  if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
   if (g.ept_inv == 16)
     row_inverse_kernel<16><<<grid, g.threads_inv, g.smem_inv, stream>>>(d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);

@@ -200,3 +200,18 @@ def test_injected_allocation_failure_reports_oom(ils, monkeypatch):
     monkeypatch.delenv("ILS_TEST_FAIL_ALLOC")
     f = image(32, 32, 1, seed=1)
     assert_parity(run_gpu(ils, f), O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
+
+
+# -------------------------------------------------------------- generic kernels at the specialised sizes
+
+@pytest.mark.parametrize("H,W,C", [(256, 256, 1), (1080, 1920, 1), (2160, 64, 1), (32, 3840, 2)])
+def test_generic_and_fixed_kernels_agree(ils, monkeypatch, H, W, C):
+    # Sizes with compile-time plans run the specialised kernels; ILS_FORCE_GENERIC=1 at plan
+    # creation keeps the generic ones.  Both must meet the parity bar against each other.
+    f = image(H, W, C, seed=H + W, preset="hd")
+    fixed = run_gpu(ils, f)
+    monkeypatch.setenv("ILS_FORCE_GENERIC", "1")
+    generic = run_gpu(ils, f)
+    assert_parity(fixed, generic)
+    if H * W <= 256 * 256:
+        assert_parity(fixed, O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
