@@ -82,8 +82,6 @@ float ils_plan_c(const ils_plan* plan);
  * ils_smooth - Algorithm 1 with u^0 = f.
  *   f : device pointer, C x H x W float32 input (read only).
  *   u : device pointer, C x H x W float32 output; must not overlap f.
- * If checkpointing is on (ils_set_checkpointing), also stores u^0..u^{N-1}
- * inside the plan for ils_backward.
  */
 ils_status ils_smooth(ils_plan* plan, const float* f, float* u, void* stream);
 
@@ -102,6 +100,31 @@ ils_status ils_smooth_from(ils_plan* plan, const float* f, const float* u0, floa
  * Uses device staging buffers owned by the plan (allocated on first use).
  */
 ils_status ils_smooth_host(ils_plan* plan, const float* f_host, float* u_host, void* stream);
+
+/*
+ * ils_smooth_checkpointed - Algorithm 1 (from u0, or from f when u0 is NULL) that
+ * also stores the iterates u^0 .. u^{N-1} for ils_backward.
+ *   ckpt : device pointer, caller-owned, N x C x H x W float32 (iterate n at offset
+ *          n*C*H*W); must not overlap f, u0 or u.  May be NULL only when N = 0.
+ */
+ils_status ils_smooth_checkpointed(ils_plan* plan, const float* f, const float* u0, float* u, float* ckpt,
+                                   void* stream);
+
+/*
+ * ils_backward - gradient of a scalar loss L through Algorithm 1 (reverse mode; the
+ * paper has no adjoint, this is the chain rule through Eq. 9 and Eq. 7).  With A the
+ * Eq. 9 operator (symmetric) and g = dL/du^{n+1}, each step computes r = A^-1 g with
+ * the same FFT solve, adds r to dL/df, and forms dL/du^n =
+ * lambda/2 sum_* grad_*^T [g''(grad_* u^n) * grad_* r], g'' from Appendix B.
+ *   ckpt    : the iterates written by ils_smooth_checkpointed for this input (read only).
+ *   grad_u  : device pointer, dL/du^N, C x H x W (read only).
+ *   grad_f  : device pointer, receives dL/df (the direct dependence through Eq. 9's F(f)),
+ *             plus dL/du^0 when grad_u0 is NULL (u^0 = f for plain smoothing).
+ *   grad_u0 : NULL, or a device pointer receiving dL/du^0 separately (warm starts).
+ * Outputs must not overlap each other or grad_u.
+ */
+ils_status ils_backward(ils_plan* plan, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
+                        void* stream);
 
 /*
  * Per-kernel timing, for measurement tools.  Kernel kinds of one ils_smooth call:

@@ -243,7 +243,7 @@ def energy(u, f, lam, p, eps):
 # Adjoint of Algorithm 1 with respect to f
 # ----------------------------------------------------------------------------
 
-def ils_backward(f, grad_u, lam, p, eps, N, c=None):
+def ils_backward(f, grad_u, lam, p, eps, N, c=None, u0=None, split=False):
     """Gradient of <grad_u, u^N(f)> with respect to f, on one H x W channel (float64).
 
     The paper has no adjoint; this is the chain rule through Algorithm 1.
@@ -252,13 +252,15 @@ def ils_backward(f, grad_u, lam, p, eps, N, c=None):
     u^{n+1} = A^{-1} (f + lam/2 sum_* grad_*^T mu(grad_* u^n)), u^0 = f, so with
     g = dL/du^{n+1}:
         r = A^{-1} g;   dL/df += r;   dL/du^n = lam/2 sum_* grad_*^T [ g''(grad_* u^n) * grad_* r ],
-    where g'' = d mu / dx is the Appendix B second derivative.  Finally dL/df += dL/du^0.
+    where g'' = d mu / dx is the Appendix B second derivative.  Finally dL/df += dL/du^0
+    (u^0 = f).  With a warm start u0 the iterates start from u0 and, if split, the pair
+    (dL/df through Eq. 9 only, dL/du^0) is returned instead of their sum.
     """
     f = np.asarray(f, dtype=np.float64)
     H, W = f.shape
     if c is None:
         c = c0(p, eps)
-    _, iterates = ils_channel(f, lam, p, eps, N, c=c, return_iterates=True)
+    _, iterates = ils_channel(f, lam, p, eps, N, u0=u0, c=c, return_iterates=True)
     den = denominator(H, W, lam, c)
     g = np.asarray(grad_u, dtype=np.float64).copy()
     gf = np.zeros_like(f)
@@ -268,7 +270,7 @@ def ils_backward(f, grad_u, lam, p, eps, N, c=None):
         un = iterates[n]
         g = (lam / 2.0) * (grad_x_T(g2(grad_x(un), p, eps, c) * grad_x(r))
                            + grad_y_T(g2(grad_y(un), p, eps, c) * grad_y(r)))
-    return gf + g
+    return (gf, g) if split else gf + g
 
 
 # ----------------------------------------------------------------------------

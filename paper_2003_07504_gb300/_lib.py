@@ -50,6 +50,8 @@ SIGNATURES = {
     "ils_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_smooth_checkpointed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_set_profiling": (c_int, [c_void_p, c_int]),
     "ils_get_profile": (c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_longlong)]),
     "ils_smooth_noalloc": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int,

@@ -23,7 +23,6 @@ struct ils_plan {
   Tables tab;
   MuParams mp;
   float2* spec[2];     // ping-pong row-spectrum workspaces, C*H*(W/2) complex each
-  float* ckpt;         // N*C*H*W floats when checkpointing is on
   float* stage_f;      // device staging for ils_smooth_host
   float* stage_u;
   // optional per-kernel event timing (ils_set_profiling)
@@ -76,10 +75,12 @@ bool smooth_235(int n) {
   return n == 1;
 }
 
-bool overlaps(const void* a, const void* b, size_t bytes) {
+// [a, a + na) and [b, b + nb) intersect
+bool overlaps2(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-  return x < y + bytes && y < x + bytes;
+  return x < y + nb && y < x + na;
 }
+bool overlaps(const void* a, const void* b, size_t bytes) { return overlaps2(a, bytes, b, bytes); }
 
 void destroy_events(ils_plan* pl) {
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
@@ -91,7 +92,6 @@ void free_plan_memory(ils_plan* pl) {
   destroy_events(pl);
   cudaFree(pl->spec[0]);
   cudaFree(pl->spec[1]);
-  cudaFree(pl->ckpt);
   cudaFree(pl->stage_f);
   cudaFree(pl->stage_u);
   cudaFree(pl->tab.twW);
@@ -117,7 +117,7 @@ cudaError_t mark(ils_plan* pl, int slot, int kind, cudaStream_t st) {
   return cudaEventRecord(pl->ev[slot], st);
 }
 
-ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, cudaStream_t st) {
+ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st) {
   const size_t n = (size_t)pl->C * pl->H * pl->W;
   const size_t bytes = n * sizeof(float);
   cudaError_t e;
@@ -129,7 +129,7 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, cuda
   for (int it = 0; it < pl->N; ++it) {
     float2* out = pl->spec[it & 1];
     const float2* in = it == 0 ? nullptr : pl->spec[(it - 1) & 1];
-    float* ck = pl->ckpt ? pl->ckpt + (size_t)it * n : nullptr;
+    float* ck = ckpt ? ckpt + (size_t)it * n : nullptr;
     if ((e = mark(pl, slot++, it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW, st))) return cuda_fail(e, "event");
     if ((e = launch_row_forward(pl->desc, pl->geo, pl->tab, pl->mp, f, it == 0 ? u0 : nullptr, in, out, ck, st)))
       return cuda_fail(e, "row pass launch");
@@ -289,7 +289,61 @@ ils_status ils_smooth_from(ils_plan* pl, const float* f, const float* u0, float*
   if (pl == nullptr || f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
   const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
   if (overlaps(f, u, bytes) || (u0 != nullptr && overlaps(u0, u, bytes))) return ILS_ERR_INVALID_ARG;
-  return run_ils(pl, f, u0, u, static_cast<cudaStream_t>(stream));
+  return run_ils(pl, f, u0, u, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+ils_status ils_smooth_checkpointed(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt,
+                                   void* stream) {
+  if (pl == nullptr || f == nullptr || u == nullptr || (ckpt == nullptr && pl->N > 0)) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  const size_t cbytes = bytes * (size_t)pl->N;
+  if (overlaps(f, u, bytes) || (u0 != nullptr && overlaps(u0, u, bytes))) return ILS_ERR_INVALID_ARG;
+  if (pl->N > 0 && (overlaps2(ckpt, cbytes, f, bytes) || overlaps2(ckpt, cbytes, u, bytes) ||
+                    (u0 != nullptr && overlaps2(ckpt, cbytes, u0, bytes))))
+    return ILS_ERR_INVALID_ARG;
+  return run_ils(pl, f, u0, u, pl->N > 0 ? ckpt : nullptr, static_cast<cudaStream_t>(stream));
+}
+
+ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
+                        void* stream) {
+  if (pl == nullptr || grad_u == nullptr || grad_f == nullptr || (ckpt == nullptr && pl->N > 0))
+    return ILS_ERR_INVALID_ARG;
+  const size_t n = (size_t)pl->C * pl->H * pl->W;
+  const size_t bytes = n * sizeof(float);
+  if (overlaps(grad_u, grad_f, bytes) || (grad_u0 != nullptr && (overlaps(grad_u0, grad_f, bytes) ||
+                                                               overlaps(grad_u0, grad_u, bytes))))
+    return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (pl->N == 0) {
+    // u = u^0: the whole gradient belongs to u^0 (= f unless a separate u^0 gradient is asked for)
+    if (grad_u0 != nullptr) {
+      if ((e = cudaMemcpyAsync(grad_u0, grad_u, bytes, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy");
+      if ((e = cudaMemsetAsync(grad_f, 0, bytes, st))) return cuda_fail(e, "memset");
+    } else if ((e = cudaMemcpyAsync(grad_f, grad_u, bytes, cudaMemcpyDeviceToDevice, st))) {
+      return cuda_fail(e, "copy");
+    }
+    return ILS_OK;
+  }
+  // spectrum of grad_u (a row pass with lambda = 0 is a plain forward row FFT), then r = A^-1 grad_u
+  MuParams plain = pl->mp;
+  plain.half_lambda = 0.0f;
+  if ((e = launch_row_forward(pl->desc, pl->geo, pl->tab, plain, grad_u, grad_u, nullptr, pl->spec[0], nullptr, st)))
+    return cuda_fail(e, "row pass launch");
+  if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, pl->spec[0], st))) return cuda_fail(e, "column pass launch");
+  int cur = 0;
+  for (int it = pl->N - 1; it >= 0; --it) {
+    const bool last = it == 0;
+    if ((e = launch_row_adjoint(pl->desc, pl->geo, pl->tab, pl->mp, pl->spec[cur], ckpt + (size_t)it * n, grad_f,
+                                it == pl->N - 1, grad_u0, last, pl->spec[cur ^ 1], st)))
+      return cuda_fail(e, "adjoint row pass launch");
+    if (!last) {
+      if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, pl->spec[cur ^ 1], st)))
+        return cuda_fail(e, "column pass launch");
+      cur ^= 1;
+    }
+  }
+  return ILS_OK;
 }
 
 ils_status ils_smooth(ils_plan* pl, const float* f, float* u, void* stream) {
@@ -310,7 +364,7 @@ ils_status ils_smooth_host(ils_plan* pl, const float* f_host, float* u_host, voi
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(pl->stage_f, f_host, bytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D copy");
-  if ((s = run_ils(pl, pl->stage_f, nullptr, pl->stage_u, st))) return s;
+  if ((s = run_ils(pl, pl->stage_f, nullptr, pl->stage_u, nullptr, st))) return s;
   if ((e = cudaMemcpyAsync(u_host, pl->stage_u, bytes, cudaMemcpyDeviceToHost, st))) return cuda_fail(e, "D2H copy");
   if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "cudaStreamSynchronize");
   return ILS_OK;

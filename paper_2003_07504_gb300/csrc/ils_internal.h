@@ -53,6 +53,9 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
                              cudaStream_t stream);
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
                                float* u, cudaStream_t stream);
+cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
+                               const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
+                               bool last, float2* spec_out, cudaStream_t stream);
 cudaError_t set_kernel_attributes();
 
 // Compile-time specialised kernels (ils_kernels_fixed.cu).

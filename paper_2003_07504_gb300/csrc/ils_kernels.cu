@@ -82,7 +82,9 @@ row_forward_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
 #pragma unroll
   for (int b = 0; b < EPT; ++b) {
     const int w = threadIdx.x + b * T;
-    if (w < nout * M) {
+    if (w < nout * M && mp.half_lambda == 0.0f) {   // lambda = 0 (or a plain row FFT): r = f
+      rr[b] = fc[w];
+    } else if (w < nout * M) {
       const int i = w / M;
       const int m = w - i * M;
       const int ci = (i + 1) * M;
@@ -179,6 +181,117 @@ col_solve_kernel(int H, int M, int G, FftPlan planH, const float2* __restrict__ 
     const int y = w / g;
     base[(size_t)y * M + (w - y * g)] = sm[smem_idx(w)];
   }
+}
+
+// ---------------------------------------------------------------- adjoint row pass
+// Reverse-mode step n of Algorithm 1 (not in the paper; the chain rule through Eq. 9 and Eq. 7).
+// With A the Eq. 9 operator (symmetric: its Fourier eigenvalues are real and even) and
+// gbar = dL/du^{n+1}: r = A^-1 gbar arrives as a row spectrum from the column pass.
+//   fbar += r                                            (u^{n+1} depends on f linearly)
+//   gbar' = lambda/2 sum_* grad_*^T [ g''(grad_* u^n) * grad_* r ]   (dL/du^n; g'' = dmu/dx, App. B)
+// and gbar' is forward-FFT'd for the next step, or (last step) added to the u^0 gradient.
+// g''(x) = c - p (x^2+eps)^(p/2-2) ((p-1) x^2 + eps).
+__device__ __forceinline__ float g2_appb(float x, const MuParams& mp) {
+  const float x2 = x * x;
+  const float t = x2 + mp.eps;
+  const float w = exp2f((mp.a - 1.0f) * __log2f(t));
+  return fmaf(-mp.p * w, fmaf(mp.p - 1.0f, x2, mp.eps), mp.c);
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
+row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW, MuParams mp,
+                   const float2* __restrict__ spec_in, const float* __restrict__ u_n, float* __restrict__ fbar,
+                   int fbar_first, float* __restrict__ gu0, int last, float2* __restrict__ spec_out) {
+  extern __shared__ float2 sm[];
+  const int M = W >> 1;
+  const int ch = blockIdx.y;
+  const int y0 = blockIdx.x * rows;
+  const int nout = min(rows, H - y0);
+  const int nin = nout + 2;
+  const size_t plane = (size_t)H * M;
+  const int T = blockDim.x;
+  {
+    const float2* src = spec_in + ch * plane;
+    for (int w = threadIdx.x; w < nin * M; w += T) {
+      const int i = w / M;
+      const int m = w - i * M;
+      sm[smem_idx(w)] = src[(size_t)wrap_row(y0 - 1 + i, H) * M + m];
+    }
+    __syncthreads();
+    const int P = M / 2 + 1;
+    for (int w = threadIdx.x; w < nin * P; w += T) {
+      const int i = w / P;
+      c2r_pre_pair(sm, i * M, M, w - i * P, twW);
+    }
+    __syncthreads();
+    fft_smem<EPT, true>(sm, planM, nin, 1, M, twW, 2);
+  }
+  const float2* uc = reinterpret_cast<const float2*>(u_n) + ch * plane;
+  float2* fb = reinterpret_cast<float2*>(fbar) + ch * plane;
+  float2* g0 = gu0 ? reinterpret_cast<float2*>(gu0) + ch * plane : nullptr;
+  float2 rr[EPT];
+#pragma unroll
+  for (int b = 0; b < EPT; ++b) {
+    const int w = threadIdx.x + b * T;
+    if (w < nout * M) {
+      const int i = w / M;
+      const int m = w - i * M;
+      const int y = y0 + i;
+      const int ml = m == 0 ? M - 1 : m - 1, mr = m == M - 1 ? 0 : m + 1;
+      const int ci = (i + 1) * M;
+      const float2 rc = sm[smem_idx(ci + m)];
+      const float rl = sm[smem_idx(ci + ml)].y;
+      const float rrt = sm[smem_idx(ci + mr)].x;
+      const float2 ru = sm[smem_idx(i * M + m)];
+      const float2 rd = sm[smem_idx((i + 2) * M + m)];
+      const float2 uc0 = uc[(size_t)y * M + m];
+      const float ul = uc[(size_t)y * M + ml].y;
+      const float ur = uc[(size_t)y * M + mr].x;
+      const float2 uu = uc[(size_t)wrap_row(y - 1, H) * M + m];
+      const float2 ud = uc[(size_t)wrap_row(y + 1, H) * M + m];
+      // q_x at x0-1, x0, x0+1 and q_y at (y-1, x) and (y, x)
+      const float qx_l = g2_appb(uc0.x - ul, mp) * (rc.x - rl);
+      const float qx_c = g2_appb(uc0.y - uc0.x, mp) * (rc.y - rc.x);
+      const float qx_r = g2_appb(ur - uc0.y, mp) * (rrt - rc.y);
+      const float qy0u = g2_appb(uc0.x - uu.x, mp) * (rc.x - ru.x);
+      const float qy0d = g2_appb(ud.x - uc0.x, mp) * (rd.x - rc.x);
+      const float qy1u = g2_appb(uc0.y - uu.y, mp) * (rc.y - ru.y);
+      const float qy1d = g2_appb(ud.y - uc0.y, mp) * (rd.y - rc.y);
+      const float2 gb = make_float2(mp.half_lambda * ((qx_l - qx_c) + (qy0u - qy0d)),
+                                    mp.half_lambda * ((qx_c - qx_r) + (qy1u - qy1d)));
+      const size_t o = (size_t)y * M + m;
+      float2 acc = fbar_first ? make_float2(0.f, 0.f) : fb[o];
+      acc.x += rc.x;
+      acc.y += rc.y;
+      if (last && g0 == nullptr) {
+        acc.x += gb.x;
+        acc.y += gb.y;
+      }
+      fb[o] = acc;
+      if (last && g0 != nullptr) g0[o] = gb;
+      rr[b] = gb;
+    }
+  }
+  if (last) return;   // block-uniform
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < EPT; ++b) {
+    const int w = threadIdx.x + b * T;
+    if (w < nout * M) sm[smem_idx(w)] = rr[b];
+  }
+  __syncthreads();
+  fft_smem<EPT, false>(sm, planM, nout, 1, M, twW, 2);
+  {
+    const int P = M / 2 + 1;
+    for (int w = threadIdx.x; w < nout * P; w += T) {
+      const int i = w / P;
+      r2c_post_pair(sm, i * M, M, w - i * P, twW);
+    }
+  }
+  __syncthreads();
+  float2* dst = spec_out + ch * plane + (size_t)y0 * M;
+  for (int w = threadIdx.x; w < nout * M; w += T) dst[w] = sm[smem_idx(w)];
 }
 
 // ---------------------------------------------------------------- (3) final inverse row pass
@@ -312,6 +425,8 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(col_solve_kernel<32>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16>))) return e;
   if ((e = allow_smem(row_inverse_kernel<32>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<16>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<32>))) return e;
   return fixed_set_attributes();
 }
 
@@ -363,6 +478,21 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
     row_inverse_kernel<16><<<grid, g.threads_inv, g.smem_inv, stream>>>(d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
   else
     row_inverse_kernel<32><<<grid, g.threads_inv, g.smem_inv, stream>>>(d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
+                               const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
+                               bool last, float2* spec_out, cudaStream_t stream) {
+  dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
+  if (g.ept_row == 16)
+    row_adjoint_kernel<16><<<grid, g.threads_row, g.smem_fwd, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp,
+                                                                        spec_in, u_n, fbar, fbar_first, gu0, last,
+                                                                        spec_out);
+  else
+    row_adjoint_kernel<32><<<grid, g.threads_row, g.smem_fwd, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp,
+                                                                        spec_in, u_n, fbar, fbar_first, gu0, last,
+                                                                        spec_out);
   return cudaGetLastError();
 }
 

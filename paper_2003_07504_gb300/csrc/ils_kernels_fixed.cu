@@ -342,7 +342,10 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
           const int m = t + q * T;
-          if (m < M) {
+          if (m < M && mp.half_lambda == 0.0f) {   // lambda = 0 (or a plain row FFT): r = f
+            rv[q] = fr[m];
+            if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = U(o + 1, m);
+          } else if (m < M) {
             const float2 c = U(o + 1, m);
             const float ul = U(o + 1, m == 0 ? M - 1 : m - 1).y;
             const float ur = U(o + 1, m == M - 1 ? 0 : m + 1).x;

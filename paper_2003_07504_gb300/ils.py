@@ -85,6 +85,35 @@ class Plan:
             _lib.check(st, "ils_smooth_from")
         return out
 
+    def smooth_checkpointed(self, f: torch.Tensor, out: torch.Tensor | None = None,
+                            u0: torch.Tensor | None = None, stream=None):
+        """Forward pass that also returns the iterates u^0..u^{N-1} (N x C x H x W) for backward()."""
+        f3 = self._as3d(f)
+        _check_image(f3, self.shape, "f")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_image(self._as3d(out), self.shape, "out")
+        if u0 is not None:
+            _check_image(self._as3d(u0), self.shape, "u0")
+        ckpt = torch.empty((max(self.N, 1),) + self.shape, dtype=torch.float32, device=f.device)
+        st = _lib.lib().ils_smooth_checkpointed(self._h, f.data_ptr(), 0 if u0 is None else u0.data_ptr(),
+                                                out.data_ptr(), ckpt.data_ptr(), _stream_ptr(stream))
+        _lib.check(st, "ils_smooth_checkpointed")
+        return out, ckpt
+
+    def backward(self, ckpt: torch.Tensor, grad_u: torch.Tensor, separate_u0: bool = False, stream=None):
+        """dL/df (and dL/du^0 if separate_u0) from dL/du^N and the forward's checkpoints."""
+        _check_image(self._as3d(grad_u), self.shape, "grad_u")
+        if ckpt.dtype != torch.float32 or not ckpt.is_cuda or not ckpt.is_contiguous() or \
+                tuple(ckpt.shape) != (max(self.N, 1),) + self.shape:
+            raise ValueError("ckpt must come from smooth_checkpointed of this plan")
+        grad_f = torch.empty_like(grad_u)
+        grad_u0 = torch.empty_like(grad_u) if separate_u0 else None
+        st = _lib.lib().ils_backward(self._h, ckpt.data_ptr(), grad_u.data_ptr(), grad_f.data_ptr(),
+                                     0 if grad_u0 is None else grad_u0.data_ptr(), _stream_ptr(stream))
+        _lib.check(st, "ils_backward")
+        return (grad_f, grad_u0) if separate_u0 else grad_f
+
     def set_profiling(self, on: bool) -> None:
         _lib.check(_lib.lib().ils_set_profiling(self._h, 1 if on else 0), "ils_set_profiling")
 
@@ -104,6 +133,38 @@ class Plan:
         st = _lib.lib().ils_smooth_host(self._h, f_host.data_ptr(), out_host.data_ptr(), _stream_ptr(stream))
         _lib.check(st, "ils_smooth_host")
         return out_host
+
+
+class ILSFunction(torch.autograd.Function):
+    """u = ILS(f) (optionally from a warm start u0) as a differentiable op.
+
+    Forward keeps the iterates u^0..u^{N-1} (caller-owned checkpoints, one N x C x H x W
+    tensor per call) and backward runs the library's hand-written adjoint on them.
+    """
+
+    @staticmethod
+    def forward(ctx, f, plan, u0=None):
+        fc = f.contiguous()
+        u0c = None if u0 is None else u0.contiguous()
+        u, ckpt = plan.smooth_checkpointed(fc, u0=u0c)
+        ctx.plan = plan
+        ctx.has_u0 = u0 is not None
+        ctx.save_for_backward(ckpt)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (ckpt,) = ctx.saved_tensors
+        g = grad_u.contiguous()
+        if ctx.has_u0:
+            gf, gu0 = ctx.plan.backward(ckpt, g, separate_u0=True)
+            return gf, None, gu0
+        return ctx.plan.backward(ckpt, g), None, None
+
+
+def ils_function(f: torch.Tensor, plan: Plan, u0: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable ILS (see ILSFunction)."""
+    return ILSFunction.apply(f, plan, u0)
 
 
 _plans: dict = {}

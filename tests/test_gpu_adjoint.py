@@ -1,0 +1,133 @@
+"""The hand-written adjoint (ils_backward through the C ABI, and ILSFunction in autograd)
+against the FP64 oracle's reverse-mode gradient and finite differences of the oracle.
+
+Bar: relative max-norm error <= 1e-4 against the FP64 gradient.  FP32 forward errors are
+~1e-6 of a [0,1] image; g'' = c - h(x) cancels to O(x^2) near x = 0 with c ~ 200, so its
+absolute FP32 error is ~1e-5 c-relative, which bounds the gradient error well below 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_07504_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ils():
+    import torch
+    from paper_2003_07504_gb300 import build
+    build.build()
+    from paper_2003_07504_gb300 import ils as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def rel_err(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(1e-30, np.abs(b).max()))
+
+
+def gpu_grad(ils, f, w, lam=1.0, p=0.8, N=4, u0=None, separate=False):
+    import torch
+    C, H, W = f.shape
+    with ils.Plan(H, W, C, lam, p, 1e-4, N) as plan:
+        ft = torch.from_numpy(f).cuda()
+        u0t = None if u0 is None else torch.from_numpy(u0).cuda()
+        u, ck = plan.smooth_checkpointed(ft, u0=u0t)
+        plain = plan.smooth(ft, u0=u0t)
+        torch.cuda.synchronize()
+        assert torch.equal(u, plain)   # checkpointing does not change the forward
+        out = plan.backward(ck, torch.from_numpy(w).cuda(), separate_u0=separate)
+        torch.cuda.synchronize()
+        if separate:
+            return out[0].cpu().numpy(), out[1].cpu().numpy()
+        return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,C,lam,p,N", [
+    (32, 40, 1, 1.0, 0.8, 4), (45, 64, 2, 2.0, 1.0, 3), (64, 64, 1, 0.5, 0.5, 2), (30, 48, 3, 1.0, 0.8, 1),
+    (256, 256, 1, 1.0, 0.8, 4), (75, 30, 1, 3.5, 0.8, 4),
+])
+def test_adjoint_matches_fp64_reverse_mode(ils, H, W, C, lam, p, N):
+    f = synth.preset_image(H, W, C, "small", H + W + C)
+    w = synth.random_field(f.shape, seed=7)
+    g = gpu_grad(ils, f, w, lam, p, N)
+    for ch in range(C):
+        want = O.ils_backward(f[ch].astype(np.float64), w[ch].astype(np.float64), lam, p, 1e-4, N)
+        assert rel_err(g[ch], want) <= REL_TOL
+
+
+def test_adjoint_against_finite_differences_of_the_fp64_forward(ils):
+    # <dL/df, v> against central differences of the FP64 forward.  h = 1e-5: with
+    # sqrt(eps) = 0.01 the curvature scale, h = 1e-3 leaves O(1e-2) truncation error.
+    H, W = 48, 64
+    f = synth.preset_image(H, W, 1, "small", 3)
+    w = synth.random_field(f.shape, seed=8)
+    g = gpu_grad(ils, f, w)[0].astype(np.float64)
+    f64, w64 = f[0].astype(np.float64), w[0].astype(np.float64)
+    rng = np.random.default_rng(2)
+    for trial in range(3):
+        v = rng.normal(size=(H, W))
+        h = 1e-5
+        fd = (np.sum(w64 * O.ils_channel(f64 + h * v, 1.0, 0.8, 1e-4, 4)) -
+              np.sum(w64 * O.ils_channel(f64 - h * v, 1.0, 0.8, 1e-4, 4))) / (2 * h)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-4)
+    # the h = 1e-3 difference named for this check agrees only to its truncation error
+    v = rng.normal(size=(H, W))
+    h = 1e-3
+    fd3 = (np.sum(w64 * O.ils_channel(f64 + h * v, 1.0, 0.8, 1e-4, 4)) -
+           np.sum(w64 * O.ils_channel(f64 - h * v, 1.0, 0.8, 1e-4, 4))) / (2 * h)
+    assert np.sum(g * v) == pytest.approx(fd3, rel=0.15)
+
+
+def test_adjoint_warm_start_split(ils):
+    H, W = 40, 48
+    f = synth.preset_image(H, W, 1, "small", 11)
+    u0 = synth.random_field(f.shape, seed=12, lo=0.0, hi=1.0)
+    w = synth.random_field(f.shape, seed=13)
+    gf, gu0 = gpu_grad(ils, f, w, u0=u0, separate=True)
+    want_f, want_u0 = O.ils_backward(f[0].astype(np.float64), w[0].astype(np.float64), 1.0, 0.8, 1e-4, 4,
+                                     u0=u0[0].astype(np.float64), split=True)
+    assert rel_err(gf[0], want_f) <= REL_TOL
+    assert rel_err(gu0[0], want_u0) <= REL_TOL
+
+
+def test_adjoint_n0_and_lambda0(ils):
+    f = synth.preset_image(16, 24, 1, "small", 1)
+    w = synth.random_field(f.shape, seed=2)
+    np.testing.assert_array_equal(gpu_grad(ils, f, w, N=0), w)      # u = f
+    g = gpu_grad(ils, f, w, lam=0.0)                                   # u = f for every N
+    assert np.abs(g - w).max() < 1e-5
+
+
+def test_autograd_function(ils):
+    import torch
+    H, W = 36, 60
+    f = synth.preset_image(H, W, 2, "small", 21)
+    w = synth.random_field(f.shape, seed=22)
+    with ils.Plan(H, W, 2) as plan:
+        ft = torch.from_numpy(f).cuda().requires_grad_(True)
+        u = ils.ils_function(ft, plan)
+        loss = (u * torch.from_numpy(w).cuda()).sum()
+        loss.backward()
+        g = ft.grad.cpu().numpy()
+    for ch in range(2):
+        want = O.ils_backward(f[ch].astype(np.float64), w[ch].astype(np.float64), 1.0, 0.8, 1e-4, 4)
+        assert rel_err(g[ch], want) <= REL_TOL
+
+
+def test_adjoint_batch_of_512_images_against_fp64_samples(ils):
+    # 16 gray 512 x 512 images as one 16-channel plan; two channels checked against the
+    # FP64 reverse mode element by element, the rest by channel independence.
+    import torch
+    C, H, W = 16, 512, 512
+    f = synth.preset_image(H, W, C, "small", 512)
+    w = synth.random_field(f.shape, seed=513)
+    g = gpu_grad(ils, f, w)
+    for ch in (0, 11):
+        want = O.ils_backward(f[ch].astype(np.float64), w[ch].astype(np.float64), 1.0, 0.8, 1e-4, 4)
+        assert rel_err(g[ch], want) <= REL_TOL
+    np.testing.assert_array_equal(gpu_grad(ils, f[5:6].copy(), w[5:6].copy()), g[5:6])

@@ -320,3 +320,17 @@ def test_golden_regression_vector():
     f = np.array([float(v) for v in rows[0].split()]).reshape(12, 10)
     u = np.array([float(v) for v in rows[1].split()]).reshape(12, 10)
     np.testing.assert_allclose(O.ils_channel(f, 1.0, 0.8, 1e-4, 4), u, atol=1e-12)
+
+
+def test_adjoint_split_for_a_warm_start():
+    # dL/df through Eq. 9 and dL/du^0 separately, each against finite differences of the forward.
+    H, W, lam, p, eps, N = 6, 7, 1.0, 0.8, 1e-4, 3
+    f = small_image(H, W, seed=31)
+    u0 = np.random.default_rng(3).uniform(size=(H, W))
+    w = np.random.default_rng(4).normal(size=(H, W))
+    gf, gu0 = O.ils_backward(f, w, lam, p, eps, N, u0=u0, split=True)
+    v = np.random.default_rng(5).normal(size=(H, W))
+    h = 1e-6
+    L = lambda ff, uu: np.sum(w * O.ils_channel(ff, lam, p, eps, N, u0=uu))
+    assert np.sum(gf * v) == pytest.approx((L(f + h * v, u0) - L(f - h * v, u0)) / (2 * h), rel=1e-6, abs=1e-7)
+    assert np.sum(gu0 * v) == pytest.approx((L(f, u0 + h * v) - L(f, u0 - h * v)) / (2 * h), rel=1e-6, abs=1e-7)
