@@ -159,6 +159,73 @@ def run_reference(args):
     return 0
 
 
+def adjoint_leg(ils, torch, dev, steps):
+    """Backward of N=4 ILS w.r.t. f for 16 gray 512 x 512 images (one 16-channel plan):
+    forward with checkpoints, then the hand-written adjoint; CUDA events on the stream."""
+    from paper_2003_07504_gb300 import synth
+    Ca, Ha, Wa = 16, 512, 512
+    f = torch.from_numpy(synth.preset_image(Ha, Wa, Ca, "small", 512)).to(dev)
+    gu = torch.from_numpy(synth.random_field((Ca, Ha, Wa), seed=513)).to(dev)
+    stream = torch.cuda.current_stream()
+    with ils.Plan(Ha, Wa, Ca, LAM, P, EPS, N_ITERS) as plan:
+        for _ in range(3):
+            u, ck = plan.smooth_checkpointed(f)
+            plan.backward(ck, gu)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = bwd = 0.0
+        for _ in range(steps):
+            ev[0].record(stream)
+            u, ck = plan.smooth_checkpointed(f)
+            ev[1].record(stream)
+            plan.backward(ck, gu)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+    return {"workload": "16 x 512x512 gray FP32, N=4: forward with checkpoints + ils_backward",
+            "forward_ckpt_ms": fwd / steps, "backward_ms": bwd / steps,
+            "images_per_s_fwd_bwd": Ca / ((fwd + bwd) / steps / 1000.0)}
+
+
+BATCH_SIZES = ((480, 640), (720, 1280), (1080, 1920), (1536, 2048))
+
+
+def batch_leg(ils, torch, dev, steps, flush):
+    """64 RGB frames, sizes drawn uniformly from BATCH_SIZES, per-frame lambda ~ U(0.5, 2),
+    p in {0.8, 1.0}, N = 4, autotuned kernels, one CUDA-graph launch per step."""
+    from paper_2003_07504_gb300 import synth
+    rng = np.random.default_rng(4000)
+    frames, px = [], 0
+    for k in range(64):
+        hh, ww = BATCH_SIZES[rng.integers(len(BATCH_SIZES))]
+        lam = float(rng.uniform(0.5, 2.0))
+        p = float(rng.choice([0.8, 1.0]))
+        f = torch.from_numpy(synth.preset_image(hh, ww, 3, "hd", 4000 + k)).to(dev)
+        frames.append((f, torch.empty_like(f), lam, p, EPS, N_ITERS))
+        px += hh * ww
+    stream = torch.cuda.current_stream()
+    with ils.Batch(frames, autotune=True) as b:
+        for _ in range(3):
+            b.run()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            b.run()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            tot += s0.elapsed_time(s1)
+    ms = tot / steps
+    nbytes = sum(bytes_model(f.shape[1], f.shape[2], 3, N_ITERS)[1] for f, *_ in frames)
+    peak, _ = load_peaks()
+    return {"workload": "64 RGB FP32 frames, sizes uniform over 640x480 / 1280x720 / 1920x1080 / 2048x1536, "
+                        "lambda~U(0.5,2), p in {0.8,1}, N=4, one graph launch",
+            "ms_per_batch": ms, "frames_per_s": 64 / (ms / 1000.0), "mpix_per_s": px / (ms / 1000.0) / 1e6,
+            "algorithmic_gbs": nbytes / (ms / 1000.0) / 1e9, "frac_of_hbm_peak": nbytes / (ms / 1000.0) / 1e9 / peak}
+
+
 def cpu_baseline_sample(budget_s: float = 20.0):
     """The oracle on one channel of the frame (bounded: 1 channel, N=4), scaled to fps."""
     import oracle as O
@@ -277,6 +344,9 @@ def run_ours(args):
             "gpu_launches": sum(v[1] for v in prof.values()),
             "clocks": clocks,
         }
+        if not args.no_extras:
+            line["adjoint"] = adjoint_leg(ils, torch, dev, max(3, min(args.steps, 20)))
+            line["batch"] = batch_leg(ils, torch, dev, max(3, min(args.steps, 10)), flush)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
@@ -299,6 +369,7 @@ def main():
     ap.add_argument("--height", type=int, default=H)
     ap.add_argument("--width", type=int, default=W)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint / batch / warm-start legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

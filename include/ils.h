@@ -127,6 +127,53 @@ ils_status ils_backward(ils_plan* plan, const float* ckpt, const float* grad_u, 
                         void* stream);
 
 /*
+ * Batches of frames of uneven size (not in the paper: a serving-side extension).
+ * Each frame carries its own size, parameters and buffers; channels are independent
+ * as for a plan.  f and u are device pointers; no frame's u may overlap any frame's f
+ * or u, and a frame's f may not overlap its own u.
+ */
+typedef struct {
+  int H, W, C, N;
+  float lambda, p, eps;
+  const float* f;
+  float* u;
+} ils_frame;
+
+typedef struct ils_batch ils_batch; /* opaque */
+
+#define ILS_BATCH_AUTOTUNE 1 /* time the kernel variants per size class at creation */
+
+/*
+ * ils_batch_create - validate the frames, group them into size classes (shared FFT
+ * plans and tables; per-frame Eq. 7 parameters and Eq. 9 denominators), spread them
+ * over parallel branches, allocate the workspaces and capture every pass of every
+ * frame into one CUDA graph.  The frame pointers are baked into the graph: run the
+ * batch only while those buffers are alive, and create a new batch for new buffers.
+ * With ILS_BATCH_AUTOTUNE, each size class times its compile-time tile shapes and the
+ * generic kernels on the current device and keeps the fastest; if the environment
+ * variable ILS_AUTOTUNE_CACHE names a file, choices are read from and appended to it.
+ * ILS_BATCH_BRANCHES (default 8) sets the number of parallel branches.
+ */
+ils_status ils_batch_create(const ils_frame* frames, int count, int flags, ils_batch** out);
+
+/* One graph launch of the whole batch on `stream` (asynchronous). */
+ils_status ils_batch_run(ils_batch* batch, void* stream);
+
+/* Free a batch (synchronizes the device).  NULL is accepted. */
+ils_status ils_batch_destroy(ils_batch* batch);
+
+/*
+ * Introspection for tools and tests: the branch a frame runs on (return value, or -1
+ * for a bad argument) and the kernel variants its class uses (-1 = generic kernels,
+ * otherwise an index into the library's table of compile-time plans).
+ */
+int ils_batch_kernel_choice(const ils_batch* batch, int frame, int* row_variant, int* col_variant);
+
+/* ils_batch_create (no autotuning) + ils_batch_run + ils_batch_destroy; returns after
+ * the batch has finished on `stream`. */
+ils_status ils_smooth_batched(const ils_frame* frames, int count, void* stream);
+
+/*
  * Per-kernel timing, for measurement tools.  Kernel kinds of one ils_smooth call:
  *   ILS_KERNEL_ROW_FIRST   - first fused row pass (reads f or u0; stencil; forward row FFT)
  *   ILS_KERNEL_ROW         - later fused row passes (inverse row FFT of u^n; stencil; forward row FFT)

@@ -54,6 +54,11 @@ SIGNATURES = {
     "ils_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_set_profiling": (c_int, [c_void_p, c_int]),
     "ils_get_profile": (c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_longlong)]),
+    "ils_batch_create": (c_int, [ctypes.c_void_p, c_int, c_int, P(c_void_p)]),
+    "ils_batch_run": (c_int, [c_void_p, c_void_p]),
+    "ils_batch_destroy": (c_int, [c_void_p]),
+    "ils_batch_kernel_choice": (c_int, [c_void_p, c_int, P(c_int), P(c_int)]),
+    "ils_smooth_batched": (c_int, [ctypes.c_void_p, c_int, c_void_p]),
     "ils_smooth_noalloc": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int,
                                    c_void_p, c_void_p, c_void_p]),
 }

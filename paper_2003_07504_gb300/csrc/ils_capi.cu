@@ -155,6 +155,12 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
 
 }  // namespace
 
+namespace ils {
+void record_cuda_error(const char* where, cudaError_t e) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+}
+}  // namespace ils
+
 extern "C" {
 
 const char* ils_status_string(ils_status s) {

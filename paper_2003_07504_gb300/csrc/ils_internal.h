@@ -57,10 +57,13 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream);
 cudaError_t set_kernel_attributes();
+void record_cuda_error(const char* where, cudaError_t e);  // text for ils_last_error()
 
 // Compile-time specialised kernels (ils_kernels_fixed.cu).
 int fixed_row_index(int M);
 int fixed_col_index(int H);
+int fixed_row_variants(int M, int* idx, int max);  // all entries for a length (first = default)
+int fixed_col_variants(int H, int* idx, int max);
 cudaError_t fixed_set_attributes();
 cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
                               const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,

@@ -489,15 +489,27 @@ constexpr ColEntry col_entry() {
   return ColEntry{PL::N, PL::TPS, G, col_fixed_kernel<PL, G, MINB>};
 }
 
+// Several entries may share a length: the first is the default, the others are
+// alternative tile shapes the batch autotuner may pick.
 const RowEntry kRows[] = {
     row_entry<FixedPlan<128, 8, 16>, 8, 8>(),
+    row_entry<FixedPlan<320, 8, 8, 5>, 6, 8>(),
+    row_entry<FixedPlan<640, 8, 8, 10>, 6, 8>(),
     row_entry<FixedPlan<960, 10, 12, 8>, 6, 8>(),
+    row_entry<FixedPlan<1024, 8, 8, 16>, 4, 6>(),
     row_entry<FixedPlan<1920, 16, 12, 10>, 3, 4>(),
+    row_entry<FixedPlan<960, 10, 12, 8>, 2, 4>(),
+    row_entry<FixedPlan<640, 8, 8, 10>, 2, 4>(),
 };
 const ColEntry kCols[] = {
     col_entry<FixedPlan<256, 16, 16>, 16>(),
+    col_entry<FixedPlan<480, 8, 6, 10>, 4, 2>(),
+    col_entry<FixedPlan<720, 8, 9, 10>, 4, 2>(),
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
+    col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),
     col_entry<FixedPlan<2160, 12, 12, 15>, 4>(),
+    col_entry<FixedPlan<1080, 12, 10, 9>, 8>(),
+    col_entry<FixedPlan<720, 8, 9, 10>, 8>(),
 };
 
 }  // namespace
@@ -513,6 +525,19 @@ int fixed_col_index(int H) {
   for (int i = 0; i < (int)(sizeof(kCols) / sizeof(kCols[0])); ++i)
     if (kCols[i].H == H) return i;
   return -1;
+}
+
+int fixed_row_variants(int M, int* idx, int max) {
+  int n = 0;
+  for (int i = 0; i < (int)(sizeof(kRows) / sizeof(kRows[0])) && n < max; ++i)
+    if (kRows[i].M == M) idx[n++] = i;
+  return n;
+}
+int fixed_col_variants(int H, int* idx, int max) {
+  int n = 0;
+  for (int i = 0; i < (int)(sizeof(kCols) / sizeof(kCols[0])) && n < max; ++i)
+    if (kCols[i].H == H) idx[n++] = i;
+  return n;
 }
 
 static size_t row_smem(int rows, int M) { return (size_t)smem_elems(rows * M) * sizeof(float2); }

@@ -135,6 +135,69 @@ class Plan:
         return out_host
 
 
+class Batch:
+    """Frames of uneven size smoothed by one CUDA-graph launch (ils_batch_create / ils_batch_run).
+
+    frames: sequence of (f, u, lam, p, eps, N) with f, u contiguous float32 CUDA tensors of
+    shape (C, H, W) (or (H, W)).  The tensors must stay alive while the batch is used.
+    """
+
+    def __init__(self, frames, autotune: bool = False):
+        arr = (_lib.Frame * len(frames))()
+        self._keep = []
+        for i, (f, u, lam, p, eps, N) in enumerate(frames):
+            shape = (1, *f.shape) if f.dim() == 2 else tuple(f.shape)
+            _check_image(f.view(shape), shape, "f")
+            _check_image(u.view(shape), shape, "u")
+            C, H, W = shape
+            arr[i] = _lib.Frame(H, W, C, int(N), float(lam), float(p), float(eps), f.data_ptr(), u.data_ptr())
+            self._keep.append((f, u))
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().ils_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(frames),
+                                               1 if autotune else 0, ctypes.byref(h)), "ils_batch_create")
+        self._h = h
+        self.count = len(frames)
+
+    def run(self, stream=None) -> None:
+        _lib.check(_lib.lib().ils_batch_run(self._h, _stream_ptr(stream)), "ils_batch_run")
+
+    def choice(self, i: int):
+        """(branch, row kernel variant, column kernel variant) of frame i (-1 = generic kernels)."""
+        r, c = ctypes.c_int(), ctypes.c_int()
+        br = _lib.lib().ils_batch_kernel_choice(self._h, i, ctypes.byref(r), ctypes.byref(c))
+        return br, r.value, c.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().ils_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def smooth_batched(frames, stream=None) -> None:
+    """One-shot batch: create, run, wait, destroy (ils_smooth_batched)."""
+    arr = (_lib.Frame * len(frames))()
+    for i, (f, u, lam, p, eps, N) in enumerate(frames):
+        shape = (1, *f.shape) if f.dim() == 2 else tuple(f.shape)
+        _check_image(f.view(shape), shape, "f")
+        _check_image(u.view(shape), shape, "u")
+        C, H, W = shape
+        arr[i] = _lib.Frame(H, W, C, int(N), float(lam), float(p), float(eps), f.data_ptr(), u.data_ptr())
+    _lib.check(_lib.lib().ils_smooth_batched(ctypes.cast(arr, ctypes.c_void_p), len(frames), _stream_ptr(stream)),
+               "ils_smooth_batched")
+
+
 class ILSFunction(torch.autograd.Function):
     """u = ILS(f) (optionally from a warm start u0) as a differentiable op.
 
