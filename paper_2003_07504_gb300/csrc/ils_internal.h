@@ -24,6 +24,7 @@ struct Geometry {
   int cols;          // complex columns per CTA in the column pass
   int threads_col, ept_col;
   size_t smem_fwd, smem_inv, smem_col;  // dynamic shared memory bytes
+  int warp_row;      // index of a warp-per-row kernel for M = W/2, or -1
   int fixed_row;     // index of a compile-time row plan for M = W/2, or -1 (generic kernels)
   int fixed_col;     // index of a compile-time column plan for H, or -1
 };
@@ -71,5 +72,14 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
                               cudaStream_t stream);
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream);
+
+// Warp-per-row kernels (ils_rows_warp.cu).
+int warp_row_variants(int M, int* idx, int max);
+cudaError_t warp_set_attributes();
+cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
+                             const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
+                             cudaStream_t stream);
+cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
+                             cudaStream_t stream);
 
 }  // namespace ils

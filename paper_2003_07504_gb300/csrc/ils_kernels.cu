@@ -403,9 +403,16 @@ bool pick_geometry(int H, int W, Geometry* g) {
   g->smem_col = (size_t)smem_elems(H * G) * sizeof(float2);
   // Compile-time plans where one exists; ILS_FORCE_GENERIC=1 keeps the generic kernels
   // (used by the tests to cover both implementations on the same sizes).
+  // ILS_ROW_IMPL=fixed|generic selects the block-per-strip or generic row kernels instead
+  // of the warp-per-row ones (tests compare the implementations on the same sizes).
   const char* force = getenv("ILS_FORCE_GENERIC");
   const bool generic = force != nullptr && force[0] == '1';
-  g->fixed_row = generic ? -1 : fixed_row_index(M);
+  const char* impl = getenv("ILS_ROW_IMPL");
+  const bool no_warp = generic || (impl != nullptr && (impl[0] == 'f' || impl[0] == 'g'));
+  const bool no_fixed = generic || (impl != nullptr && impl[0] == 'g');
+  int wv[4];
+  g->warp_row = (!no_warp && warp_row_variants(M, wv, 4) > 0) ? wv[0] : -1;
+  g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
   g->fixed_col = generic ? -1 : fixed_col_index(H);
   return true;
 }
@@ -427,12 +434,14 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(row_inverse_kernel<32>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<32>))) return e;
+  if ((e = warp_set_attributes())) return e;
   return fixed_set_attributes();
 }
 
 cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
                                const float* f, const float* u0, const float2* spec_in, float2* spec_out,
                                float* u_ckpt, cudaStream_t stream) {
+  if (g.warp_row >= 0) return warp_row_forward(g.warp_row, d, t, mp, f, u0, spec_in, spec_out, u_ckpt, stream);
   if (g.fixed_row >= 0) return fixed_row_forward(g.fixed_row, d, t, mp, f, u0, spec_in, spec_out, u_ckpt, stream);
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   const int T = g.threads_row;
@@ -472,6 +481,7 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
 
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
                                float* u, cudaStream_t stream) {
+  if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream);
   if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
   if (g.ept_inv == 16)

@@ -1,0 +1,298 @@
+// Row passes with one warp per image row, for row lengths W = 64 L (M = W/2 = 32 L complex).
+//
+// A warp transforms one packed complex row of M = 32 L points as a 32 x L four-step FFT:
+// lane n1 holds x[n1 + 32 n2] (n2 = 0..L-1, a coalesced row load), runs the L-point DFT
+// over its registers (ils_dft.cuh), multiplies by w_M^{n1 k2}, and the warp transposes
+// through its own shared-memory row buffer (stride 33, conflict free) so that lane k2 < L
+// holds the 32 values of index k2 and runs the 32-point DFT: X[k2 + L k1] lands in
+// register k1 of lane k2.  The only barriers inside a transform are __syncwarp.
+//
+// The fused row pass of iteration n (see ils_kernels.cu for the passes and the packed
+// spectrum layout) then needs two CTA barriers per strip: after the inverse transforms of
+// the ROWS + 2 rows (the stencil reads neighbouring rows) and after the stencil (a row's
+// buffer is reused by its forward transform).
+#include <cuda_runtime.h>
+
+#include "ils_dft.cuh"
+#include "ils_internal.h"
+
+namespace ils {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (y >= H ? y - H : y); }
+
+// Eq. 7: mu = c g - p g (g^2 + eps)^(p/2 - 1)
+__device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
+  const float t = fmaf(g, g, mp.eps);
+  const float w = exp2f(mp.a * __log2f(t));
+  return g * fmaf(-mp.p, w, mp.c);
+}
+
+template <int L>
+struct WarpRow {
+  static constexpr int M = 32 * L;
+  static constexpr int STRIDE = 33;                       // complex per transposed line
+  static constexpr int BUF = (L * STRIDE > M ? L * STRIDE : M);  // complex per row buffer
+
+  // v: lane holds x[lane + 32 n2]; out (lanes < L): X[lane + L k1].  buf: this warp's buffer.
+  // twW[t] = exp(-2 pi i t / (2M)).
+  template <bool INV>
+  __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[32], float2* buf, int lane,
+                                             const float2* __restrict__ twW) {
+    dft_reg<L, INV>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < L; ++k2) {
+      float2 w = __ldg(&twW[2 * lane * k2]);
+      if (INV) w.y = -w.y;
+      v[k2] = cmul(v[k2], w);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < L; ++k2) buf[k2 * STRIDE + lane] = v[k2];
+    __syncwarp();
+    if (lane < L) {
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) out[n1] = buf[lane * STRIDE + n1];
+      dft_reg<32, INV>(out);
+    }
+    __syncwarp();
+  }
+
+  // Inverse real transform of the packed half spectrum X (global row) into buf in natural
+  // order: buf[m] = (x[2m], x[2m+1]) * (the unnormalized factor 2M; the column pass divides).
+  __device__ __forceinline__ static void inverse_row_to_buf(const float2* __restrict__ X, float2* buf, int lane,
+                                                            const float2* __restrict__ twW) {
+    float2 v[L];
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int k = lane + 32 * n2;
+      if (k == 0) {
+        const float2 x = X[0];
+        v[n2] = c2(x.x + x.y, x.x - x.y);
+      } else {
+        // Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/(2M)} (X[k] - conj X[M-k])
+        const float2 a = X[k], b = cconj(X[M - k]);
+        const float2 s = cadd(a, b), d = csub(a, b);
+        const float2 t = cmul(cconj(__ldg(&twW[k])), d);
+        v[n2] = c2(s.x - t.y, s.y + t.x);
+      }
+    }
+    float2 out[32];
+    fft<true>(v, out, buf, lane, twW);
+    if (lane < L) {
+#pragma unroll
+      for (int k1 = 0; k1 < 32; ++k1) buf[lane + L * k1] = out[k1];
+    }
+    __syncwarp();
+  }
+
+  // Inverse real transform of X straight to a global row of u.
+  __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* dst, float2* buf,
+                                                               int lane, const float2* __restrict__ twW) {
+    float2 v[L];
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int k = lane + 32 * n2;
+      if (k == 0) {
+        const float2 x = X[0];
+        v[n2] = c2(x.x + x.y, x.x - x.y);
+      } else {
+        const float2 a = X[k], b = cconj(X[M - k]);
+        const float2 s = cadd(a, b), d = csub(a, b);
+        const float2 t = cmul(cconj(__ldg(&twW[k])), d);
+        v[n2] = c2(s.x - t.y, s.y + t.x);
+      }
+    }
+    float2 out[32];
+    fft<true>(v, out, buf, lane, twW);
+    if (lane < L) {
+#pragma unroll
+      for (int k1 = 0; k1 < 32; ++k1) dst[lane + L * k1] = out[k1];
+    }
+  }
+
+  // Forward real transform of r (lane holds r-pairs at m = lane + 32 n2) to the packed
+  // half spectrum in the global row dst (slot 0 = (X[0], X[M])).
+  __device__ __forceinline__ static void forward_row_to_global(float2 (&v)[L], float2* dst, float2* buf, int lane,
+                                                               const float2* __restrict__ twW) {
+    float2 out[32];
+    fft<false>(v, out, buf, lane, twW);
+    if (lane < L) {
+#pragma unroll
+      for (int k1 = 0; k1 < 32; ++k1) buf[lane + L * k1] = out[k1];
+    }
+    __syncwarp();
+    // pairs (k, M-k), k = 0..M/2
+#pragma unroll
+    for (int q = 0; q < (M / 2 + 1 + 31) / 32; ++q) {
+      const int k = lane + 32 * q;
+      if (k > M / 2) continue;
+      if (k == 0) {
+        const float2 z = buf[0];
+        dst[0] = c2(z.x + z.y, z.x - z.y);
+      } else {
+        const float2 a = buf[k], b = buf[M - k];
+        const float2 fa = cscale(cadd(a, cconj(b)), 0.5f), fo = cscale(csub(a, cconj(b)), 0.5f);
+        dst[k] = cadd(fa, cmul(__ldg(&twW[k]), c2(fo.y, -fo.x)));
+        if (M - k != k) {
+          const float2 fb = cscale(cadd(b, cconj(a)), 0.5f), fq = cscale(csub(b, cconj(a)), 0.5f);
+          dst[M - k] = cadd(fb, cmul(__ldg(&twW[M - k]), c2(fq.y, -fq.x)));
+        }
+      }
+    }
+    __syncwarp();
+  }
+};
+
+// Fused row pass: CTA = ROWS + 2 warps over rows y0-1 .. y0+ROWS (periodic); warp w holds
+// strip row w in buffer w.  FIRST: u^0 rows are read from u0 (or f); otherwise rebuilt by the
+// inverse transform of spec_in.  Then warp o+1 computes r for output row o and transforms it.
+template <int L, int ROWS, bool FIRST>
+__global__ void __launch_bounds__((ROWS + 2) * 32, (ROWS + 2) * 32 <= 256 ? 2 : 1)
+row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
+                    const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
+                    float* __restrict__ u_ckpt) {
+  using WR = WarpRow<L>;
+  constexpr int M = WR::M;
+  extern __shared__ float2 sm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int strips = (H + ROWS - 1) / ROWS;
+  const int ch = blockIdx.x / strips;
+  const int y0 = (blockIdx.x - ch * strips) * ROWS;
+  const int nout = min(ROWS, H - y0);
+  const size_t plane = (size_t)H * M;
+  float2* buf = sm + w * WR::BUF;
+  auto U = [&](int row, int m) -> float2 { return sm[row * WR::BUF + m]; };
+  if (w < nout + 2) {
+    const int yy = wrap_row(y0 - 1 + w, H);
+    if (FIRST) {
+      const float2* src = reinterpret_cast<const float2*>(u0 != nullptr ? u0 : f) + ch * plane + (size_t)yy * M;
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) buf[lane + 32 * n2] = src[lane + 32 * n2];
+    } else {
+      WR::inverse_row_to_buf(spec_in + ch * plane + (size_t)yy * M, buf, lane, twW);
+    }
+  }
+  __syncthreads();
+  const int o = w - 1;  // output row of this warp
+  const bool out_live = o >= 0 && o < nout;
+  float2 v[L];
+  if (out_live) {
+    const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
+    const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
+    if (mp.half_lambda == 0.0f) {  // lambda = 0 (or a plain row FFT): r = f
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) {
+        const int m = lane + 32 * n2;
+        v[n2] = fr[m];
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = U(w, m);
+      }
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) {
+        const int m = lane + 32 * n2;
+        const float2 c = U(w, m);
+        const float ul = U(w, m == 0 ? M - 1 : m - 1).y;
+        const float ur = U(w, m == M - 1 ? 0 : m + 1).x;
+        const float2 up = U(w - 1, m);
+        const float2 dn = U(w + 1, m);
+        const float2 fv = fr[m];
+        const float mx_l = mu_eq7(c.x - ul, mp);
+        const float mx_c = mu_eq7(c.y - c.x, mp);
+        const float mx_r = mu_eq7(ur - c.y, mp);
+        const float my0u = mu_eq7(c.x - up.x, mp);
+        const float my0d = mu_eq7(dn.x - c.x, mp);
+        const float my1u = mu_eq7(c.y - up.y, mp);
+        const float my1d = mu_eq7(dn.y - c.y, mp);
+        v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x),
+                   fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
+      }
+    }
+  }
+  __syncthreads();
+  if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+}
+
+// Final inverse row pass: one warp per row, ROWS rows per CTA.
+template <int L, int ROWS>
+__global__ void __launch_bounds__(ROWS * 32)
+row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u) {
+  using WR = WarpRow<L>;
+  constexpr int M = WR::M;
+  extern __shared__ float2 sm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int strips = (H + ROWS - 1) / ROWS;
+  const int ch = blockIdx.x / strips;
+  const int y = (blockIdx.x - ch * strips) * ROWS + w;
+  if (y >= H) return;  // warp-uniform; no CTA barrier below
+  const size_t off = ch * (size_t)H * M + (size_t)y * M;
+  WR::inverse_row_to_global(spec + off, reinterpret_cast<float2*>(u) + off, sm + w * WR::BUF, lane, twW);
+}
+
+using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
+using InvFn = void (*)(int, const float2*, const float2*, float*);
+
+struct WarpRowEntry {
+  int M, rows_fwd, rows_inv, buf;
+  FwdFn first, later;
+  InvFn inv;
+};
+
+template <int L, int RF, int RI>
+constexpr WarpRowEntry warp_entry() {
+  return WarpRowEntry{32 * L, RF, RI, WarpRow<L>::BUF, row_warp_fwd_kernel<L, RF, true>,
+                      row_warp_fwd_kernel<L, RF, false>, row_warp_inv_kernel<L, RI>};
+}
+
+const WarpRowEntry kWarpRows[] = {
+    warp_entry<4, 14, 16>(),   // W = 256
+    warp_entry<10, 14, 16>(),  // W = 640
+    warp_entry<20, 6, 8>(),    // W = 1280
+    warp_entry<30, 6, 8>(),    // W = 1920
+    warp_entry<32, 6, 8>(),    // W = 2048
+    warp_entry<30, 14, 8>(),   // W = 1920, taller strips (autotune alternative)
+};
+
+}  // namespace
+
+int warp_row_variants(int M, int* idx, int max) {
+  int n = 0;
+  for (int i = 0; i < (int)(sizeof(kWarpRows) / sizeof(kWarpRows[0])) && n < max; ++i)
+    if (kWarpRows[i].M == M) idx[n++] = i;
+  return n;
+}
+
+cudaError_t warp_set_attributes() {
+  cudaError_t e;
+  for (const WarpRowEntry& r : kWarpRows) {
+    const int sf = (r.rows_fwd + 2) * r.buf * (int)sizeof(float2), si = r.rows_inv * r.buf * (int)sizeof(float2);
+    if ((e = cudaFuncSetAttribute(r.first, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    if ((e = cudaFuncSetAttribute(r.later, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
+                             const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
+                             cudaStream_t stream) {
+  const WarpRowEntry& r = kWarpRows[idx];
+  const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
+  const size_t smem = (size_t)(r.rows_fwd + 2) * r.buf * sizeof(float2);
+  FwdFn fn = spec_in == nullptr ? r.first : r.later;
+  fn<<<blocks, (r.rows_fwd + 2) * 32, smem, stream>>>(d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
+  return cudaGetLastError();
+}
+
+cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
+                             cudaStream_t stream) {
+  const WarpRowEntry& r = kWarpRows[idx];
+  const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
+  const size_t smem = (size_t)r.rows_inv * r.buf * sizeof(float2);
+  r.inv<<<blocks, r.rows_inv * 32, smem, stream>>>(d.H, t.twW, spec, u);
+  return cudaGetLastError();
+}
+
+}  // namespace ils

@@ -215,3 +215,18 @@ def test_generic_and_fixed_kernels_agree(ils, monkeypatch, H, W, C):
     assert_parity(fixed, generic)
     if H * W <= 256 * 256:
         assert_parity(fixed, O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
+
+
+@pytest.mark.parametrize("H,W,C", [(256, 256, 1), (1080, 1920, 1), (48, 640, 3), (40, 1280, 2), (30, 2048, 1)])
+def test_row_implementations_agree(ils, monkeypatch, H, W, C):
+    # warp-per-row kernels (default where W = 64 L) against the block-per-strip fixed kernels
+    f = image(H, W, C, seed=H * 3 + W, preset="hd")
+    warp = run_gpu(ils, f)
+    monkeypatch.setenv("ILS_ROW_IMPL", "fixed")
+    fixed = run_gpu(ils, f)
+    monkeypatch.setenv("ILS_ROW_IMPL", "generic")
+    generic = run_gpu(ils, f)
+    assert_parity(warp, fixed)
+    assert_parity(warp, generic)
+    if H * W <= 256 * 256:
+        assert_parity(warp, O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
