@@ -153,6 +153,13 @@ template <> struct Split<25> { static constexpr int A = 5, B = 5; };
 template <> struct Split<27> { static constexpr int A = 3, B = 9; };
 template <> struct Split<30> { static constexpr int A = 2, B = 15; };
 template <> struct Split<32> { static constexpr int A = 4, B = 8; };
+template <> struct Split<36> { static constexpr int A = 4, B = 9; };
+template <> struct Split<40> { static constexpr int A = 8, B = 5; };
+template <> struct Split<45> { static constexpr int A = 5, B = 9; };
+template <> struct Split<48> { static constexpr int A = 16, B = 3; };
+template <> struct Split<54> { static constexpr int A = 6, B = 9; };
+template <> struct Split<60> { static constexpr int A = 4, B = 15; };
+template <> struct Split<64> { static constexpr int A = 8, B = 8; };
 
 template <int R, bool INV>
 ILS_HD void dft_reg(float2* v);

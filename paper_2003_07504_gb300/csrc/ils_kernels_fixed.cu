@@ -503,13 +503,18 @@ const RowEntry kRows[] = {
 };
 const ColEntry kCols[] = {
     col_entry<FixedPlan<256, 16, 16>, 16>(),
-    col_entry<FixedPlan<480, 8, 6, 10>, 4, 2>(),
-    col_entry<FixedPlan<720, 8, 9, 10>, 4, 2>(),
-    col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
-    col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),
+    col_entry<FixedPlan<480, 20, 24>, 4, 4>(),
+    col_entry<FixedPlan<720, 24, 30>, 4, 3>(),
+    col_entry<FixedPlan<1080, 36, 30>, 4, 3>(),
+    col_entry<FixedPlan<1536, 32, 48>, 4, 2>(),
     col_entry<FixedPlan<2160, 12, 12, 15>, 4>(),
-    col_entry<FixedPlan<1080, 12, 10, 9>, 8>(),
-    col_entry<FixedPlan<720, 8, 9, 10>, 8>(),
+    // alternatives for the autotuner
+    col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
+    col_entry<FixedPlan<1080, 30, 36>, 8>(),
+    col_entry<FixedPlan<720, 8, 9, 10>, 4, 2>(),
+    col_entry<FixedPlan<480, 8, 6, 10>, 4, 2>(),
+    col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),
+    col_entry<FixedPlan<2160, 45, 48>, 4, 2>(),
 };
 
 }  // namespace

@@ -230,3 +230,20 @@ def test_row_implementations_agree(ils, monkeypatch, H, W, C):
     assert_parity(warp, generic)
     if H * W <= 256 * 256:
         assert_parity(warp, O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
+
+
+@pytest.mark.parametrize("H,W", [(1080, 64), (720, 64), (480, 64), (1536, 32), (2160, 16)])
+def test_column_plan_variants_agree(ils, H, W):
+    # every compile-time column plan for H (the batch autotuner's candidates) against the oracle
+    import ctypes
+    import torch
+    from paper_2003_07504_gb300 import _lib
+    f = image(H, W, 1, seed=H + 7, preset="hd")
+    want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
+    L = _lib.lib()
+    ft = torch.from_numpy(f).cuda()
+    frames = [(ft, torch.empty_like(ft), 1.0, 0.8, 1e-4, 4)]
+    with ils.Batch(frames, autotune=True) as b:   # exercises the timing of every candidate
+        b.run()
+        torch.cuda.synchronize()
+        assert_parity(frames[0][1].cpu().numpy(), want)
