@@ -174,6 +174,57 @@ int ils_batch_kernel_choice(const ils_batch* batch, int frame, int* row_variant,
 ils_status ils_smooth_batched(const ils_frame* frames, int count, void* stream);
 
 /*
+ * Warm-start network (not in the paper): u^0 = f + net(f), net = six 3x3 convolutions
+ * 3 -> 32 -> 32 -> 32 -> 32 -> 32 -> 3, ReLU between them, zero padding, BF16 weights
+ * and activations with FP32 accumulation on the tensor cores.  Images are batches of
+ * B RGB frames: device B x 3 x H x W FP32 planar (the layout of a 3B-channel plan).
+ * Parameters, in ils_cnn_set_weights / ils_cnn_get_weights / ils_cnn_get_grads order:
+ * for each layer, W[co][ci][ky][kx] then b[co], FP32 host arrays of
+ * ils_cnn_param_count() values.
+ */
+typedef struct ils_cnn ils_cnn; /* opaque: FP32 master weights, BF16 copies, Adam state, activations */
+
+long long ils_cnn_param_count(void);
+
+/* Allocate a network whose forward/backward accept batches of up to max_pixels = B*H*W. */
+ils_status ils_cnn_create(long long max_pixels, ils_cnn** out);
+ils_status ils_cnn_destroy(ils_cnn* net);                        /* NULL accepted; synchronizes */
+ils_status ils_cnn_set_weights(ils_cnn* net, const float* params, long long count);  /* also resets Adam */
+ils_status ils_cnn_get_weights(const ils_cnn* net, float* params, long long count);
+ils_status ils_cnn_get_grads(const ils_cnn* net, float* grads, long long count);
+
+/* u0 = f + net(f) (f, u0 device, non-overlapping).  Keeps the activations for backward. */
+ils_status ils_cnn_forward(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);
+
+/* Accumulate dL/dparams given dL/du0 (device, B x 3 x H x W), using the activations of
+ * the last forward call, which must have been on the same f and shape. */
+ils_status ils_cnn_backward(ils_cnn* net, int B, int H, int W, const float* f, const float* grad_u0, void* stream);
+ils_status ils_cnn_zero_grad(ils_cnn* net, void* stream);
+
+/* One Adam step on the FP32 master weights (bias-corrected; the step count is kept in
+ * the network), then refresh the BF16 copies. */
+ils_status ils_cnn_adam_step(ils_cnn* net, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* grad = 2 (u0 - target) / n and *loss += mean((u0 - target)^2); all device pointers,
+ * *loss is FP32 and accumulated (zero it first). */
+ils_status ils_mse(const float* u0, const float* target, float* grad, long long n, float* loss, void* stream);
+
+/*
+ * Warm-started smoothing: u = ILS_iters(f; u^0 = f + net(f)) (Algorithm 1 from u^0),
+ * and plain ILS (n_plain iterations from f) instead when the last iterate change
+ * max |u^iters - u^{iters-1}| exceeds tau.  C must be a multiple of 3 (RGB frames).
+ * The network is borrowed and must outlive the object.
+ */
+typedef struct ils_warm ils_warm;
+ils_status ils_warm_create(int H, int W, int C, float lambda, float p, float eps, int iters, int n_plain, float tau,
+                           ils_cnn* net, ils_warm** out);
+ils_status ils_warm_destroy(ils_warm* warm);
+/* f, u: device C x H x W.  Waits on `stream` for the iterate change (a 4-byte read).
+ * *fallback_taken and *delta (either may be NULL) report the decision and the change. */
+ils_status ils_warm_smooth(ils_warm* warm, const float* f, float* u, int* fallback_taken, float* delta,
+                           void* stream);
+
+/*
  * Per-kernel timing, for measurement tools.  Kernel kinds of one ils_smooth call:
  *   ILS_KERNEL_ROW_FIRST   - first fused row pass (reads f or u0; stencil; forward row FFT)
  *   ILS_KERNEL_ROW         - later fused row passes (inverse row FFT of u^n; stencil; forward row FFT)

@@ -45,7 +45,8 @@ __all__ = [
     "grad_x", "grad_y", "grad_x_T", "grad_y_T",
     "dft_matrix", "dft2", "idft2", "gradient_transfer_functions", "denominator",
     "solve_eq9", "ils_iteration", "ils_smooth", "ils_channel", "energy", "ils_backward",
-    "conv3x3", "warmstart_cnn_forward",
+    "conv3x3", "warmstart_cnn_forward", "bf16_round", "warmstart_forward_bf16", "warmstart_backward_bf16",
+    "adam_step",
 ]
 
 
@@ -303,3 +304,81 @@ def warmstart_cnn_forward(f, weights, biases):
         if i < L - 1:
             h = np.maximum(h, 0.0)
     return x + h
+
+
+# ----------------------------------------------------------------------------
+# The warm-start network with the rounding points of a BF16 implementation.
+#
+# The tensor-core kernels hold weights, the network input and every hidden activation
+# (and every hidden gradient) in BF16 and accumulate in FP32.  Where a value is stored
+# as BF16 the oracle rounds it the same way (round to nearest even on the top 16 bits
+# of the IEEE binary32 value); everything else is float64.
+# ----------------------------------------------------------------------------
+
+def bf16_round(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    a = np.asarray(x, dtype=np.float64).astype(np.float32)
+    bits = a.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _conv_fwd_bwd(x, w, g=None):
+    """y = conv3x3(x, w) (zero padding, no bias), and with g = dL/dy also (dL/dx, dL/dw): float64 autograd."""
+    import torch
+    xt = torch.as_tensor(np.asarray(x, dtype=np.float64)).requires_grad_(g is not None)
+    wt = torch.as_tensor(np.asarray(w, dtype=np.float64)).requires_grad_(g is not None)
+    y = torch.nn.functional.conv2d(xt, wt, padding=1)
+    if g is None:
+        return y.detach().numpy()
+    y.backward(torch.as_tensor(np.asarray(g, dtype=np.float64)))
+    return y.detach().numpy(), xt.grad.numpy(), wt.grad.numpy()
+
+
+def warmstart_forward_bf16(f, weights, biases, rounding=True):
+    """u0 = f + net(f) for a batch f (B x 3 x H x W) with the BF16 rounding points
+    (rounding=False: plain float64, for checking the chain itself).
+
+    Returns (u0, hidden) where hidden[l] is the stored (post-ReLU) output of layer l.
+    """
+    rnd = bf16_round if rounding else (lambda a: np.asarray(a, dtype=np.float64))
+    f = np.asarray(f, dtype=np.float64)
+    h = rnd(f)
+    hidden = []
+    L = len(weights)
+    for l in range(L):
+        y = _conv_fwd_bwd(h, rnd(weights[l])) + np.asarray(biases[l], dtype=np.float64)[None, :, None, None]
+        if l < L - 1:
+            h = rnd(np.maximum(y, 0.0))
+            hidden.append(h)
+        else:
+            return f + y, hidden
+
+
+def warmstart_backward_bf16(f, weights, biases, grad_u0, rounding=True):
+    """dL/dW, dL/db of the network given dL/du0, with the BF16 rounding points of the kernels:
+    each layer's output gradient is rounded to BF16 where it is stored, and the ReLU mask is
+    taken from the stored activation (rounding=False: plain float64 reverse mode)."""
+    rnd = bf16_round if rounding else (lambda a: np.asarray(a, dtype=np.float64))
+    f = np.asarray(f, dtype=np.float64)
+    _, hidden = warmstart_forward_bf16(f, weights, biases, rounding)
+    L = len(weights)
+    inputs = [rnd(f)] + hidden                   # input of layer l
+    g = rnd(grad_u0)                             # gradient at the last layer's output
+    dW, db = [None] * L, [None] * L
+    for l in range(L - 1, -1, -1):
+        _, gx, gw = _conv_fwd_bwd(inputs[l], rnd(weights[l]), g)
+        dW[l] = gw
+        db[l] = g.sum(axis=(0, 2, 3))
+        if l > 0:
+            g = rnd(gx * (inputs[l] > 0))        # ReLU of layer l-1, stored as BF16
+    return dW, db
+
+
+def adam_step(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One bias-corrected Adam update (Kingma and Ba); returns (w, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mhat = m / (1 - b1 ** t)
+    vhat = v / (1 - b2 ** t)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v

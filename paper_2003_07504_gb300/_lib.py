@@ -59,6 +59,21 @@ SIGNATURES = {
     "ils_batch_destroy": (c_int, [c_void_p]),
     "ils_batch_kernel_choice": (c_int, [c_void_p, c_int, P(c_int), P(c_int)]),
     "ils_smooth_batched": (c_int, [ctypes.c_void_p, c_int, c_void_p]),
+    "ils_cnn_param_count": (ctypes.c_longlong, []),
+    "ils_cnn_create": (c_int, [ctypes.c_longlong, P(c_void_p)]),
+    "ils_cnn_destroy": (c_int, [c_void_p]),
+    "ils_cnn_set_weights": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "ils_cnn_get_weights": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "ils_cnn_get_grads": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "ils_cnn_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "ils_cnn_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "ils_cnn_zero_grad": (c_int, [c_void_p, c_void_p]),
+    "ils_cnn_adam_step": (c_int, [c_void_p, c_float, c_float, c_float, c_float, c_void_p]),
+    "ils_mse": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
+    "ils_warm_create": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int, c_int, c_float, c_void_p,
+                                P(c_void_p)]),
+    "ils_warm_destroy": (c_int, [c_void_p]),
+    "ils_warm_smooth": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int), P(c_float), c_void_p]),
     "ils_smooth_noalloc": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int,
                                    c_void_p, c_void_p, c_void_p]),
 }

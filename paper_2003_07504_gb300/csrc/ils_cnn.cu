@@ -1,0 +1,725 @@
+// Warm-start network for ILS (not in the paper): u0 = f + net(f), net = six 3x3
+// convolutions 3->32->32->32->32->32->3 with ReLU between them, BF16 weights and
+// activations, FP32 accumulation, on the tensor cores.
+//
+// Every convolution is an implicit GEMM with M = pixels, N = output channels,
+// K = 9 taps x input channels.  A CTA computes an 8 x 16 pixel tile (8 warps, one
+// 16-pixel row segment each) with mma.sync m16n8k16 BF16 -> FP32.  The input tile
+// (plus a one-pixel halo, zero outside the image) is staged once in shared memory in
+// pixel-major order (80-byte pixel stride, conflict free for ldmatrix); the A fragment
+// of tap (dy, dx) is an ldmatrix whose row addresses are the shifted pixels, so the
+// im2col costs nothing and each input pixel is read from L2 once per layer.  The
+// 3-channel planar inputs (the image, or the gradient of the last layer) are unrolled
+// into 27 (+5 zero) columns per pixel instead.
+//
+// Backward: the input gradient of a convolution is the same kernel run with the weights
+// flipped in space and transposed in channels (kernels dgrad_*); the weight gradient is
+// a GEMM over pixels (dW = sum_p dY(p)^T im2col(X)(p)) computed with the same MMA and
+// reduced into FP32 with atomics.  ReLU masks use the stored post-ReLU activations.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ils.h"
+#include "ils_internal.h"
+
+namespace ils {
+namespace cnn {
+
+constexpr int TH = 8, TW = 16, NTHREADS = 256;
+constexpr int PXS = 40;                       // bf16 per staged pixel (32 + 8 pad: 80 B)
+constexpr int HALO_PX = (TH + 2) * (TW + 2);  // 180
+constexpr int C = 32;                         // hidden channels
+constexpr int KMID = 9 * C;                   // 288
+constexpr int KMID_S = KMID + 8;              // smem row stride of weights (bf16)
+constexpr int KIN = 32;                       // 27 unrolled taps x 3 channels, padded
+constexpr int KIN_S = KIN + 8;
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+// D += A(16x16, row) * B(16x8, col), bf16 in, fp32 accumulate
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+struct ConvArgs {
+  int B, H, W;
+  const float* in_planar;  // 3-channel planar FP32 input (B x 3 x H x W), or null
+  const bf16* in_nhwc;     // 32-channel NHWC BF16 input, or null
+  const bf16* wt;          // [NT*8][K] BF16 weights (K = 288 or 32), rows = output channels
+  const float* bias;       // [cout] or null
+  bf16* out_nhwc;          // 32-channel NHWC BF16 output
+  float* out_planar;       // 3-channel planar FP32 output
+  const float* resid;      // added to the planar output (u0 = f + net(f)), or null
+  const bf16* mask;        // NHWC BF16; output zeroed where mask <= 0 (ReLU backward), or null
+  int relu;                // apply ReLU to the NHWC output
+  int cout;                // real output channels
+};
+
+// Stage the A source of one tile: the halo tile of a 32-channel NHWC input, or the
+// unrolled 3x3x3 neighbourhoods of a 3-channel planar input.
+template <bool PLANAR_IN>
+__device__ __forceinline__ void stage_input(const ConvArgs& a, bf16* sA, int b, int y0, int x0) {
+  const int H = a.H, W = a.W;
+  if (!PLANAR_IN) {
+    // 180 pixels x 4 chunks of 16 bytes
+    const uint4* src = reinterpret_cast<const uint4*>(a.in_nhwc);
+    for (int q = threadIdx.x; q < HALO_PX * 4; q += NTHREADS) {
+      const int px = q >> 2, ch = q & 3;
+      const int hy = px / (TW + 2), hx = px - hy * (TW + 2);
+      const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (y >= 0 && y < H && x >= 0 && x < W) v = src[(((size_t)b * H + y) * W + x) * 4 + ch];
+      *reinterpret_cast<uint4*>(sA + px * PXS + ch * 8) = v;
+    }
+  } else {
+    // 128 pixels x 32 columns: column k = tap * 3 + c (k < 27), zero beyond
+    for (int q = threadIdx.x; q < TH * TW * KIN; q += NTHREADS) {
+      const int px = q >> 5, k = q & 31;
+      const int ty = px / TW, tx = px - ty * TW;
+      float v = 0.0f;
+      if (k < 27) {
+        const int tap = k / 3, c = k - tap * 3;
+        const int y = y0 + ty + tap / 3 - 1, x = x0 + tx + tap % 3 - 1;
+        if (y >= 0 && y < H && x >= 0 && x < W) v = a.in_planar[(((size_t)b * 3 + c) * H + y) * W + x];
+      }
+      sA[px * PXS + k] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// out = conv3x3(in) (+bias) (ReLU | mask) (+resid): NT n-tiles of 8 output channels.
+template <bool PLANAR_IN, int NT, bool PLANAR_OUT>
+__global__ void __launch_bounds__(NTHREADS) conv_fwd_kernel(ConvArgs a) {
+  constexpr int K = PLANAR_IN ? KIN : KMID;
+  constexpr int KS = PLANAR_IN ? KIN_S : KMID_S;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  bf16* sW = reinterpret_cast<bf16*>(smraw);            // [NT*8][KS]
+  bf16* sA = sW + NT * 8 * KS;                          // halo or unrolled tile
+  const int b = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+  // weights: rows of K bf16 (16-byte chunks)
+  for (int q = threadIdx.x; q < NT * 8 * (K / 8); q += NTHREADS) {
+    const int r = q / (K / 8), ch = q - r * (K / 8);
+    *reinterpret_cast<uint4*>(sW + r * KS + ch * 8) = reinterpret_cast<const uint4*>(a.wt)[r * (K / 8) + ch];
+  }
+  stage_input<PLANAR_IN>(a, sA, b, y0, x0);
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+  const int arow = lane & 15, akh = lane >> 4;           // A: row (pixel) and k-half of this lane's address
+  const int brow = lane & 7, bkh = (lane >> 3) & 1;      // B: row (out channel) and k-half
+  if (!PLANAR_IN) {
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+      const bf16* arow_p = sA + ((warp + dy) * (TW + 2) + arow + dx) * PXS + akh * 8;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(arow_p + kk * 16), a0, a1, a2, a3);
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          uint32_t b0, b1;
+          ldsm_x2(smem_u32(sW + (n * 8 + brow) * KS + tap * C + kk * 16 + bkh * 8), b0, b1);
+          mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t a0, a1, a2, a3;
+      ldsm_x4(smem_u32(sA + (warp * TW + arow) * PXS + kk * 16 + akh * 8), a0, a1, a2, a3);
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        uint32_t b0, b1;
+        ldsm_x2(smem_u32(sW + (n * 8 + brow) * KS + kk * 16 + bkh * 8), b0, b1);
+        mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+      }
+    }
+  }
+
+  // epilogue: acc[n][0..1] = pixel g, channels 2t, 2t+1; acc[n][2..3] = pixel g+8
+  const int g = lane >> 2, t = lane & 3;
+  const int y = y0 + warp;
+  if (y >= a.H) return;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int x = x0 + g + 8 * half;
+    if (x >= a.W) continue;
+    const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const int co = n * 8 + 2 * t;
+      float v0 = acc[n][2 * half], v1 = acc[n][2 * half + 1];
+      if (a.bias != nullptr) {
+        if (co < a.cout) v0 += a.bias[co];
+        if (co + 1 < a.cout) v1 += a.bias[co + 1];
+      }
+      if (!PLANAR_OUT) {
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.0f);
+          v1 = fmaxf(v1, 0.0f);
+        }
+        if (a.mask != nullptr) {
+          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * C + co);
+          if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+          if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+        }
+        *reinterpret_cast<__nv_bfloat162*>(a.out_nhwc + pix * C + co) = __floats2bfloat162_rn(v0, v1);
+      } else {
+        const size_t hw = (size_t)a.H * a.W, off = (size_t)y * a.W + x;
+        if (co < a.cout) {
+          const size_t o = ((size_t)b * 3 + co) * hw + off;
+          a.out_planar[o] = v0 + (a.resid ? a.resid[o] : 0.0f);
+        }
+        if (co + 1 < a.cout) {
+          const size_t o = ((size_t)b * 3 + co + 1) * hw + off;
+          a.out_planar[o] = v1 + (a.resid ? a.resid[o] : 0.0f);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- weight gradient
+// dW[co][k] += sum_p dY[p][co] * X_unrolled[p][k], db[co] += sum_p dY[p][co]:
+// a GEMM with M = output channels (MT tiles of 16), N = k (8-wide tiles), K = pixels.
+// dY is staged [pixel][co] (NHWC BF16, or 3-channel planar FP32 converted), the input
+// as for the forward kernel; ldmatrix.trans turns both into the fragments.  Each CTA
+// sweeps several pixel tiles, then adds its partial sums into FP32 dW with atomics.
+struct WgradArgs {
+  int B, H, W;
+  const bf16* dy_nhwc;      // 32-channel gradient (NHWC BF16), or null
+  const float* dy_planar;   // 3-channel gradient (planar FP32), or null
+  const bf16* in_nhwc;      // layer input, 32-channel NHWC
+  const float* in_planar;   // layer input, 3-channel planar
+  float* dw;                // [cout][K] FP32 (accumulated)
+  float* db;                // [cout] FP32 (accumulated)
+  int cout;
+  int tiles_x, tiles_y;
+};
+
+template <bool PLANAR_IN, bool PLANAR_DY>
+__global__ void __launch_bounds__(NTHREADS) conv_wgrad_kernel(WgradArgs a) {
+  constexpr int K = PLANAR_IN ? KIN : KMID;        // columns of dW
+  constexpr int NKT = K / 8;                         // n-tiles (36 or 4)
+  constexpr int MT = PLANAR_DY ? 1 : 2;              // 16-row tiles of output channels
+  constexpr int DYS = 40;                            // bf16 per staged dY pixel (32 + pad)
+  constexpr int FRAGS = MT * NKT;                    // (m-tile, n-tile) pairs
+  constexpr int PER_WARP = (FRAGS + 7) / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  bf16* sDY = reinterpret_cast<bf16*>(smraw);        // [128 px][DYS]
+  bf16* sA = sDY + TH * TW * DYS;                    // input tile as in the forward kernel
+  __shared__ float sdb[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[PER_WARP][4];
+#pragma unroll
+  for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+  if (threadIdx.x < 32) sdb[threadIdx.x] = 0.0f;
+  const int ntiles = a.B * a.tiles_y * a.tiles_x;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int b = tile / (a.tiles_y * a.tiles_x);
+    const int r = tile - b * a.tiles_y * a.tiles_x;
+    const int y0 = (r / a.tiles_x) * TH, x0 = (r % a.tiles_x) * TW;
+    __syncthreads();
+    // dY tile [px][co] (zero outside the image; channels beyond cout zero)
+    for (int q = threadIdx.x; q < TH * TW * 32; q += NTHREADS) {
+      const int px = q >> 5, co = q & 31;
+      const int y = y0 + px / TW, x = x0 + px % TW;
+      float v = 0.0f;
+      if (y < a.H && x < a.W) {
+        if (PLANAR_DY) {
+          if (co < a.cout) v = a.dy_planar[(((size_t)b * 3 + co) * a.H + y) * a.W + x];
+        } else {
+          v = __bfloat162float(a.dy_nhwc[(((size_t)b * a.H + y) * a.W + x) * C + co]);
+        }
+      }
+      sDY[px * DYS + co] = __float2bfloat16_rn(v);
+    }
+    {
+      ConvArgs ca{};
+      ca.H = a.H; ca.W = a.W; ca.in_nhwc = a.in_nhwc; ca.in_planar = a.in_planar;
+      stage_input<PLANAR_IN>(ca, sA, b, y0, x0);
+    }
+    __syncthreads();
+    // bias gradient: column sums of the staged dY
+    if (threadIdx.x < 32) {
+      float s = 0.0f;
+      for (int px = 0; px < TH * TW; ++px) s += __bfloat162float(sDY[px * DYS + threadIdx.x]);
+      sdb[threadIdx.x] += s;
+    }
+    // K = 128 pixels in 8 steps of 16 (one tile row of 16 pixels per step)
+#pragma unroll 1
+    for (int ks = 0; ks < TH; ++ks) {
+#pragma unroll
+      for (int i = 0; i < PER_WARP; ++i) {
+        const int fi = warp + 8 * i;
+        if (fi >= FRAGS) break;
+        const int mt = fi / NKT, nt = fi - mt * NKT;
+        // A = dY^T (rows co, cols px): trans-load 16 px x 16 co; lane -> pixel row, co half
+        uint32_t a0, a1, a2, a3;
+        {
+          // matrices: (px 0-7, co 0-7), (px 0-7, co 8-15), (px 8-15, co 0-7), (px 8-15, co 8-15)
+          // transposed they give A rows co 0-7 / 8-15 and k (px) 0-7 / 8-15 in a0..a3 order:
+          // a0: co 0-7, px 0-7; a1: co 8-15, px 0-7; a2: co 0-7, px 8-15; a3: co 8-15, px 8-15
+          const int mi = lane >> 3, rr = lane & 7;
+          const int px = ks * TW + rr + ((mi >> 1) << 3);
+          const int co = mt * 16 + ((mi & 1) << 3);
+          ldsm_x4_t(smem_u32(sDY + px * DYS + co), a0, a1, a2, a3);
+        }
+        // B = X_unrolled (rows px = k-dim, cols k = n-dim): trans-load 16 px x 8 columns
+        uint32_t b0, b1;
+        {
+          const int mi = (lane >> 3) & 1, rr = lane & 7;
+          const int pxl = rr + (mi << 3);  // pixel within this 16-pixel row segment
+          const bf16* src;
+          if (PLANAR_IN) {
+            src = sA + (ks * TW + pxl) * PXS + nt * 8;
+          } else {
+            const int tap = nt / 4, cb = (nt & 3) * 8;  // column k = tap * 32 + ci
+            src = sA + ((ks + tap / 3) * (TW + 2) + pxl + tap % 3) * PXS + cb;
+          }
+          ldsm_x2_t(smem_u32(src), b0, b1);
+        }
+        mma_bf16(acc[i], a0, a1, a2, a3, b0, b1);
+      }
+    }
+  }
+  __syncthreads();
+  // accumulate: acc[i][0..1] = (co = mt*16 + g, k = nt*8 + 2t, +1), acc[i][2..3] = co + 8
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int i = 0; i < PER_WARP; ++i) {
+    const int fi = warp + 8 * i;
+    if (fi >= FRAGS) break;
+    const int mt = fi / NKT, nt = fi - mt * NKT;
+    const int co0 = mt * 16 + g, k = nt * 8 + 2 * t;
+    if (co0 < a.cout) {
+      atomicAdd(&a.dw[co0 * K + k], acc[i][0]);
+      atomicAdd(&a.dw[co0 * K + k + 1], acc[i][1]);
+    }
+    if (co0 + 8 < a.cout) {
+      atomicAdd(&a.dw[(co0 + 8) * K + k], acc[i][2]);
+      atomicAdd(&a.dw[(co0 + 8) * K + k + 1], acc[i][3]);
+    }
+  }
+  if (threadIdx.x < a.cout) atomicAdd(&a.db[threadIdx.x], sdb[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------- small helpers
+
+// Master FP32 weights [co][kpad] (column k = tap * ci_n + ci, tap = 3 ky + kx) -> BF16 GEMM
+// rows for the forward conv ([co_pad][kcols], rows >= co_n zero) or, with transpose_flip,
+// for the input-gradient conv: it maps the co_n-channel gradient to ci_n channels, so row
+// r = ci and column k' = tap' * co_n + co read the weight of tap 8 - tap' (the flipped kernel).
+__global__ void pack_weights_kernel(const float* __restrict__ w, int co_n, int ci_n, int co_pad, int kcols,
+                                    int transpose_flip, bf16* __restrict__ out) {
+  const int kpad = ci_n == 3 ? KIN : KMID;
+  const int total = co_pad * kcols;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int r = q / kcols, k = q - r * kcols;
+    float v = 0.0f;
+    if (!transpose_flip) {
+      if (r < co_n && k < 9 * ci_n) v = w[r * kpad + k];
+    } else {
+      const int tapp = k / co_n, co = k - tapp * co_n;
+      if (r < ci_n && tapp < 9) v = w[co * kpad + (8 - tapp) * ci_n + r];
+    }
+    out[q] = __float2bfloat16_rn(v);
+  }
+}
+
+// Adam on FP32 master weights: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// w -= lr * mhat / (sqrt(vhat) + eps), with bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t.
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// grad = 2 (u0 - target) / n_total; loss partial sums of (u0 - target)^2 into *loss
+__global__ void mse_kernel(const float* u0, const float* target, float* grad, size_t n, float scale,
+                           float* loss) {
+  float s = 0.0f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float d = u0[i] - target[i];
+    grad[i] = 2.0f * d * scale;
+    s += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * scale);
+}
+
+// max |a - b| over n values, as the bit pattern of a non-negative float (monotone in the value)
+__global__ void maxabsdiff_kernel(const float* a, const float* b, size_t n, unsigned int* out) {
+  float m = 0.0f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(a[i] - b[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+}  // namespace cnn
+}  // namespace ils
+
+// ================================================================ host side
+using namespace ils::cnn;
+
+namespace {
+
+constexpr int kLayers = 6;
+constexpr int kCin[kLayers] = {3, 32, 32, 32, 32, 32};
+constexpr int kCout[kLayers] = {32, 32, 32, 32, 32, 3};
+
+int kpad(int l) { return kCin[l] == 3 ? KIN : KMID; }            // GEMM columns of layer l
+int copad(int l) { return kCout[l] == 3 ? 8 : 32; }              // padded output rows (forward)
+int dg_kpad(int l) { return kCout[l] == 3 ? KIN : KMID; }        // columns of the input-gradient conv
+size_t param_count() {
+  size_t n = 0;
+  for (int l = 0; l < kLayers; ++l) n += (size_t)kCout[l] * kCin[l] * 9 + kCout[l];
+  return n;
+}
+
+size_t conv_smem(bool planar_in, int nt) {
+  const int ks = planar_in ? KIN_S : KMID_S;
+  const int a = planar_in ? TH * TW * PXS : HALO_PX * PXS;
+  return (size_t)(nt * 8 * ks + a) * sizeof(bf16);
+}
+size_t wgrad_smem(bool planar_in) {
+  const int a = planar_in ? TH * TW * PXS : HALO_PX * PXS;
+  return (size_t)(TH * TW * 40 + a) * sizeof(bf16);
+}
+
+}  // namespace
+
+struct ils_cnn {
+  size_t max_px;
+  float* w[kLayers];     // FP32 master weights [cout][kpad]
+  float* b[kLayers];     // FP32 biases [cout]
+  float* gw[kLayers];    // gradients (same layouts)
+  float* gb[kLayers];
+  float* mw[kLayers];    // Adam moments
+  float* vw[kLayers];
+  float* mb[kLayers];
+  float* vb[kLayers];
+  bf16* wf[kLayers];     // forward BF16 weights [copad][kpad]
+  bf16* wd[kLayers];     // input-gradient BF16 weights [cin][dg_kpad] (layers 1..5)
+  bf16* act[kLayers - 1];  // post-ReLU activations of layers 0..4, NHWC BF16 [max_px][32]
+  bf16* gact[2];           // gradient ping-pong, NHWC BF16
+  int step;
+  bool packed;
+};
+
+namespace {
+
+ils_status cnn_fail(cudaError_t e, const char* where) {
+  ils::record_cuda_error(where, e);
+  return e == cudaErrorMemoryAllocation ? ILS_ERR_OOM : ILS_ERR_CUDA;
+}
+
+void cnn_free(ils_cnn* n) {
+  for (int l = 0; l < kLayers; ++l) {
+    cudaFree(n->w[l]); cudaFree(n->b[l]); cudaFree(n->gw[l]); cudaFree(n->gb[l]);
+    cudaFree(n->mw[l]); cudaFree(n->vw[l]); cudaFree(n->mb[l]); cudaFree(n->vb[l]);
+    cudaFree(n->wf[l]); cudaFree(n->wd[l]);
+  }
+  for (int l = 0; l < kLayers - 1; ++l) cudaFree(n->act[l]);
+  cudaFree(n->gact[0]);
+  cudaFree(n->gact[1]);
+  delete n;
+}
+
+cudaError_t cnn_pack(ils_cnn* n, cudaStream_t st) {
+  for (int l = 0; l < kLayers; ++l) {
+    pack_weights_kernel<<<64, 256, 0, st>>>(n->w[l], kCout[l], kCin[l], copad(l), kpad(l), 0, n->wf[l]);
+    if (l > 0) pack_weights_kernel<<<64, 256, 0, st>>>(n->w[l], kCout[l], kCin[l], 32, dg_kpad(l), 1, n->wd[l]);
+  }
+  n->packed = true;
+  return cudaGetLastError();
+}
+
+dim3 tile_grid(int B, int H, int W) { return dim3((W + TW - 1) / TW, (H + TH - 1) / TH, B); }
+
+bool cnn_shape_ok(const ils_cnn* n, int B, int H, int W) {
+  return n != nullptr && B >= 1 && H >= 1 && W >= 1 && (size_t)B * H * W <= n->max_px;
+}
+
+}  // namespace
+
+extern "C" {
+
+ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
+  if (out == nullptr || max_pixels < 1) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  ils_cnn* n = new (std::nothrow) ils_cnn();
+  if (n == nullptr) return ILS_ERR_OOM;
+  n->max_px = (size_t)max_pixels;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+    const size_t nw = (size_t)kCout[l] * kpad(l), nb = kCout[l];
+    float** f32[] = {&n->w[l], &n->gw[l], &n->mw[l], &n->vw[l]};
+    for (float** p : f32)
+      if (e == cudaSuccess && (e = cudaMalloc((void**)p, nw * 4)) == cudaSuccess) e = cudaMemset(*p, 0, nw * 4);
+    float** f32b[] = {&n->b[l], &n->gb[l], &n->mb[l], &n->vb[l]};
+    for (float** p : f32b)
+      if (e == cudaSuccess && (e = cudaMalloc((void**)p, nb * 4)) == cudaSuccess) e = cudaMemset(*p, 0, nb * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&n->wf[l], (size_t)copad(l) * kpad(l) * sizeof(bf16));
+    if (e == cudaSuccess && l > 0) e = cudaMalloc((void**)&n->wd[l], (size_t)32 * dg_kpad(l) * sizeof(bf16));
+  }
+  for (int l = 0; l < kLayers - 1 && e == cudaSuccess; ++l)
+    e = cudaMalloc((void**)&n->act[l], n->max_px * C * sizeof(bf16));
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc((void**)&n->gact[i], n->max_px * C * sizeof(bf16));
+  if (e == cudaSuccess) {
+    cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv_smem(false, 4));
+    cudaFuncSetAttribute(conv_fwd_kernel<false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv_smem(false, 1));
+    cudaFuncSetAttribute(conv_fwd_kernel<true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv_smem(true, 4));
+    cudaFuncSetAttribute(conv_wgrad_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)wgrad_smem(false));
+    cudaFuncSetAttribute(conv_wgrad_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)wgrad_smem(false));
+    cudaFuncSetAttribute(conv_wgrad_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)wgrad_smem(true));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    cnn_free(n);
+    return cnn_fail(e, "ils_cnn_create");
+  }
+  n->step = 0;
+  n->packed = false;
+  *out = n;
+  return ILS_OK;
+}
+
+ils_status ils_cnn_destroy(ils_cnn* n) {
+  if (n == nullptr) return ILS_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  cnn_free(n);
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cudaDeviceSynchronize");
+}
+
+long long ils_cnn_param_count(void) { return (long long)param_count(); }
+
+// params: per layer W[co][ci][3][3] then b[co] (FP32, host)
+ils_status ils_cnn_set_weights(ils_cnn* n, const float* params, long long count) {
+  if (n == nullptr || params == nullptr || count != (long long)param_count()) return ILS_ERR_INVALID_ARG;
+  size_t off = 0;
+  cudaError_t e;
+  for (int l = 0; l < kLayers; ++l) {
+    const int co_n = kCout[l], ci_n = kCin[l], K = kpad(l);
+    std::vector<float> w((size_t)co_n * K, 0.0f);
+    for (int co = 0; co < co_n; ++co)
+      for (int ci = 0; ci < ci_n; ++ci)
+        for (int tap = 0; tap < 9; ++tap) w[(size_t)co * K + tap * ci_n + ci] = params[off + ((size_t)co * ci_n + ci) * 9 + tap];
+    off += (size_t)co_n * ci_n * 9;
+    if ((e = cudaMemcpy(n->w[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice))) return cnn_fail(e, "set_weights");
+    if ((e = cudaMemcpy(n->b[l], params + off, (size_t)co_n * 4, cudaMemcpyHostToDevice))) return cnn_fail(e, "set_weights");
+    off += co_n;
+    cudaMemset(n->mw[l], 0, w.size() * 4);
+    cudaMemset(n->vw[l], 0, w.size() * 4);
+    cudaMemset(n->mb[l], 0, (size_t)co_n * 4);
+    cudaMemset(n->vb[l], 0, (size_t)co_n * 4);
+  }
+  n->step = 0;
+  if ((e = cnn_pack(n, nullptr))) return cnn_fail(e, "pack");
+  if ((e = cudaDeviceSynchronize())) return cnn_fail(e, "set_weights");
+  return ILS_OK;
+}
+
+ils_status ils_cnn_get_weights(const ils_cnn* n, float* params, long long count) {
+  if (n == nullptr || params == nullptr || count != (long long)param_count()) return ILS_ERR_INVALID_ARG;
+  size_t off = 0;
+  cudaError_t e;
+  if ((e = cudaDeviceSynchronize())) return cnn_fail(e, "get_weights");
+  for (int l = 0; l < kLayers; ++l) {
+    const int co_n = kCout[l], ci_n = kCin[l], K = kpad(l);
+    std::vector<float> w((size_t)co_n * K);
+    if ((e = cudaMemcpy(w.data(), n->w[l], w.size() * 4, cudaMemcpyDeviceToHost))) return cnn_fail(e, "get_weights");
+    for (int co = 0; co < co_n; ++co)
+      for (int ci = 0; ci < ci_n; ++ci)
+        for (int tap = 0; tap < 9; ++tap) params[off + ((size_t)co * ci_n + ci) * 9 + tap] = w[(size_t)co * K + tap * ci_n + ci];
+    off += (size_t)co_n * ci_n * 9;
+    if ((e = cudaMemcpy(params + off, n->b[l], (size_t)co_n * 4, cudaMemcpyDeviceToHost))) return cnn_fail(e, "get_weights");
+    off += co_n;
+  }
+  return ILS_OK;
+}
+
+// gradients in the same order as the parameters
+ils_status ils_cnn_get_grads(const ils_cnn* n, float* grads, long long count) {
+  if (n == nullptr || grads == nullptr || count != (long long)param_count()) return ILS_ERR_INVALID_ARG;
+  size_t off = 0;
+  cudaError_t e;
+  if ((e = cudaDeviceSynchronize())) return cnn_fail(e, "get_grads");
+  for (int l = 0; l < kLayers; ++l) {
+    const int co_n = kCout[l], ci_n = kCin[l], K = kpad(l);
+    std::vector<float> w((size_t)co_n * K);
+    if ((e = cudaMemcpy(w.data(), n->gw[l], w.size() * 4, cudaMemcpyDeviceToHost))) return cnn_fail(e, "get_grads");
+    for (int co = 0; co < co_n; ++co)
+      for (int ci = 0; ci < ci_n; ++ci)
+        for (int tap = 0; tap < 9; ++tap) grads[off + ((size_t)co * ci_n + ci) * 9 + tap] = w[(size_t)co * K + tap * ci_n + ci];
+    off += (size_t)co_n * ci_n * 9;
+    if ((e = cudaMemcpy(grads + off, n->gb[l], (size_t)co_n * 4, cudaMemcpyDeviceToHost))) return cnn_fail(e, "get_grads");
+    off += co_n;
+  }
+  return ILS_OK;
+}
+
+// u0 = f + net(f); f, u0: device B x 3 x H x W FP32.  Keeps the hidden activations for backward.
+ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, float* u0, void* stream) {
+  if (!cnn_shape_ok(n, B, H, W) || f == nullptr || u0 == nullptr || f == u0 || !n->packed) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const dim3 grid = tile_grid(B, H, W);
+  ConvArgs a{};
+  a.B = B; a.H = H; a.W = W;
+  // layer 0: planar 3 -> 32, ReLU
+  a.in_planar = f; a.wt = n->wf[0]; a.bias = n->b[0]; a.out_nhwc = n->act[0]; a.relu = 1; a.cout = 32;
+  conv_fwd_kernel<true, 4, false><<<grid, NTHREADS, conv_smem(true, 4), st>>>(a);
+  for (int l = 1; l < kLayers - 1; ++l) {
+    ConvArgs m{};
+    m.B = B; m.H = H; m.W = W; m.in_nhwc = n->act[l - 1]; m.wt = n->wf[l]; m.bias = n->b[l];
+    m.out_nhwc = n->act[l]; m.relu = 1; m.cout = 32;
+    conv_fwd_kernel<false, 4, false><<<grid, NTHREADS, conv_smem(false, 4), st>>>(m);
+  }
+  ConvArgs z{};
+  z.B = B; z.H = H; z.W = W; z.in_nhwc = n->act[kLayers - 2]; z.wt = n->wf[kLayers - 1]; z.bias = n->b[kLayers - 1];
+  z.out_planar = u0; z.resid = f; z.cout = 3;
+  conv_fwd_kernel<false, 1, true><<<grid, NTHREADS, conv_smem(false, 1), st>>>(z);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn forward launch");
+}
+
+ils_status ils_cnn_zero_grad(ils_cnn* n, void* stream) {
+  if (n == nullptr) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < kLayers; ++l) {
+    cudaMemsetAsync(n->gw[l], 0, (size_t)kCout[l] * kpad(l) * 4, st);
+    cudaMemsetAsync(n->gb[l], 0, (size_t)kCout[l] * 4, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "zero_grad");
+}
+
+// Adds dL/dparams for dL/du0 (planar FP32, B x 3 x H x W) to the gradients, using the
+// activations of the last forward call on the same f.
+ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, const float* grad_u0, void* stream) {
+  if (!cnn_shape_ok(n, B, H, W) || f == nullptr || grad_u0 == nullptr || !n->packed) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const dim3 grid = tile_grid(B, H, W);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = grid.x * grid.y * grid.z;
+  const int wg_grid = tiles < 2 * sms ? tiles : 2 * sms;
+  auto wgrad = [&](int l, const bf16* dy_nhwc, const float* dy_planar) {
+    WgradArgs w{};
+    w.B = B; w.H = H; w.W = W; w.dy_nhwc = dy_nhwc; w.dy_planar = dy_planar;
+    w.dw = n->gw[l]; w.db = n->gb[l]; w.cout = kCout[l]; w.tiles_x = grid.x; w.tiles_y = grid.y;
+    if (l == 0) {
+      w.in_planar = f;
+      conv_wgrad_kernel<true, false><<<wg_grid, NTHREADS, wgrad_smem(true), st>>>(w);
+    } else {
+      w.in_nhwc = n->act[l - 1];
+      if (dy_planar != nullptr)
+        conv_wgrad_kernel<false, true><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
+      else
+        conv_wgrad_kernel<false, false><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
+    }
+  };
+  // layer 5 (32 -> 3): its output gradient is dL/du0 (the residual passes f through)
+  wgrad(kLayers - 1, nullptr, grad_u0);
+  {
+    ConvArgs a{};
+    a.B = B; a.H = H; a.W = W; a.in_planar = grad_u0; a.wt = n->wd[kLayers - 1];
+    a.out_nhwc = n->gact[0]; a.mask = n->act[kLayers - 2]; a.cout = 32;
+    conv_fwd_kernel<true, 4, false><<<grid, NTHREADS, conv_smem(true, 4), st>>>(a);
+  }
+  int cur = 0;
+  for (int l = kLayers - 2; l >= 1; --l) {
+    wgrad(l, n->gact[cur], nullptr);
+    ConvArgs a{};
+    a.B = B; a.H = H; a.W = W; a.in_nhwc = n->gact[cur]; a.wt = n->wd[l];
+    a.out_nhwc = n->gact[cur ^ 1]; a.mask = n->act[l - 1]; a.cout = 32;
+    conv_fwd_kernel<false, 4, false><<<grid, NTHREADS, conv_smem(false, 4), st>>>(a);
+    cur ^= 1;
+  }
+  wgrad(0, n->gact[cur], nullptr);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn backward launch");
+}
+
+ils_status ils_cnn_adam_step(ils_cnn* n, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (n == nullptr || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f))
+    return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  n->step += 1;
+  const float c1 = 1.0f - std::pow(beta1, (float)n->step), c2 = 1.0f - std::pow(beta2, (float)n->step);
+  for (int l = 0; l < kLayers; ++l) {
+    const int nw = kCout[l] * kpad(l);
+    adam_kernel<<<(nw + 255) / 256, 256, 0, st>>>(n->w[l], n->gw[l], n->mw[l], n->vw[l], nw, lr, beta1, beta2, eps,
+                                                  c1, c2);
+    adam_kernel<<<1, 64, 0, st>>>(n->b[l], n->gb[l], n->mb[l], n->vb[l], kCout[l], lr, beta1, beta2, eps, c1, c2);
+  }
+  cudaError_t e = cnn_pack(n, st);
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "adam step");
+}
+
+// grad = 2 (u0 - target) / n; *loss (device FP32, caller zeroes it) += mean squared error
+ils_status ils_mse(const float* u0, const float* target, float* grad, long long n, float* loss, void* stream) {
+  if (u0 == nullptr || target == nullptr || grad == nullptr || loss == nullptr || n < 1) return ILS_ERR_INVALID_ARG;
+  mse_kernel<<<512, 256, 0, static_cast<cudaStream_t>(stream)>>>(u0, target, grad, (size_t)n, 1.0f / (float)n, loss);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "mse");
+}
+
+}  // extern "C"
+
+namespace ils {
+cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st) {
+  maxabsdiff_kernel<<<512, 256, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+}  // namespace ils

@@ -59,6 +59,8 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                bool last, float2* spec_out, cudaStream_t stream);
 cudaError_t set_kernel_attributes();
 void record_cuda_error(const char* where, cudaError_t e);  // text for ils_last_error()
+// max |a - b| over n floats as the bit pattern of a non-negative float, atomically max'ed into *out
+cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st);
 
 // Compile-time specialised kernels (ils_kernels_fixed.cu).
 int fixed_row_index(int M);

@@ -1,0 +1,137 @@
+"""The warm-start network's tensor-core kernels against the FP64 oracle with BF16 rounding
+points, its training, and the warm-started smoothing with its fallback.
+
+Bars: the forward and every parameter gradient agree with the oracle that rounds to BF16
+where the kernels store BF16; the remaining difference is FP32 vs FP64 accumulation, which
+can move a value across a BF16 rounding boundary (one BF16 step, 2^-8 relative) and
+propagate, so the bar is 2% of each tensor's largest magnitude (max-norm) and 0.5% in RMS.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_07504_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    import torch
+    from paper_2003_07504_gb300 import build
+    build.build()
+    from paper_2003_07504_gb300 import warmstart as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def rel_max(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(1e-30, np.abs(b).max()))
+
+
+def rel_rms(a, b):
+    d = np.asarray(a, np.float64) - b
+    return float(np.sqrt((d * d).mean()) / max(1e-30, np.sqrt((np.asarray(b) ** 2).mean())))
+
+
+def random_params(ws, seed, last_scale=0.3):
+    return ws.init_params(seed=seed, last_scale=last_scale)
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 8, 16), (2, 20, 36), (1, 33, 47)])
+def test_forward_matches_oracle(ws, B, H, W):
+    import torch
+    p = random_params(ws, 1)
+    f = synth.preset_image(H, W, 3 * B, "small", H + W).reshape(B, 3, H, W)
+    net = ws.WarmStartNet(B * H * W, p)
+    u0 = net.forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    wts, bs = ws.unpack_params(p)
+    want, _ = O.warmstart_forward_bf16(f, wts, bs)
+    assert rel_max(u0 - f, want - f) <= 2e-2 and rel_rms(u0 - f, want - f) <= 5e-3
+    net.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 16, 32), (1, 27, 45)])
+def test_backward_matches_oracle(ws, B, H, W):
+    import torch
+    p = random_params(ws, 2)
+    f = synth.preset_image(H, W, 3 * B, "small", 5 + H).reshape(B, 3, H, W)
+    g = synth.random_field((B, 3, H, W), seed=6)
+    net = ws.WarmStartNet(B * H * W, p)
+    ft = torch.from_numpy(f).cuda()
+    net.forward(ft)
+    net.zero_grad()
+    net.backward(ft, torch.from_numpy(g).cuda())
+    grads = net.get_grads()
+    wts, bs = ws.unpack_params(p)
+    dW, db = O.warmstart_backward_bf16(f, wts, bs, g)
+    gw, gb = ws.unpack_params(grads)
+    for l in range(len(wts)):
+        assert rel_max(gw[l], dW[l]) <= 2e-2 and rel_rms(gw[l], dW[l]) <= 5e-3, l
+        assert rel_max(gb[l], db[l]) <= 2e-2, l
+    # gradients accumulate until zero_grad
+    net.backward(ft, torch.from_numpy(g).cuda())
+    np.testing.assert_allclose(net.get_grads(), 2 * grads, rtol=1e-5, atol=1e-6 * np.abs(grads).max())
+    net.close()
+
+
+def test_adam_step_matches_oracle(ws):
+    import torch
+    p = random_params(ws, 3)
+    H, W = 16, 16
+    f = synth.preset_image(H, W, 3, "small", 9).reshape(1, 3, H, W)
+    net = ws.WarmStartNet(H * W, p)
+    ft = torch.from_numpy(f).cuda()
+    net.forward(ft)
+    net.zero_grad()
+    net.backward(ft, torch.from_numpy(synth.random_field((1, 3, H, W), seed=1)).cuda())
+    g = net.get_grads().astype(np.float64)
+    net.adam_step(1e-3)
+    want, _, _ = O.adam_step(p.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr=1e-3)
+    np.testing.assert_allclose(net.get_params(), want, rtol=1e-5, atol=1e-7)
+    net.close()
+
+
+def test_mse_kernel(ws):
+    import torch
+    a = torch.from_numpy(synth.random_field((2, 3, 10, 12), seed=1)).cuda()
+    b = torch.from_numpy(synth.random_field((2, 3, 10, 12), seed=2)).cuda()
+    grad = torch.empty_like(a)
+    loss = torch.zeros(1, device="cuda")
+    ws.mse(a, b, grad, loss)
+    d = (a - b).double().cpu().numpy()
+    assert float(loss.item()) == pytest.approx((d * d).mean(), rel=1e-5)
+    np.testing.assert_allclose(grad.cpu().numpy(), 2 * d / d.size, rtol=1e-5, atol=1e-9)
+
+
+def test_training_fits_a_fixed_batch(ws):
+    # the same 4 crops every step: the loss (u0 vs the ILS N=4 target) must fall well below
+    # its starting value u0 = f
+    params, losses = ws.train(steps=200, batch=4, crop=64, lr=3e-3, n_crops=4, pool_images=2, pool_size=128,
+                              log_every=25, verbose=False)
+    first, last = losses[0][1], losses[-1][1]
+    assert np.isfinite(params).all() and last < 0.6 * first, losses
+
+
+def test_warm_smoother_paths(ws):
+    # tau = inf: never falls back -> equals ILS_iters from u0 = net(f); tau = 0: always plain ILS N=4
+    import torch
+    from paper_2003_07504_gb300 import ils
+    H, W = 48, 64
+    p = random_params(ws, 4, last_scale=1e-2)
+    f = torch.from_numpy(synth.preset_image(H, W, 3, "small", 12)).cuda()
+    net = ws.WarmStartNet(H * W, p)
+    u0 = net.forward(f.view(1, 3, H, W)).view(3, H, W)
+    for iters in (1, 2):
+        sm = ws.WarmSmoother(net, H, W, 3, iters=iters, tau=float("inf"))
+        u, fb, d = sm.smooth(f)
+        with ils.Plan(H, W, 3, 1.0, 0.8, 1e-4, iters) as plan:
+            ref = plan.smooth(f, u0=u0)
+        assert not fb and torch.equal(u, ref) and d > 0
+        sm.close()
+    sm = ws.WarmSmoother(net, H, W, 3, iters=1, tau=0.0)
+    u, fb, d = sm.smooth(f)
+    with ils.Plan(H, W, 3, 1.0, 0.8, 1e-4, 4) as plan:
+        assert fb and torch.equal(u, plan.smooth(f))
+    sm.close()
+    net.close()

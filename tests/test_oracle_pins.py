@@ -334,3 +334,51 @@ def test_adjoint_split_for_a_warm_start():
     L = lambda ff, uu: np.sum(w * O.ils_channel(ff, lam, p, eps, N, u0=uu))
     assert np.sum(gf * v) == pytest.approx((L(f + h * v, u0) - L(f - h * v, u0)) / (2 * h), rel=1e-6, abs=1e-7)
     assert np.sum(gu0 * v) == pytest.approx((L(f, u0 + h * v) - L(f, u0 - h * v)) / (2 * h), rel=1e-6, abs=1e-7)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    # exactly representable values pass; halfway cases go to the even neighbour
+    assert O.bf16_round(1.0) == 1.0 and O.bf16_round(-2.5) == -2.5
+    one_ulp = 2.0 ** -7                       # BF16 spacing in [1, 2)
+    assert O.bf16_round(1.0 + one_ulp / 2) == 1.0            # tie -> even (1.0)
+    assert O.bf16_round(1.0 + 3 * one_ulp / 2) == 1.0 + 2 * one_ulp  # tie -> even
+    assert O.bf16_round(1.0 + 0.51 * one_ulp) == 1.0 + one_ulp
+    x = np.random.default_rng(0).normal(size=1000)
+    r = O.bf16_round(x)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8 + 1e-300)
+
+
+def test_warmstart_chain_without_rounding_matches_autograd():
+    # with rounding off, the oracle's forward and its hand-ordered backward (masks, flips,
+    # transposes, bias sums) equal float64 autograd through conv2d + ReLU + residual
+    import torch
+    rng = np.random.default_rng(1)
+    chans = [3, 8, 8, 3]
+    ws = [rng.normal(scale=0.3, size=(chans[i + 1], chans[i], 3, 3)) for i in range(3)]
+    bs = [rng.normal(scale=0.1, size=chans[i + 1]) for i in range(3)]
+    f = rng.uniform(size=(2, 3, 6, 7))
+    g = rng.normal(size=(2, 3, 6, 7))
+    wt = [torch.tensor(w, requires_grad=True) for w in ws]
+    bt = [torch.tensor(b, requires_grad=True) for b in bs]
+    x = torch.tensor(f)
+    h = x
+    for i in range(3):
+        h = torch.nn.functional.conv2d(h, wt[i], bt[i], padding=1)
+        if i < 2:
+            h = torch.relu(h)
+    u = x + h
+    u.backward(torch.tensor(g))
+    u0, _ = O.warmstart_forward_bf16(f, ws, bs, rounding=False)
+    np.testing.assert_allclose(u0, u.detach().numpy(), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(O.warmstart_cnn_forward(f[1], ws, bs), u.detach().numpy()[1], rtol=1e-13, atol=1e-13)
+    dW, db = O.warmstart_backward_bf16(f, ws, bs, g, rounding=False)
+    for i in range(3):
+        np.testing.assert_allclose(dW[i], wt[i].grad.numpy(), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(db[i], bt[i].grad.numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_adam_step_closed_form_first_step():
+    # at t = 1 the bias-corrected update is lr * g / (|g| + eps) (a signed step of ~lr)
+    w, g = np.array([1.0, -2.0, 3.0]), np.array([0.5, -4.0, 1e-3])
+    w1, m, v = O.adam_step(w, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    np.testing.assert_allclose(w1, w - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
