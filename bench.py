@@ -226,6 +226,55 @@ def batch_leg(ils, torch, dev, steps, flush):
             "algorithmic_gbs": nbytes / (ms / 1000.0) / 1e9, "frac_of_hbm_peak": nbytes / (ms / 1000.0) / 1e9 / peak}
 
 
+def warm_leg(torch, dev, steps, flush):
+    """Learned warm start vs plain ILS at 1920x1080 RGB (lambda=1, p=0.8): fps of the whole
+    warm path (network + 1 or 2 ILS iterations + the iterate-change check and fallback
+    decision) against plain N=4, and each result's RMS distance to converged ILS from f
+    (ILS iterated until the largest per-iteration change is < 1e-6, capped at 2000)."""
+    from paper_2003_07504_gb300 import ils, synth, warmstart as ws
+    path = ws.DEFAULT_WEIGHTS
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights file"}
+    f = torch.from_numpy(synth.preset_image(H, W, C, "hd", 90004)).to(dev)
+    net = ws.WarmStartNet(H * W, ws.load_params(path))
+    ustar, its = ws.converged_ils(lambda h, w, c, n: ils.Plan(h, w, c, LAM, P, EPS, n), f, max_iters=2000)
+    rms = lambda u: float(((u - ustar) ** 2).mean().sqrt())
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    out = {"workload": "1920x1080 RGB, lambda=1, p=0.8, eps=1e-4; reference = ILS from f to convergence",
+           "reference_iterations": its, "uses_tcgen05": net.uses_tcgen05}
+    with ils.Plan(H, W, C, LAM, P, EPS, N_ITERS) as p4:
+        u4 = p4.smooth(f)
+        ms = timed(lambda: p4.smooth(f, out=u4))
+        out["plain_N4"] = {"fps": 1000.0 / ms, "ms": ms, "rms_to_converged": rms(u4)}
+    for iters in (1, 2):
+        sm = ws.WarmSmoother(net, H, W, C, LAM, P, EPS, iters=iters, n_plain=N_ITERS, tau=1.0)
+        u, fb, d = sm.smooth(f)
+        res = {"rms_to_converged": rms(u), "fallback": fb, "last_change": d}
+        res["ms"] = timed(lambda: sm.smooth(f, out=u))
+        res["fps"] = 1000.0 / res["ms"]
+        out[f"warm_{iters}_iter"] = res
+        sm.close()
+    net.check()
+    net.close()
+    return out
+
+
 def cpu_baseline_sample(budget_s: float = 20.0):
     """The oracle on one channel of the frame (bounded: 1 channel, N=4), scaled to fps."""
     import oracle as O
@@ -347,6 +396,7 @@ def run_ours(args):
         if not args.no_extras:
             line["adjoint"] = adjoint_leg(ils, torch, dev, max(3, min(args.steps, 20)))
             line["batch"] = batch_leg(ils, torch, dev, max(3, min(args.steps, 10)), flush)
+            line["warm_start"] = warm_leg(torch, dev, max(3, min(args.steps, 10)), flush)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)

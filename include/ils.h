@@ -201,6 +201,16 @@ ils_status ils_cnn_forward(ils_cnn* net, int B, int H, int W, const float* f, fl
 ils_status ils_cnn_backward(ils_cnn* net, int B, int H, int W, const float* f, const float* grad_u0, void* stream);
 ils_status ils_cnn_zero_grad(ils_cnn* net, void* stream);
 
+/* The four 32 -> 32 layers (and their input gradients) run on the tcgen05 tensor cores
+ * (TMA loads, tensor-memory accumulators) when the driver offers tensor-map encoding,
+ * else on the mma.sync kernels; ILS_CNN_TC=0 in the environment at creation forces the
+ * latter.  Returns 1 when the tcgen05 kernels are in use. */
+int ils_cnn_uses_tcgen05(const ils_cnn* net);
+
+/* Waits for the device; returns ILS_ERR_TIMEOUT (and clears it) if a tensor-core kernel's
+ * bounded wait on its own copies or MMAs gave up since the last check. */
+ils_status ils_cnn_check(ils_cnn* net);
+
 /* One Adam step on the FP32 master weights (bias-corrected; the step count is kept in
  * the network), then refresh the BF16 copies. */
 ils_status ils_cnn_adam_step(ils_cnn* net, float lr, float beta1, float beta2, float eps, void* stream);

@@ -68,6 +68,8 @@ SIGNATURES = {
     "ils_cnn_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "ils_cnn_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "ils_cnn_zero_grad": (c_int, [c_void_p, c_void_p]),
+    "ils_cnn_uses_tcgen05": (c_int, [c_void_p]),
+    "ils_cnn_check": (c_int, [c_void_p]),
     "ils_cnn_adam_step": (c_int, [c_void_p, c_float, c_float, c_float, c_float, c_void_p]),
     "ils_mse": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
     "ils_warm_create": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int, c_int, c_float, c_void_p,

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -102,15 +103,25 @@ __device__ __forceinline__ void stage_input(const ConvArgs& a, bf16* sA, int b, 
       *reinterpret_cast<uint4*>(sA + px * PXS + ch * 8) = v;
     }
   } else {
-    // 128 pixels x 32 columns: column k = tap * 3 + c (k < 27), zero beyond
+    // the 3-channel halo tile as FP32 (coalesced along x), then 128 pixels x 32 columns:
+    // column k = tap * 3 + c (k < 27), zero beyond
+    float* halo = reinterpret_cast<float*>(sA + TH * TW * PXS);   // [3][TH+2][TW+2]
+    for (int q = threadIdx.x; q < 3 * HALO_PX; q += NTHREADS) {
+      const int c = q / HALO_PX, r = q - c * HALO_PX;
+      const int hy = r / (TW + 2), hx = r - hy * (TW + 2);
+      const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+      float v = 0.0f;
+      if (y >= 0 && y < H && x >= 0 && x < W) v = a.in_planar[(((size_t)b * 3 + c) * H + y) * W + x];
+      halo[q] = v;
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < TH * TW * KIN; q += NTHREADS) {
       const int px = q >> 5, k = q & 31;
       const int ty = px / TW, tx = px - ty * TW;
       float v = 0.0f;
       if (k < 27) {
         const int tap = k / 3, c = k - tap * 3;
-        const int y = y0 + ty + tap / 3 - 1, x = x0 + tx + tap % 3 - 1;
-        if (y >= 0 && y < H && x >= 0 && x < W) v = a.in_planar[(((size_t)b * 3 + c) * H + y) * W + x];
+        v = halo[c * HALO_PX + (ty + tap / 3) * (TW + 2) + tx + tap % 3];
       }
       sA[px * PXS + k] = __float2bfloat16_rn(v);
     }
@@ -419,13 +430,15 @@ size_t param_count() {
   return n;
 }
 
+// planar inputs: unrolled tile (bf16) followed by the FP32 3-channel halo tile
+constexpr int kPlanarA = TH * TW * PXS + 2 * 3 * HALO_PX;   // in bf16 units
 size_t conv_smem(bool planar_in, int nt) {
   const int ks = planar_in ? KIN_S : KMID_S;
-  const int a = planar_in ? TH * TW * PXS : HALO_PX * PXS;
+  const int a = planar_in ? kPlanarA : HALO_PX * PXS;
   return (size_t)(nt * 8 * ks + a) * sizeof(bf16);
 }
 size_t wgrad_smem(bool planar_in) {
-  const int a = planar_in ? TH * TW * PXS : HALO_PX * PXS;
+  const int a = planar_in ? kPlanarA : HALO_PX * PXS;
   return (size_t)(TH * TW * 40 + a) * sizeof(bf16);
 }
 
@@ -447,6 +460,8 @@ struct ils_cnn {
   bf16* gact[2];           // gradient ping-pong, NHWC BF16
   int step;
   bool packed;
+  int* err;    // device flag raised by a tensor-core kernel whose bounded wait gave up
+  bool tc;     // middle layers on the tcgen05 kernel
 };
 
 namespace {
@@ -465,6 +480,7 @@ void cnn_free(ils_cnn* n) {
   for (int l = 0; l < kLayers - 1; ++l) cudaFree(n->act[l]);
   cudaFree(n->gact[0]);
   cudaFree(n->gact[1]);
+  cudaFree(n->err);
   delete n;
 }
 
@@ -508,6 +524,11 @@ ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
   for (int l = 0; l < kLayers - 1 && e == cudaSuccess; ++l)
     e = cudaMalloc((void**)&n->act[l], n->max_px * C * sizeof(bf16));
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc((void**)&n->gact[i], n->max_px * C * sizeof(bf16));
+  if (e == cudaSuccess && (e = cudaMalloc((void**)&n->err, sizeof(int))) == cudaSuccess) e = cudaMemset(n->err, 0, 4);
+  // ILS_CNN_TC=0 keeps every layer on the mma.sync kernels
+  const char* tcenv = getenv("ILS_CNN_TC");
+  n->tc = ils::conv32_tc_available() && !(tcenv != nullptr && tcenv[0] == '0');
+  if (e == cudaSuccess && n->tc) e = ils::conv32_tc_set_attributes();
   if (e == cudaSuccess) {
     cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)conv_smem(false, 4));
@@ -618,6 +639,11 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   a.in_planar = f; a.wt = n->wf[0]; a.bias = n->b[0]; a.out_nhwc = n->act[0]; a.relu = 1; a.cout = 32;
   conv_fwd_kernel<true, 4, false><<<grid, NTHREADS, conv_smem(true, 4), st>>>(a);
   for (int l = 1; l < kLayers - 1; ++l) {
+    if (n->tc) {
+      cudaError_t e = ils::launch_conv32_tc(B, H, W, n->act[l - 1], n->wf[l], n->b[l], n->act[l], nullptr, 1, n->err, st);
+      if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
+      continue;
+    }
     ConvArgs m{};
     m.B = B; m.H = H; m.W = W; m.in_nhwc = n->act[l - 1]; m.wt = n->wf[l]; m.bias = n->b[l];
     m.out_nhwc = n->act[l]; m.relu = 1; m.cout = 32;
@@ -630,6 +656,21 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn forward launch");
 }
+
+// Waits for the device and reports (then clears) a timeout raised by a tensor-core kernel.
+ils_status ils_cnn_check(ils_cnn* n) {
+  if (n == nullptr) return ILS_ERR_INVALID_ARG;
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, n->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cnn_fail(e, "ils_cnn_check");
+  if (flag) {
+    cudaMemset(n->err, 0, sizeof(int));
+    return ILS_ERR_TIMEOUT;
+  }
+  return ILS_OK;
+}
+
+int ils_cnn_uses_tcgen05(const ils_cnn* n) { return n != nullptr && n->tc ? 1 : 0; }
 
 ils_status ils_cnn_zero_grad(ils_cnn* n, void* stream) {
   if (n == nullptr) return ILS_ERR_INVALID_ARG;
@@ -679,6 +720,13 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
   int cur = 0;
   for (int l = kLayers - 2; l >= 1; --l) {
     wgrad(l, n->gact[cur], nullptr);
+    if (n->tc) {
+      cudaError_t e = ils::launch_conv32_tc(B, H, W, n->gact[cur], n->wd[l], nullptr, n->gact[cur ^ 1], n->act[l - 1], 0,
+                                       n->err, st);
+      if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
+      cur ^= 1;
+      continue;
+    }
     ConvArgs a{};
     a.B = B; a.H = H; a.W = W; a.in_nhwc = n->gact[cur]; a.wt = n->wd[l];
     a.out_nhwc = n->gact[cur ^ 1]; a.mask = n->act[l - 1]; a.cout = 32;

@@ -1,0 +1,338 @@
+// 32 -> 32 channel 3x3 convolution (the four middle layers of the warm-start network, and
+// their input gradients) on the 5th-generation tensor cores: TMA -> shared memory ->
+// tcgen05.mma (accumulator in tensor memory) -> tcgen05.ld epilogue.
+//
+// GEMM view per tile: M = 128 consecutive output pixels of one image row, N = 32 output
+// channels, K = 9 taps x 32 input channels, issued as 18 MMAs of K = 16 (BF16 in, FP32
+// accumulate).  The input rows y-1, y, y+1 over pixels x0-1 .. x0+128 are loaded by four
+// TMA copies, one per 8-channel chunk, into a chunk-major, pixel-minor shared layout:
+// byte (chunk c, row r, pixel p) = c * PLANE + (r * 130 + p) * 16.  In that layout the
+// canonical no-swizzle K-major operand (8-row x 16-byte core matrices, K-direction core
+// stride LBO, M-direction stride SBO) of tap (dy, dx) starts at (dy * 130 + dx) * 16: a
+// tap is a descriptor offset, and out-of-image pixels come from TMA's zero fill (the
+// convolution's zero padding).  The weights, [K-chunk][output channel][8], stay in
+// shared memory for all tiles of a persistent CTA.
+//
+// The kernel is a persistent pipeline: one warp issues the TMA copies into a ring of input
+// stages, one issues the MMAs into two tensor-memory accumulators, four drain them.
+// Every wait on an mbarrier is bounded; on timeout the kernel raises a flag, waits (also
+// bounded) for its own copies and MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "ils_internal.h"
+
+namespace ils {
+namespace cnn_tc {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TILE = 128;                  // pixels per tile (M)
+constexpr int HALO_W = TILE + 2;           // 130
+constexpr int PLANE = 6272;                // bytes per 8-channel chunk plane (3 x 130 x 16 = 6240, padded)
+constexpr int A_BYTES = 4 * PLANE;         // 25088
+constexpr int TMA_BYTES = 4 * 3 * HALO_W * 16;  // 24960 bytes delivered per tile
+constexpr int B_CHUNKS = 36;               // K = 288 = 36 chunks of 8
+constexpr int B_BYTES = B_CHUNKS * 32 * 16;  // 18432
+constexpr int SMEM_BYTES = A_BYTES + B_BYTES + 64;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: true when the phase completed, false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 | version 1 << 46,
+// no swizzle (layout type 0 in bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+struct TcArgs {
+  int B, H, W;
+  const bf16* wt;     // [32 co][288] BF16, column k = tap * 32 + ci (as for the mma.sync kernels)
+  const float* bias;  // [32] or null
+  bf16* out;          // NHWC BF16
+  const bf16* mask;   // NHWC BF16, or null: output zeroed where mask <= 0
+  int relu;
+  int* error;         // set to 1 when a bounded wait gave up
+  uint32_t spin;      // poll limit of the per-tile waits (a test sets it tiny to exercise the timeout path)
+};
+
+constexpr int STAGES = 3;                               // input tiles in flight
+constexpr int SMEM_PIPE = STAGES * A_BYTES + B_BYTES + 128;
+constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent, warp-specialized pipeline.  Tile i uses input stage i % STAGES and
+// accumulator i % 2 (32 tensor-memory columns each).  Barriers (phase parity from the
+// use count): full[s] TMA -> MMA, empty[s] MMA -> TMA (tcgen05.commit), accf[b] MMA ->
+// epilogue, acce[b] epilogue -> MMA (128 arrivals).
+__global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* sB = sm + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + STAGES * A_BYTES + B_BYTES);
+  __shared__ uint32_t tmem_base_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return saddr(&bars[s]); };
+  auto empty = [&](int s) { return saddr(&bars[STAGES + s]); };
+  auto accf = [&](int b) { return saddr(&bars[2 * STAGES + b]); };
+  auto acce = [&](int b) { return saddr(&bars[2 * STAGES + 2 + b]); };
+
+  for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
+    const int kc = q >> 5, co = q & 31;
+    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf(b), 1);
+      mbar_init(acce(b), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+
+  const int tiles_x = (a.W + TILE - 1) / TILE;
+  const int ntiles = a.B * a.H * tiles_x;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  bool failed = false;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int issued = 0;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int tile = blockIdx.x + i * gridDim.x;
+      const int b = tile / (a.H * tiles_x);
+      const int rr = tile - b * a.H * tiles_x;
+      const int y = rr / tiles_x, x0 = (rr - y * tiles_x) * TILE;
+      const int s = i % STAGES;
+      if (i >= STAGES && !mbar_wait(empty(s), ((i / STAGES) & 1) ^ 1, a.spin)) { failed = true; break; }
+      mbar_expect_tx(full(s), TMA_BYTES);
+      for (int c = 0; c < 4; ++c)
+        tma_load_4d(saddr(sm + s * A_BYTES + c * PLANE), &in_map, c * 8, x0 - 1, y - 1, b, full(s));
+      issued = i + 1;
+    }
+    // before the CTA may end, every copy issued must have landed (bounded)
+    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
+      if (!mbar_wait(full(i % STAGES), (i / STAGES) & 1)) failed = true;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    int issued = 0;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int s = i % STAGES, acc = i & 1;
+      if (!mbar_wait(full(s), (i / STAGES) & 1, a.spin)) { failed = true; break; }
+      if (i >= 2 && !mbar_wait(acce(acc), ((i >> 1) & 1) ^ 1, a.spin)) { failed = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = saddr(sm + s * A_BYTES), b0 = saddr(sB), d = tmem + acc * 32;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const uint32_t at = a0 + (uint32_t)((dy * HALO_W + dx) * 16);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint64_t da = smem_desc(at + kk * 2 * PLANE, PLANE, 128);
+          const uint64_t db = smem_desc(b0 + (uint32_t)((tap * 4 + kk * 2) * 512), 512, 128);
+          mma_f16(d, da, db, (tap | kk) ? 1u : 0u);
+        }
+      }
+      mma_commit(empty(s));
+      mma_commit(accf(acc));
+      issued = i + 1;
+    }
+    // the MMAs issued must complete before tensor memory is freed (bounded)
+    for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+      if (!mbar_wait(accf(i & 1), (i >> 1) & 1)) failed = true;
+  } else if (warp >= 2) {
+    // ---------------- epilogue: thread -> pixel (tensor-memory lane) 32 * (warp % 4) + lane
+    const int q = warp & 3;
+    const int px = q * 32 + lane;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int acc = i & 1;
+      if (!mbar_wait(accf(acc), (i >> 1) & 1, a.spin)) { failed = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r[32];
+      const uint32_t taddr = tmem + acc * 32 + ((uint32_t)(q * 32) << 16);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce(acc));
+      const int tile = blockIdx.x + i * gridDim.x;
+      const int b = tile / (a.H * tiles_x);
+      const int rr = tile - b * a.H * tiles_x;
+      const int y = rr / tiles_x, x = (rr - y * tiles_x) * TILE + px;
+      if (x < a.W) {
+        const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+        uint4 mk[4];
+        if (a.mask != nullptr)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) mk[t] = reinterpret_cast<const uint4*>(a.mask + pix * 32)[t];
+        uint4 o[4];
+        uint32_t* ow = reinterpret_cast<uint32_t*>(o);
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          float v0 = __uint_as_float(r[c]), v1 = __uint_as_float(r[c + 1]);
+          if (a.bias != nullptr) {
+            v0 += a.bias[c];
+            v1 += a.bias[c + 1];
+          }
+          if (a.relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          if (a.mask != nullptr) {
+            const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mk)[c >> 1];
+            if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+            if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+          }
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          ow[c >> 1] = *reinterpret_cast<uint32_t*>(&h);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) reinterpret_cast<uint4*>(a.out + pix * 32)[t] = o[t];
+      }
+    }
+  }
+  if (failed) atomicExch(a.error, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+}  // namespace cnn_tc
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool conv32_tc_available() { return encode_fn() != nullptr; }
+
+cudaError_t conv32_tc_set_attributes() {
+  return cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              cnn_tc::SMEM_PIPE);
+}
+
+// out = conv3x3_{32->32}(in) (+bias, ReLU | mask) on NHWC BF16 tensors of B x H x W x 32.
+cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
+                             const void* mask, int relu, int* error, cudaStream_t st) {
+  using namespace cnn_tc;
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  CUtensorMap map;
+  // dims (innermost first): channel, x, y, image; box: 8 channels x 130 pixels x 3 rows x 1
+  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+  const cuuint32_t box[4] = {8, HALO_W, 3, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = B * H * ((W + TILE - 1) / TILE);
+  const int grid = tiles < 2 * sms ? tiles : 2 * sms;   // two persistent CTAs per SM
+  TcArgs a{};
+  a.B = B; a.H = H; a.W = W;
+  a.wt = static_cast<const bf16*>(wt);
+  a.bias = bias;
+  a.out = static_cast<bf16*>(out);
+  a.mask = static_cast<const bf16*>(mask);
+  a.relu = relu;
+  a.error = error;
+  const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
+  a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
+  conv32_tc_kernel<<<grid, NTHR, SMEM_PIPE, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ils

@@ -59,6 +59,11 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                bool last, float2* spec_out, cudaStream_t stream);
 cudaError_t set_kernel_attributes();
 void record_cuda_error(const char* where, cudaError_t e);  // text for ils_last_error()
+// 32->32 channel conv3x3 on tcgen05 tensor cores (ils_cnn_tc.cu)
+bool conv32_tc_available();
+cudaError_t conv32_tc_set_attributes();
+cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
+                             const void* mask, int relu, int* error, cudaStream_t st);
 // max |a - b| over n floats as the bit pattern of a non-negative float, atomically max'ed into *out
 cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st);
 

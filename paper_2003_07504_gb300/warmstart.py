@@ -103,6 +103,14 @@ class WarmStartNet:
         _lib.check(_lib.lib().ils_cnn_backward(self._h, B, H, W, f.data_ptr(), grad_u0.data_ptr(), _stream_ptr()),
                    "ils_cnn_backward")
 
+    @property
+    def uses_tcgen05(self) -> bool:
+        return bool(_lib.lib().ils_cnn_uses_tcgen05(self._h))
+
+    def check(self) -> None:
+        """Raise if a tensor-core kernel's bounded wait gave up (ILS_ERR_TIMEOUT)."""
+        _lib.check(_lib.lib().ils_cnn_check(self._h), "ils_cnn_check")
+
     def zero_grad(self) -> None:
         _lib.check(_lib.lib().ils_cnn_zero_grad(self._h, _stream_ptr()), "ils_cnn_zero_grad")
 

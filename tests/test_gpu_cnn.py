@@ -135,3 +135,54 @@ def test_warm_smoother_paths(ws):
         assert fb and torch.equal(u, plan.smooth(f))
     sm.close()
     net.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 12, 128), (2, 9, 200), (1, 40, 384)])
+def test_tcgen05_layers_match_the_mma_sync_kernels(ws, monkeypatch, B, H, W):
+    # the 32 -> 32 layers on tcgen05 (TMA + tensor memory) against the mma.sync kernels:
+    # same BF16 inputs, FP32 accumulation in a different order -> BF16-rounding-level agreement
+    import torch
+    p = random_params(ws, 7)
+    f = torch.from_numpy(synth.preset_image(H, W, 3 * B, "small", 3 + W).reshape(B, 3, H, W)).cuda()
+    g = torch.from_numpy(synth.random_field((B, 3, H, W), seed=4)).cuda()
+    tc = ws.WarmStartNet(B * H * W, p)
+    monkeypatch.setenv("ILS_CNN_TC", "0")
+    ref = ws.WarmStartNet(B * H * W, p)
+    monkeypatch.delenv("ILS_CNN_TC")
+    assert tc.uses_tcgen05 and not ref.uses_tcgen05
+    outs = []
+    for net in (tc, ref):
+        u0 = net.forward(f)
+        net.zero_grad()
+        net.backward(f, g)
+        net.check()
+        outs.append((u0.cpu().numpy(), net.get_grads()))
+    assert rel_max(outs[0][0] - f.cpu().numpy(), outs[1][0] - f.cpu().numpy()) <= 2e-2
+    assert rel_max(outs[0][1], outs[1][1]) <= 2e-2 and rel_rms(outs[0][1], outs[1][1]) <= 5e-3
+    tc.close()
+    ref.close()
+
+
+def test_tcgen05_bounded_wait_reports_timeout(ws, monkeypatch):
+    # a poll limit of 1 makes the per-tile waits give up: the kernel must raise its flag,
+    # wait for its own copies, free tensor memory and return; the next call works normally
+    import torch
+    H, W = 16, 256
+    p = random_params(ws, 8)
+    f = torch.from_numpy(synth.preset_image(H, W, 3, "small", 1).reshape(1, 3, H, W)).cuda()
+    net = ws.WarmStartNet(H * W, p)
+    if not net.uses_tcgen05:
+        pytest.skip("tcgen05 path not available")
+    monkeypatch.setenv("ILS_TEST_TC_SPIN", "1")
+    net.forward(f)
+    from paper_2003_07504_gb300._lib import ILSError
+    with pytest.raises(ILSError) as e:
+        net.check()
+    assert e.value.name == "ILS_ERR_TIMEOUT"
+    monkeypatch.delenv("ILS_TEST_TC_SPIN")
+    u0 = net.forward(f)
+    net.check()
+    wts, bs = ws.unpack_params(p)
+    want, _ = O.warmstart_forward_bf16(f.cpu().numpy(), wts, bs)
+    assert rel_max(u0.cpu().numpy() - f.cpu().numpy(), want - f.cpu().numpy()) <= 2e-2
+    net.close()
