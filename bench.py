@@ -263,7 +263,7 @@ def warm_leg(torch, dev, steps, flush):
         ms = timed(lambda: p4.smooth(f, out=u4))
         out["plain_N4"] = {"fps": 1000.0 / ms, "ms": ms, "rms_to_converged": rms(u4)}
     for iters in (1, 2):
-        sm = ws.WarmSmoother(net, H, W, C, LAM, P, EPS, iters=iters, n_plain=N_ITERS, tau=1.0)
+        sm = ws.WarmSmoother(net, H, W, C, LAM, P, EPS, iters=iters, n_plain=N_ITERS, tau=ws.DEFAULT_TAU)
         u, fb, d = sm.smooth(f)
         res = {"rms_to_converged": rms(u), "fallback": fb, "last_change": d}
         res["ms"] = timed(lambda: sm.smooth(f, out=u))

@@ -101,7 +101,8 @@ std::string device_name() {
   return n;
 }
 
-// Cache file lines: "<device> <H> <W> <C> <row variant> <col variant>" (-1 = generic kernels).
+// Cache file lines: "<device> <H> <W> <C> <row variant> <col variant>": row variant 1000 + w
+// for warp-per-row entry w, else a block-per-strip entry (-1 = generic kernels).
 bool cache_lookup(const char* path, const std::string& dev, int H, int W, int C, int* rv, int* cv) {
   if (path == nullptr) return false;
   FILE* fp = std::fopen(path, "r");
@@ -163,11 +164,21 @@ ils_status autotune_class(BatchClass& c, const BatchFrame& proto) {
   int nr = fixed_row_variants(c.W / 2, rows, 7), nc = fixed_col_variants(c.H, cols, 7);
   rows[nr++] = -1;
   cols[nc++] = -1;
-  if (cache_lookup(path, dev, c.H, c.W, c.C, &rv, &cv) && std::find(rows, rows + nr, rv) != rows + nr &&
-      std::find(cols, cols + nc, cv) != cols + nc) {  // entries from another build are ignored
-    c.geo.fixed_row = rv;
-    c.geo.fixed_col = cv;
-    return ILS_OK;
+  int wl[8];
+  const int nwl = warp_row_variants(c.W / 2, wl, 8);
+  if (cache_lookup(path, dev, c.H, c.W, c.C, &rv, &cv) && std::find(cols, cols + nc, cv) != cols + nc) {
+    // entries from another build (unknown variant indices) are ignored
+    if (rv >= 1000 && std::find(wl, wl + nwl, rv - 1000) != wl + nwl) {
+      c.geo.warp_row = rv - 1000;
+      c.geo.fixed_col = cv;
+      return ILS_OK;
+    }
+    if (rv < 1000 && std::find(rows, rows + nr, rv) != rows + nr) {
+      c.geo.warp_row = -1;
+      c.geo.fixed_row = rv;
+      c.geo.fixed_col = cv;
+      return ILS_OK;
+    }
   }
   const size_t n = c.elems();
   float *f = nullptr, *u = nullptr;
@@ -180,14 +191,28 @@ ils_status autotune_class(BatchClass& c, const BatchFrame& proto) {
     cudaFree(f); cudaFree(u); cudaFree(s0); cudaFree(s1);
     return fail(e, "autotune allocation");
   }
+  // row candidates: every warp-per-row entry, then (warp kernels off) every block-per-strip
+  // entry and the generic kernels; encoded as w (>= 0) for warp entry w, -2 - i for row entry i
+  int wv[8];
+  const int nw = warp_row_variants(c.W / 2, wv, 8);
   Geometry g = c.geo;
   float best = 1e30f;
-  int best_r = g.fixed_row;
-  for (int i = 0; i < nr; ++i) {
-    g.fixed_row = rows[i];
+  int best_w = g.warp_row, best_r = g.fixed_row;
+  for (int i = 0; i < nw + nr; ++i) {
+    if (i < nw) {
+      g.warp_row = wv[i];
+    } else {
+      g.warp_row = -1;
+      g.fixed_row = rows[i - nw];
+    }
     const float ms = time_geometry(c, g, proto, f, u, s0, s1, st);
-    if (ms < best) { best = ms; best_r = rows[i]; }
+    if (ms < best) {
+      best = ms;
+      best_w = g.warp_row;
+      best_r = g.fixed_row;
+    }
   }
+  g.warp_row = best_w;
   g.fixed_row = best_r;
   best = 1e30f;
   int best_c = g.fixed_col;
@@ -196,12 +221,13 @@ ils_status autotune_class(BatchClass& c, const BatchFrame& proto) {
     const float ms = time_geometry(c, g, proto, f, u, s0, s1, st);
     if (ms < best) { best = ms; best_c = cols[i]; }
   }
+  c.geo.warp_row = best_w;
   c.geo.fixed_row = best_r;
   c.geo.fixed_col = best_c;
   cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   cudaFree(f); cudaFree(u); cudaFree(s0); cudaFree(s1);
-  cache_store(path, dev, c.H, c.W, c.C, best_r, best_c);
+  cache_store(path, dev, c.H, c.W, c.C, best_w >= 0 ? 1000 + best_w : best_r, best_c);
   return ILS_OK;
 }
 
@@ -424,7 +450,7 @@ ils_status ils_batch_destroy(ils_batch* b) {
 int ils_batch_kernel_choice(const ils_batch* b, int frame, int* row_variant, int* col_variant) {
   if (b == nullptr || frame < 0 || frame >= (int)b->fr.size()) return -1;
   const BatchClass& c = b->cls[b->fr[frame].cls];
-  if (row_variant) *row_variant = c.geo.fixed_row;
+  if (row_variant) *row_variant = c.geo.warp_row >= 0 ? 1000 + c.geo.warp_row : c.geo.fixed_row;
   if (col_variant) *col_variant = c.geo.fixed_col;
   return b->fr[frame].branch;
 }
