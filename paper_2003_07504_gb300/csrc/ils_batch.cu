@@ -74,13 +74,16 @@ cudaError_t enqueue_frame(const BatchClass& c, const BatchFrame& fr, float2* s0,
   cudaError_t e;
   if (fr.N == 0) return cudaMemcpyAsync(fr.u, fr.f, c.elems() * sizeof(float), cudaMemcpyDeviceToDevice, st);
   float2* sp[2] = {s0, s1};
+  ImageDesc d = c.desc;  // the frame's first launch in stream order, the rest chained (programmatic)
   for (int it = 0; it < fr.N; ++it) {
     float2* out = sp[it & 1];
     const float2* in = it == 0 ? nullptr : sp[(it - 1) & 1];
-    if ((e = launch_row_forward(c.desc, c.geo, t, fr.mp, fr.f, nullptr, in, out, nullptr, st))) return e;
-    if ((e = launch_col_solve(c.desc, c.geo, t, out, st))) return e;
+    d.pdl = it > 0 && pdl_enabled();
+    if ((e = launch_row_forward(d, c.geo, t, fr.mp, fr.f, nullptr, in, out, nullptr, st))) return e;
+    d.pdl = pdl_enabled();
+    if ((e = launch_col_solve(d, c.geo, t, out, st))) return e;
   }
-  return launch_row_inverse(c.desc, c.geo, t, sp[(fr.N - 1) & 1], fr.u, st);
+  return launch_row_inverse(d, c.geo, t, sp[(fr.N - 1) & 1], fr.u, st);
 }
 
 ils_status fail(cudaError_t e, const char* where) {

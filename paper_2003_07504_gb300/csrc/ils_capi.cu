@@ -126,18 +126,25 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
     return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
   }
   int slot = 0;
+  // programmatic dependent launch between this call's own kernels (not after the caller's
+  // work, and not when profiling events sit between the launches)
+  ImageDesc d = pl->desc;
+  const bool chain = !pl->profiling && pdl_enabled();
   for (int it = 0; it < pl->N; ++it) {
     float2* out = pl->spec[it & 1];
     const float2* in = it == 0 ? nullptr : pl->spec[(it - 1) & 1];
     float* ck = ckpt ? ckpt + (size_t)it * n : nullptr;
     if ((e = mark(pl, slot++, it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW, st))) return cuda_fail(e, "event");
-    if ((e = launch_row_forward(pl->desc, pl->geo, pl->tab, pl->mp, f, it == 0 ? u0 : nullptr, in, out, ck, st)))
+    d.pdl = chain && it > 0;
+    if ((e = launch_row_forward(d, pl->geo, pl->tab, pl->mp, f, it == 0 ? u0 : nullptr, in, out, ck, st)))
       return cuda_fail(e, "row pass launch");
     if ((e = mark(pl, slot++, ILS_KERNEL_COLUMN, st))) return cuda_fail(e, "event");
-    if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, out, st))) return cuda_fail(e, "column pass launch");
+    d.pdl = chain;
+    if ((e = launch_col_solve(d, pl->geo, pl->tab, out, st))) return cuda_fail(e, "column pass launch");
   }
   if ((e = mark(pl, slot++, ILS_KERNEL_ROW_INVERSE, st))) return cuda_fail(e, "event");
-  if ((e = launch_row_inverse(pl->desc, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st)))
+  d.pdl = chain;
+  if ((e = launch_row_inverse(d, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st)))
     return cuda_fail(e, "inverse row pass launch");
   if ((e = mark(pl, slot, -1, st))) return cuda_fail(e, "event");
   if (pl->profiling) {
@@ -156,6 +163,14 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
 }  // namespace
 
 namespace ils {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("ILS_PDL");
+    return e != nullptr && e[0] == '1';
+  }();
+  return on;
+}
+
 void record_cuda_error(const char* where, cudaError_t e) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
 }
@@ -334,17 +349,19 @@ ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, fl
   // spectrum of grad_u (a row pass with lambda = 0 is a plain forward row FFT), then r = A^-1 grad_u
   MuParams plain = pl->mp;
   plain.half_lambda = 0.0f;
-  if ((e = launch_row_forward(pl->desc, pl->geo, pl->tab, plain, grad_u, grad_u, nullptr, pl->spec[0], nullptr, st)))
+  ImageDesc d = pl->desc;  // first launch in caller order, the rest chained (programmatic)
+  if ((e = launch_row_forward(d, pl->geo, pl->tab, plain, grad_u, grad_u, nullptr, pl->spec[0], nullptr, st)))
     return cuda_fail(e, "row pass launch");
-  if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, pl->spec[0], st))) return cuda_fail(e, "column pass launch");
+  d.pdl = pdl_enabled();
+  if ((e = launch_col_solve(d, pl->geo, pl->tab, pl->spec[0], st))) return cuda_fail(e, "column pass launch");
   int cur = 0;
   for (int it = pl->N - 1; it >= 0; --it) {
     const bool last = it == 0;
-    if ((e = launch_row_adjoint(pl->desc, pl->geo, pl->tab, pl->mp, pl->spec[cur], ckpt + (size_t)it * n, grad_f,
+    if ((e = launch_row_adjoint(d, pl->geo, pl->tab, pl->mp, pl->spec[cur], ckpt + (size_t)it * n, grad_f,
                                 it == pl->N - 1, grad_u0, last, pl->spec[cur ^ 1], st)))
       return cuda_fail(e, "adjoint row pass launch");
     if (!last) {
-      if ((e = launch_col_solve(pl->desc, pl->geo, pl->tab, pl->spec[cur ^ 1], st)))
+      if ((e = launch_col_solve(d, pl->geo, pl->tab, pl->spec[cur ^ 1], st)))
         return cuda_fail(e, "column pass launch");
       cur ^= 1;
     }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "ils_fft.cuh"
 
 namespace ils {
@@ -14,6 +16,25 @@ struct MuParams {
   float a;       // p/2 - 1
   float half_lambda;
 };
+
+// 2^x and log2(x) on the special-function unit (PTX ex2.approx / lg2.approx, flush to
+// zero; relative error about 2^-22, far inside the smoothing's FP32 parity bar).
+__device__ __forceinline__ float sfu_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sfu_log2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Eq. 7: mu = c g - p g (g^2 + eps)^(p/2 - 1); g^2 + eps >= eps > 0, so no denormal inputs.
+__device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
+  const float t = fmaf(g, g, mp.eps);
+  return g * fmaf(-mp.p, sfu_exp2(mp.a * sfu_log2(t)), mp.c);
+}
 
 // Launch geometry picked by the host planner (validated before any launch).
 struct Geometry {
@@ -41,7 +62,39 @@ struct ImageDesc {
   int H, W, C;
   FftPlan planM;  // length W/2 (row FFT on packed complex rows)
   FftPlan planH;  // length H   (column FFT)
+  // Launch with programmatic dependent launch: set for every launch of a call except the
+  // first, i.e. when the previous work on the stream is this library's own kernel.
+  bool pdl = false;
 };
+
+// Programmatic dependent launch, device side.  Every ILS kernel lets the next grid be
+// scheduled as soon as all of its CTAs run (launch_dependents), and reads nothing that the
+// previous grid writes before griddep_wait() (which returns once that grid has completed
+// and its writes are visible; a no-op for a kernel launched without the attribute).
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Whether the kernels of one call are chained by programmatic dependent launch (ILS_PDL=1).
+// Off by default: on GB300 it measured 1% slower for a 1080p RGB frame and 3.6% slower for
+// 24 channels than plain stream order.
+bool pdl_enabled();
+
+// Kernel launch with the programmatic-stream-serialization attribute when `pdl`.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 bool make_fft_plan(int n, FftPlan* out);
 bool pick_geometry(int H, int W, Geometry* g);

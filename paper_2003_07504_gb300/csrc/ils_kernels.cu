@@ -22,12 +22,6 @@
 
 namespace ils {
 
-// Eq. 7: mu = c g - p g (g^2 + eps)^(p/2 - 1)
-__device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
-  const float t = fmaf(g, g, mp.eps);
-  const float w = exp2f(mp.a * __log2f(t));
-  return g * fmaf(-mp.p, w, mp.c);
-}
 
 __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (y >= H ? y - H : y); }
 
@@ -41,6 +35,8 @@ row_forward_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
                    const float* __restrict__ f, const float* __restrict__ u0,
                    const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
                    float* __restrict__ u_ckpt) {
+  griddep_launch();
+  griddep_wait();
   extern __shared__ float2 sm[];
   const int M = W >> 1;
   const int ch = blockIdx.y;
@@ -134,6 +130,8 @@ __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 col_solve_kernel(int H, int M, int G, FftPlan planH, const float2* __restrict__ twH,
                  const float* __restrict__ ax, const float* __restrict__ by, float scale,
                  float2* __restrict__ spec) {
+  griddep_launch();
+  griddep_wait();
   extern __shared__ float2 sm[];
   const int ch = blockIdx.y;
   const int k0 = blockIdx.x * G;
@@ -194,7 +192,7 @@ col_solve_kernel(int H, int M, int G, FftPlan planH, const float2* __restrict__ 
 __device__ __forceinline__ float g2_appb(float x, const MuParams& mp) {
   const float x2 = x * x;
   const float t = x2 + mp.eps;
-  const float w = exp2f((mp.a - 1.0f) * __log2f(t));
+  const float w = sfu_exp2((mp.a - 1.0f) * sfu_log2(t));
   return fmaf(-mp.p * w, fmaf(mp.p - 1.0f, x2, mp.eps), mp.c);
 }
 
@@ -203,6 +201,8 @@ __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW, MuParams mp,
                    const float2* __restrict__ spec_in, const float* __restrict__ u_n, float* __restrict__ fbar,
                    int fbar_first, float* __restrict__ gu0, int last, float2* __restrict__ spec_out) {
+  griddep_launch();
+  griddep_wait();
   extern __shared__ float2 sm[];
   const int M = W >> 1;
   const int ch = blockIdx.y;
@@ -299,6 +299,8 @@ template <int EPT>
 __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW,
                    const float2* __restrict__ spec, float* __restrict__ u) {
+  griddep_launch();
+  griddep_wait();
   extern __shared__ float2 sm[];
   const int M = W >> 1;
   const int ch = blockIdx.y;
@@ -404,14 +406,21 @@ bool pick_geometry(int H, int W, Geometry* g) {
   // Compile-time plans where one exists; ILS_FORCE_GENERIC=1 keeps the generic kernels
   // (used by the tests to cover both implementations on the same sizes).
   // ILS_ROW_IMPL=fixed|generic selects the block-per-strip or generic row kernels instead
-  // of the warp-per-row ones (tests compare the implementations on the same sizes).
+  // of the warp-per-row ones, ILS_ROW_IMPL=warp<k> the k-th warp-per-row variant of the
+  // length (tests compare the implementations on the same sizes).
   const char* force = getenv("ILS_FORCE_GENERIC");
   const bool generic = force != nullptr && force[0] == '1';
   const char* impl = getenv("ILS_ROW_IMPL");
   const bool no_warp = generic || (impl != nullptr && (impl[0] == 'f' || impl[0] == 'g'));
   const bool no_fixed = generic || (impl != nullptr && impl[0] == 'g');
-  int wv[4];
-  g->warp_row = (!no_warp && warp_row_variants(M, wv, 4) > 0) ? wv[0] : -1;
+  int wv[8];
+  const int nw = no_warp ? 0 : warp_row_variants(M, wv, 8);
+  int pick = 0;
+  if (impl != nullptr && impl[0] == 'w' && impl[1] == 'a' && impl[2] == 'r' && impl[3] == 'p') {
+    pick = atoi(impl + 4);
+    if (pick < 0 || pick >= nw) pick = 0;
+  }
+  g->warp_row = nw > 0 ? wv[pick] : -1;
   g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
   g->fixed_col = generic ? -1 : fixed_col_index(H);
   return true;
@@ -446,22 +455,11 @@ cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tabl
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   const int T = g.threads_row;
   const size_t S = g.smem_fwd;
-  if (g.ept_row == 16) {
-    if (spec_in == nullptr)
-      row_forward_kernel<16, true><<<grid, T, S, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, u0, nullptr,
-                                                           spec_out, u_ckpt);
-    else
-      row_forward_kernel<16, false><<<grid, T, S, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, nullptr,
-                                                            spec_in, spec_out, u_ckpt);
-  } else {
-    if (spec_in == nullptr)
-      row_forward_kernel<32, true><<<grid, T, S, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, u0, nullptr,
-                                                           spec_out, u_ckpt);
-    else
-      row_forward_kernel<32, false><<<grid, T, S, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, nullptr,
-                                                            spec_in, spec_out, u_ckpt);
-  }
-  return cudaGetLastError();
+  const bool first = spec_in == nullptr;
+  auto fn = g.ept_row == 16 ? (first ? row_forward_kernel<16, true> : row_forward_kernel<16, false>)
+                            : (first ? row_forward_kernel<32, true> : row_forward_kernel<32, false>);
+  return launch_k(d.pdl, fn, grid, T, S, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, first ? u0 : nullptr,
+                  spec_in, spec_out, u_ckpt);
 }
 
 cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables& t, float2* spec,
@@ -470,13 +468,9 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
   const int M = d.W / 2;
   dim3 grid((M + g.cols - 1) / g.cols, d.C);
   const float scale = 1.0f / ((float)d.H * (float)d.W);
-  if (g.ept_col == 16)
-    col_solve_kernel<16><<<grid, g.threads_col, g.smem_col, stream>>>(d.H, M, g.cols, d.planH, t.twH, t.ax, t.by,
-                                                                      scale, spec);
-  else
-    col_solve_kernel<32><<<grid, g.threads_col, g.smem_col, stream>>>(d.H, M, g.cols, d.planH, t.twH, t.ax, t.by,
-                                                                      scale, spec);
-  return cudaGetLastError();
+  auto fn = g.ept_col == 16 ? col_solve_kernel<16> : col_solve_kernel<32>;
+  return launch_k(d.pdl, fn, grid, g.threads_col, g.smem_col, stream, d.H, M, g.cols, d.planH, t.twH, t.ax, t.by, scale,
+                  spec);
 }
 
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
@@ -484,26 +478,17 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
   if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream);
   if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
-  if (g.ept_inv == 16)
-    row_inverse_kernel<16><<<grid, g.threads_inv, g.smem_inv, stream>>>(d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
-  else
-    row_inverse_kernel<32><<<grid, g.threads_inv, g.smem_inv, stream>>>(d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
-  return cudaGetLastError();
+  auto fn = g.ept_inv == 16 ? row_inverse_kernel<16> : row_inverse_kernel<32>;
+  return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
 }
 
 cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream) {
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
-  if (g.ept_row == 16)
-    row_adjoint_kernel<16><<<grid, g.threads_row, g.smem_fwd, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp,
-                                                                        spec_in, u_n, fbar, fbar_first, gu0, last,
-                                                                        spec_out);
-  else
-    row_adjoint_kernel<32><<<grid, g.threads_row, g.smem_fwd, stream>>>(d.H, d.W, g.rows_fwd, d.planM, t.twW, mp,
-                                                                        spec_in, u_n, fbar, fbar_first, gu0, last,
-                                                                        spec_out);
-  return cudaGetLastError();
+  auto fn = g.ept_row == 16 ? row_adjoint_kernel<16> : row_adjoint_kernel<32>;
+  return launch_k(d.pdl, fn, grid, g.threads_row, g.smem_fwd, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, spec_in,
+                  u_n, fbar, (int)fbar_first, gu0, (int)last, spec_out);
 }
 
 }  // namespace ils

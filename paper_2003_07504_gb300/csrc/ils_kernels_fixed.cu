@@ -23,12 +23,6 @@ __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (
 
 
 
-// Eq. 7: mu = c g - p g (g^2 + eps)^(p/2 - 1)
-__device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
-  const float t = fmaf(g, g, mp.eps);
-  const float w = exp2f(mp.a * __log2f(t));
-  return g * fmaf(-mp.p, w, mp.c);
-}
 
 // In place on nrows smem rows of packed half spectra X (slot 0 = (X[0], X[M])): replace X
 // by Z, the half-length sequence whose unnormalized inverse FFT is W (x[2m] + i x[2m+1]):
@@ -75,6 +69,8 @@ template <class PL, int G, int MINB>
 __global__ void __launch_bounds__(G * PL::TPS, MINB)
 col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __restrict__ ax,
                  const float* __restrict__ by, float scale, float2* __restrict__ spec) {
+  griddep_launch();
+  griddep_wait();
   constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = N / R0, NS1 = N / R1, NSL = N / RL;
   extern __shared__ float2 sm[];
@@ -300,6 +296,8 @@ __global__ void __launch_bounds__((ROWS + 2) * PL::TPS, 1)
 row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                      const float* __restrict__ u0, const float2* __restrict__ spec_in,
                      float2* __restrict__ spec_out, float* __restrict__ u_ckpt) {
+  griddep_launch();
+  griddep_wait();
   constexpr int M = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL, TPS = PL::TPS;
   constexpr int NS0 = M / R0, NS1 = M / R1, NSL = M / RL;
   constexpr int P = M / 2 + 1;
@@ -439,6 +437,8 @@ template <class PL, int ROWS>
 __global__ void __launch_bounds__(ROWS * PL::TPS, 1)
 row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ spec,
                      float* __restrict__ u) {
+  griddep_launch();
+  griddep_wait();
   constexpr int M = PL::N, TPS = PL::TPS;
   extern __shared__ float2 sm[];
   const int strips = (H + ROWS - 1) / ROWS;
@@ -572,8 +572,7 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
   const size_t smem = row_smem(r.rows_fwd + 2, r.M);
   const int tiles = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
   RowFwdFn fn = spec_in == nullptr ? r.first : r.later;
-  fn<<<tiles, threads, smem, stream>>>(d.H, d.C, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
-  return cudaGetLastError();
+  return launch_k(d.pdl, fn, tiles, threads, smem, stream, d.H, d.C, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }
 
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
@@ -582,8 +581,7 @@ cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, cons
   const int threads = r.rows_inv * r.tps;
   const size_t smem = row_smem(r.rows_inv, r.M);
   const int tiles = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
-  r.inv<<<tiles, threads, smem, stream>>>(d.H, d.C, t.twW, spec, u);
-  return cudaGetLastError();
+  return launch_k(d.pdl, r.inv, tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u);
 }
 
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream) {
@@ -593,8 +591,7 @@ cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2
   const size_t smem = (size_t)smem_elems(c.H * c.G) * sizeof(float2);
   const int tiles = (M + c.G - 1) / c.G * d.C;
   const float scale = 1.0f / ((float)d.H * (float)d.W);
-  c.fn<<<tiles, threads, smem, stream>>>(M, d.C, t.twH, t.ax, t.by, scale, spec);
-  return cudaGetLastError();
+  return launch_k(d.pdl, c.fn, tiles, threads, smem, stream, M, d.C, t.twH, t.ax, t.by, scale, spec);
 }
 
 }  // namespace ils

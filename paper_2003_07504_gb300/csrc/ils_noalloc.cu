@@ -137,7 +137,9 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
   for (int it = 0; it < N; ++it) {
     float2* out = spec[it & 1];
     const float2* in = it == 0 ? nullptr : spec[(it - 1) & 1];
+    d.pdl = it > 0 && pdl_enabled();  // after the table kernel: stream order; then chained (programmatic)
     if ((e = launch_row_forward(d, g, t, mp, f, nullptr, in, out, nullptr, st))) return ILS_ERR_CUDA;
+    d.pdl = pdl_enabled();
     if ((e = launch_col_solve(d, g, t, out, st))) return ILS_ERR_CUDA;
   }
   if ((e = launch_row_inverse(d, g, t, spec[(N - 1) & 1], u, st))) return ILS_ERR_CUDA;

@@ -23,12 +23,13 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (y >= H ? y - H : y); }
 
-// Eq. 7: mu = c g - p g (g^2 + eps)^(p/2 - 1)
-__device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
-  const float t = fmaf(g, g, mp.eps);
-  const float w = exp2f(mp.a * __log2f(t));
-  return g * fmaf(-mp.p, w, mp.c);
+// 16-byte asynchronous global -> shared copies (cp.async; completion waited per thread).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 
 template <int L>
 struct WarpRow {
@@ -148,11 +149,19 @@ struct WarpRow {
 // Fused row pass: CTA = ROWS + 2 warps over rows y0-1 .. y0+ROWS (periodic); warp w holds
 // strip row w in buffer w.  FIRST: u^0 rows are read from u0 (or f); otherwise rebuilt by the
 // inverse transform of spec_in.  Then warp o+1 computes r for output row o and transforms it.
-template <int L, int ROWS, bool FIRST>
+// SHARED: each mu is evaluated once (mu_y of a row boundary passed between warps through
+// shared memory, mu_x between lanes by shuffle; three CTA barriers); otherwise every warp
+// evaluates the mu of all four gradients of each of its pixels and of the left neighbour
+// (two barriers, no cross-warp data beyond the strip rows).
+// STAGE (with SHARED): the f rows of the output rows are copied to shared memory
+// asynchronously at the start (behind the inverse transforms) instead of being loaded in
+// the stencil.
+template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED>
 __global__ void __launch_bounds__((ROWS + 2) * 32, (ROWS + 2) * 32 <= 256 ? 2 : 1)
 row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                     const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
                     float* __restrict__ u_ckpt) {
+  griddep_launch();
   using WR = WarpRow<L>;
   constexpr int M = WR::M;
   extern __shared__ float2 sm[];
@@ -164,6 +173,20 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   const size_t plane = (size_t)H * M;
   float2* buf = sm + w * WR::BUF;
   auto U = [&](int row, int m) -> float2 { return sm[row * WR::BUF + m]; };
+  const int o = w - 1;  // output row of this warp
+  const bool out_live = o >= 0 && o < nout;
+  float2* fst = sm + (ROWS + 2) * WR::BUF + max(o, 0) * M;  // staged f row (STAGE)
+  if (STAGE && out_live && mp.half_lambda != 0.0f) {
+    const float2* src = reinterpret_cast<const float2*>(f) + ch * plane + (size_t)(y0 + o) * M;
+    if ((reinterpret_cast<size_t>(src) & 15) == 0) {
+#pragma unroll
+      for (int q = 0; q < M / 64; ++q) cp_async16(fst + 2 * (lane + 32 * q), src + 2 * (lane + 32 * q));
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) fst[lane + 32 * n2] = src[lane + 32 * n2];
+    }
+  }
+  griddep_wait();  // f is never written by this library's kernels; the spectrum is
   if (w < nout + 2) {
     const int yy = wrap_row(y0 - 1 + w, H);
     if (FIRST) {
@@ -175,20 +198,27 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
     }
   }
   __syncthreads();
-  const int o = w - 1;  // output row of this warp
-  const bool out_live = o >= 0 && o < nout;
   float2 v[L];
-  if (out_live) {
-    const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
-    const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
-    if (mp.half_lambda == 0.0f) {  // lambda = 0 (or a plain row FFT): r = f
+  if (mp.half_lambda == 0.0f) {  // lambda = 0 (or a plain row FFT): r = f
+    if (out_live) {
+      const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
+      const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) {
         const int m = lane + 32 * n2;
         v[n2] = fr[m];
         if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = U(w, m);
       }
-    } else {
+      WR::forward_row_to_global(v, spec_out + rowoff, buf, lane, twW);
+    }
+    return;
+  }
+  if constexpr (!SHARED) {
+    // Stencil (Eq. 7 and the divergence of Eq. 9's numerator) per pixel pair from the
+    // strip rows alone: mu of the pair's four gradients and of the left neighbour's.
+    if (out_live) {
+      const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
+      const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) {
         const int m = lane + 32 * n2;
@@ -210,15 +240,77 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
         if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
       }
     }
+    __syncthreads();
+    if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+    return;
+  }
+  // Stencil (Eq. 7 and the divergence of Eq. 9's numerator), each mu evaluated once:
+  // S1: warp b <= nout computes mu_y at the boundary between strip rows b and b+1.
+  float2 Y[L];
+  if (w <= nout) {
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = lane + 32 * n2;
+      const float2 a = U(w, m), b = U(w + 1, m);
+      Y[n2] = c2(mu_eq7(b.x - a.x, mp), mu_eq7(b.y - a.y, mp));
+    }
+  }
+  if (STAGE) cp_async_wait_all();
+  __syncthreads();
+  // S2: an output warp forms r = f + lambda/2 (div_x mu_x - mu_y(own boundary)) from its own
+  // row, mu_x once per pixel; x neighbours move between lanes by shuffle, so each lane reads
+  // and then overwrites only its own pairs (mu_y of its boundary replaces u in place).
+  if (w <= nout) {
+    const size_t rowoff = ch * plane + (size_t)(y0 + max(o, 0)) * M;
+    const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
+    float2 cn = buf[lane];
+    const float u_first = __shfl_sync(kFull, cn.x, 0);  // pixel 0: right neighbour of pixel 2M-1
+    float carry = 0.0f;  // mu_x of the pixel left of lane 0's pair
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = lane + 32 * n2;
+      const float2 c = cn;
+      if (n2 + 1 < L) cn = buf[m + 32];
+      if (out_live) {
+        const float nx_in = __shfl_down_sync(kFull, c.x, 1);
+        const float nx_wrap = __shfl_sync(kFull, n2 + 1 < L ? cn.x : u_first, 0);
+        const float nx = lane == 31 ? nx_wrap : nx_in;  // u at pixel 2m+2
+        const float mx_c = mu_eq7(c.y - c.x, mp);     // mu_x at pixel 2m
+        const float mx_r = mu_eq7(nx - c.y, mp);      // mu_x at pixel 2m+1
+        const float up = __shfl_up_sync(kFull, mx_r, 1);
+        const float mx_l = lane == 0 ? carry : up;    // mu_x at pixel 2m-1
+        carry = __shfl_sync(kFull, mx_r, 31);
+        const float2 fv = STAGE ? fst[m] : fr[m];
+        v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) - Y[n2].x, fv.x),
+                   fmaf(mp.half_lambda, (mx_c - mx_r) - Y[n2].y, fv.y));
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
+      }
+      buf[m] = Y[n2];
+    }
+    // lane 0's first pair: the left neighbour of pixel 0 is pixel 2M-1, finished last
+    if (out_live && lane == 0) v[0].x = fmaf(mp.half_lambda, carry, v[0].x);
   }
   __syncthreads();
-  if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+  // S3: add mu_y of the boundary above (written by warp w-1); that row buffer has no other
+  // reader now, so it becomes this warp's scratch for the forward transform.
+  if (out_live) {
+    const float2* above = sm + (w - 1) * WR::BUF;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const float2 t = above[lane + 32 * n2];
+      v[n2] = c2(fmaf(mp.half_lambda, t.x, v[n2].x), fmaf(mp.half_lambda, t.y, v[n2].y));
+    }
+    __syncwarp();
+    WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, sm + (w - 1) * WR::BUF, lane, twW);
+  }
 }
 
 // Final inverse row pass: one warp per row, ROWS rows per CTA.
 template <int L, int ROWS>
 __global__ void __launch_bounds__(ROWS * 32)
 row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u) {
+  griddep_launch();
+  griddep_wait();
   using WR = WarpRow<L>;
   constexpr int M = WR::M;
   extern __shared__ float2 sm[];
@@ -235,24 +327,31 @@ using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*,
 using InvFn = void (*)(int, const float2*, const float2*, float*);
 
 struct WarpRowEntry {
-  int M, rows_fwd, rows_inv, buf;
+  int M, rows_fwd, rows_inv, buf, stage;
   FwdFn first, later;
   InvFn inv;
 };
 
-template <int L, int RF, int RI>
+// STAGE only where the staged rows still leave room for two CTAs per SM.
+template <int L, int RF, int RI, bool STAGE, bool SHARED>
 constexpr WarpRowEntry warp_entry() {
-  return WarpRowEntry{32 * L, RF, RI, WarpRow<L>::BUF, row_warp_fwd_kernel<L, RF, true>,
-                      row_warp_fwd_kernel<L, RF, false>, row_warp_inv_kernel<L, RI>};
+  static_assert(SHARED || !STAGE, "f staging is part of the shared-mu stencil");
+  return WarpRowEntry{32 * L, RF, RI, WarpRow<L>::BUF, STAGE ? RF * 32 * L : 0,
+                      row_warp_fwd_kernel<L, RF, true, STAGE, SHARED>, row_warp_fwd_kernel<L, RF, false, STAGE, SHARED>,
+                      row_warp_inv_kernel<L, RI>};
 }
 
+// The first entry of a length is its default; the others are autotune alternatives.
 const WarpRowEntry kWarpRows[] = {
-    warp_entry<4, 14, 16>(),   // W = 256
-    warp_entry<10, 14, 16>(),  // W = 640
-    warp_entry<20, 6, 8>(),    // W = 1280
-    warp_entry<30, 6, 8>(),    // W = 1920
-    warp_entry<32, 6, 8>(),    // W = 2048
-    warp_entry<30, 14, 8>(),   // W = 1920, taller strips (autotune alternative)
+    warp_entry<4, 14, 16, true, true>(),     // W = 256
+    warp_entry<10, 14, 16, true, true>(),    // W = 640
+    warp_entry<20, 6, 8, true, true>(),      // W = 1280
+    warp_entry<30, 6, 8, true, true>(),      // W = 1920
+    warp_entry<32, 6, 8, false, true>(),     // W = 2048
+    warp_entry<30, 14, 8, false, true>(),    // W = 1920, taller strips
+    warp_entry<30, 6, 8, false, false>(),    // W = 1920, per-pair stencil
+    warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
+    warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
 };
 
 }  // namespace
@@ -267,7 +366,8 @@ int warp_row_variants(int M, int* idx, int max) {
 cudaError_t warp_set_attributes() {
   cudaError_t e;
   for (const WarpRowEntry& r : kWarpRows) {
-    const int sf = (r.rows_fwd + 2) * r.buf * (int)sizeof(float2), si = r.rows_inv * r.buf * (int)sizeof(float2);
+    const int sf = ((r.rows_fwd + 2) * r.buf + r.stage) * (int)sizeof(float2);
+    const int si = r.rows_inv * r.buf * (int)sizeof(float2);
     if ((e = cudaFuncSetAttribute(r.first, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     if ((e = cudaFuncSetAttribute(r.later, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
@@ -280,10 +380,9 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
                              cudaStream_t stream) {
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  const size_t smem = (size_t)(r.rows_fwd + 2) * r.buf * sizeof(float2);
+  const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage) * sizeof(float2);
   FwdFn fn = spec_in == nullptr ? r.first : r.later;
-  fn<<<blocks, (r.rows_fwd + 2) * 32, smem, stream>>>(d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
-  return cudaGetLastError();
+  return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }
 
 cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
@@ -291,8 +390,7 @@ cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
   const size_t smem = (size_t)r.rows_inv * r.buf * sizeof(float2);
-  r.inv<<<blocks, r.rows_inv * 32, smem, stream>>>(d.H, t.twW, spec, u);
-  return cudaGetLastError();
+  return launch_k(d.pdl, r.inv, blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u);
 }
 
 }  // namespace ils
