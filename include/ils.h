@@ -197,6 +197,14 @@ ils_status ils_cnn_get_grads(const ils_cnn* net, float* grads, long long count);
 /* u0 = f + net(f) (f, u0 device, non-overlapping).  Keeps the activations for backward. */
 ils_status ils_cnn_forward(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);
 
+/* u0 = f + net(f) for inference (no activations kept; the last forward's activations are
+ * overwritten).  With the tcgen05 kernels in use it runs as two fused kernels, layers 1-3
+ * and 4-6, whose hidden activations stay on chip except the one 32-channel map between
+ * them; otherwise it is ils_cnn_forward.  Same numerics as ils_cnn_forward (BF16 inputs,
+ * weights and hidden activations, FP32 accumulation); results agree up to FP32
+ * accumulation order.  f, u0: device B x 3 x H x W FP32, non-overlapping. */
+ils_status ils_cnn_infer(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);
+
 /* Accumulate dL/dparams given dL/du0 (device, B x 3 x H x W), using the activations of
  * the last forward call, which must have been on the same f and shape. */
 ils_status ils_cnn_backward(ils_cnn* net, int B, int H, int W, const float* f, const float* grad_u0, void* stream);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "ils_cnn_get_grads": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
     "ils_cnn_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "ils_cnn_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "ils_cnn_infer": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "ils_cnn_zero_grad": (c_int, [c_void_p, c_void_p]),
     "ils_cnn_uses_tcgen05": (c_int, [c_void_p]),
     "ils_cnn_check": (c_int, [c_void_p]),

@@ -529,6 +529,7 @@ ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
   const char* tcenv = getenv("ILS_CNN_TC");
   n->tc = ils::conv32_tc_available() && !(tcenv != nullptr && tcenv[0] == '0');
   if (e == cudaSuccess && n->tc) e = ils::conv32_tc_set_attributes();
+  if (e == cudaSuccess && n->tc) e = ils::warm_fused_set_attributes();
   if (e == cudaSuccess) {
     cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)conv_smem(false, 4));
@@ -655,6 +656,21 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   conv_fwd_kernel<false, 1, true><<<grid, NTHREADS, conv_smem(false, 1), st>>>(z);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn forward launch");
+}
+
+// u0 = f + net(f), inference only: two fused tcgen05 kernels (layers 1-3 and 4-6, the
+// 32-channel map between them in act[2]) or, without tcgen05, the layer-by-layer forward.
+ils_status ils_cnn_infer(ils_cnn* n, int B, int H, int W, const float* f, float* u0, void* stream) {
+  if (!cnn_shape_ok(n, B, H, W) || f == nullptr || u0 == nullptr || f == u0 || !n->packed) return ILS_ERR_INVALID_ARG;
+  if (!n->tc) return ils_cnn_forward(n, B, H, W, f, u0, stream);
+  const void* w[kLayers];
+  const float* bias[kLayers];
+  for (int l = 0; l < kLayers; ++l) {
+    w[l] = n->wf[l];
+    bias[l] = n->b[l];
+  }
+  cudaError_t e = ils::launch_warm_fused(B, H, W, f, n->act[2], u0, w, bias, n->err, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ILS_OK : cnn_fail(e, "fused inference launch");
 }
 
 // Waits for the device and reports (then clears) a timeout raised by a tensor-core kernel.

@@ -24,6 +24,7 @@
 #include <stdlib.h>
 
 #include "ils_internal.h"
+#include "ils_tc.cuh"
 
 namespace ils {
 namespace cnn_tc {
@@ -37,65 +38,21 @@ constexpr int A_BYTES = 4 * PLANE;         // 25088
 constexpr int TMA_BYTES = 4 * 3 * HALO_W * 16;  // 24960 bytes delivered per tile
 constexpr int B_CHUNKS = 36;               // K = 288 = 36 chunks of 8
 constexpr int B_BYTES = B_CHUNKS * 32 * 16;  // 18432
-constexpr int SMEM_BYTES = A_BYTES + B_BYTES + 64;
-constexpr uint32_t kSpinLimit = 1u << 22;
+using tc::kSpinLimit;
+using tc::mbar_arrive;
+using tc::mbar_expect_tx;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::saddr;
+using tc::smem_desc;
+using tc::tma_load_4d;
 
-__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: true when the phase completed, false after `limit` polls
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kSpinLimit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 | version 1 << 46,
-// no swizzle (layout type 0 in bits 61-63).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B
-// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
-// M >> 4 in bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc = tc::idesc_bf16(128, 32);
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(tmem_d), "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate));
+  tc::mma_f16(tmem_d, da, db, kIdesc, accumulate);
 }
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
+using tc::mma_commit;
 
 struct TcArgs {
   int B, H, W;
@@ -111,10 +68,6 @@ struct TcArgs {
 constexpr int STAGES = 3;                               // input tiles in flight
 constexpr int SMEM_PIPE = STAGES * A_BYTES + B_BYTES + 128;
 constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // Persistent, warp-specialized pipeline.  Tile i uses input stage i % STAGES and
 // accumulator i % 2 (32 tensor-memory columns each).  Barriers (phase parity from the
@@ -295,6 +248,19 @@ EncodeTiledFn encode_fn() {
 
 bool conv32_tc_available() { return encode_fn() != nullptr; }
 
+bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return false;
+  // dims (innermost first): channel, x, y, image; box: 8 channels x box_x pixels x box_y rows x 1
+  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+  const cuuint32_t box[4] = {8, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(act), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t conv32_tc_set_attributes() {
   return cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               cnn_tc::SMEM_PIPE);
@@ -304,18 +270,9 @@ cudaError_t conv32_tc_set_attributes() {
 cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
                              const void* mask, int relu, int* error, cudaStream_t st) {
   using namespace cnn_tc;
-  EncodeTiledFn enc = encode_fn();
-  if (enc == nullptr) return cudaErrorNotSupported;
+  if (encode_fn() == nullptr) return cudaErrorNotSupported;
   CUtensorMap map;
-  // dims (innermost first): channel, x, y, image; box: 8 channels x 130 pixels x 3 rows x 1
-  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
-  const cuuint32_t box[4] = {8, HALO_W, 3, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (!make_nhwc32_map(&map, in, B, H, W, HALO_W, 3)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -117,6 +117,10 @@ bool conv32_tc_available();
 cudaError_t conv32_tc_set_attributes();
 cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
                              const void* mask, int relu, int* error, cudaStream_t st);
+// warm-start network inference as two fused tcgen05 kernels (ils_cnn_fused.cu)
+cudaError_t warm_fused_set_attributes();
+cudaError_t launch_warm_fused(int B, int H, int W, const float* f, void* act, float* u0, const void* const* w,
+                              const float* const* bias, int* error, cudaStream_t st);
 // max |a - b| over n floats as the bit pattern of a non-negative float, atomically max'ed into *out
 cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st);
 

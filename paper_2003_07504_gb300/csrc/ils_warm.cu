@@ -79,7 +79,7 @@ ils_status ils_warm_smooth(ils_warm* w, const float* f, float* u, int* fallback_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)w->C * w->H * w->W;
   ils_status s;
-  if ((s = ils_cnn_forward(w->net, w->C / 3, w->H, w->W, f, w->u0, stream))) return s;
+  if ((s = ils_cnn_infer(w->net, w->C / 3, w->H, w->W, f, w->u0, stream))) return s;
   if ((s = ils_smooth_checkpointed(w->warm, f, w->u0, u, w->ckpt, stream))) return s;
   cudaError_t e;
   if ((e = cudaMemsetAsync(w->delta_dev, 0, 4, st)) ||

@@ -101,6 +101,14 @@ class WarmStartNet:
                    "ils_cnn_forward")
         return out
 
+    def infer(self, f: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """u0 = f + net(f) without keeping activations (two fused tensor-core kernels)."""
+        B, H, W = self._shape(f)
+        out = torch.empty_like(f) if out is None else out
+        _lib.check(_lib.lib().ils_cnn_infer(self._h, B, H, W, f.data_ptr(), out.data_ptr(), _stream_ptr()),
+                   "ils_cnn_infer")
+        return out
+
     def backward(self, f: torch.Tensor, grad_u0: torch.Tensor) -> None:
         B, H, W = self._shape(f)
         self._shape(grad_u0)

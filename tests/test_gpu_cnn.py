@@ -121,7 +121,7 @@ def test_warm_smoother_paths(ws):
     p = random_params(ws, 4, last_scale=1e-2)
     f = torch.from_numpy(synth.preset_image(H, W, 3, "small", 12)).cuda()
     net = ws.WarmStartNet(H * W, p)
-    u0 = net.forward(f.view(1, 3, H, W)).view(3, H, W)
+    u0 = net.infer(f.view(1, 3, H, W)).view(3, H, W)  # the smoother's own network call
     for iters in (1, 2):
         sm = ws.WarmSmoother(net, H, W, 3, iters=iters, tau=float("inf"))
         u, fb, d = sm.smooth(f)
@@ -181,6 +181,77 @@ def test_tcgen05_bounded_wait_reports_timeout(ws, monkeypatch):
     assert e.value.name == "ILS_ERR_TIMEOUT"
     monkeypatch.delenv("ILS_TEST_TC_SPIN")
     u0 = net.forward(f)
+    net.check()
+    wts, bs = ws.unpack_params(p)
+    want, _ = O.warmstart_forward_bf16(f.cpu().numpy(), wts, bs)
+    assert rel_max(u0.cpu().numpy() - f.cpu().numpy(), want - f.cpu().numpy()) <= 2e-2
+    net.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 12, 122), (1, 25, 250), (2, 40, 300), (1, 13, 5), (1, 1, 130)])
+def test_fused_inference_matches_oracle(ws, B, H, W):
+    # two fused tcgen05 kernels (layers 1-3, 4-6): one tile, ragged tiles in x and y, several
+    # images, a single narrow tile, a single row
+    import torch
+    p = random_params(ws, 11)
+    f = synth.preset_image(H, W, 3 * B, "small", 7 * H + W).reshape(B, 3, H, W)
+    net = ws.WarmStartNet(B * H * W, p)
+    u0 = net.infer(torch.from_numpy(f).cuda()).cpu().numpy()
+    net.check()
+    wts, bs = ws.unpack_params(p)
+    want, _ = O.warmstart_forward_bf16(f, wts, bs)
+    assert rel_max(u0 - f, want - f) <= 2e-2 and rel_rms(u0 - f, want - f) <= 5e-3
+    net.close()
+
+
+def test_fused_inference_matches_layer_kernels_at_1080p(ws):
+    # full-size frame: fused inference against the layer-by-layer forward (same BF16 rounding
+    # points, FP32 accumulation in another order) with the trained weights when present
+    import os
+    import torch
+    H, W = 1080, 1920
+    p = ws.load_params(ws.DEFAULT_WEIGHTS) if os.path.exists(ws.DEFAULT_WEIGHTS) else random_params(ws, 12)
+    f = torch.from_numpy(synth.preset_image(H, W, 3, "hd", 31).reshape(1, 3, H, W)).cuda()
+    net = ws.WarmStartNet(H * W, p)
+    a = net.infer(f)
+    b = net.forward(f)
+    net.check()
+    d = (a - f).double().cpu().numpy(), (b - f).double().cpu().numpy()
+    assert rel_max(d[0], d[1]) <= 2e-2 and rel_rms(d[0], d[1]) <= 5e-3
+    # sampled pixels against the oracle on 20 x 20 windows (the receptive field is 13 x 13)
+    wts, bs = ws.unpack_params(p)
+    fh = f.cpu().numpy()
+    for (y, x) in [(0, 0), (500, 960), (1060, 1900), (37, 1911), (1075, 3)]:
+        y0, x0 = max(0, y - 6), max(0, x - 6)
+        win = fh[:, :, y0:y0 + 20, x0:x0 + 20]
+        want, _ = O.warmstart_forward_bf16(win, wts, bs)
+        yy, xx = y - y0, x - x0
+        got = a[0, :, y, x].cpu().numpy()
+        # only pixels whose 13 x 13 receptive field lies inside the window or the image edge
+        ok_y = (y < 6 or yy >= 6) and (y >= H - 6 or yy + 6 < win.shape[2])
+        ok_x = (x < 6 or xx >= 6) and (x >= W - 6 or xx + 6 < win.shape[3])
+        if ok_y and ok_x:
+            scale = max(1e-6, float(np.abs(want - win).max()))
+            assert float(np.abs(got - want[0, :, yy, xx]).max()) <= 2e-2 * scale, (y, x)
+    net.close()
+
+
+def test_fused_inference_bounded_wait_reports_timeout(ws, monkeypatch):
+    import torch
+    H, W = 30, 260
+    p = random_params(ws, 13)
+    f = torch.from_numpy(synth.preset_image(H, W, 3, "small", 2).reshape(1, 3, H, W)).cuda()
+    net = ws.WarmStartNet(H * W, p)
+    if not net.uses_tcgen05:
+        pytest.skip("tcgen05 path not available")
+    monkeypatch.setenv("ILS_TEST_TC_SPIN", "1")
+    net.infer(f)
+    from paper_2003_07504_gb300._lib import ILSError
+    with pytest.raises(ILSError) as e:
+        net.check()
+    assert e.value.name == "ILS_ERR_TIMEOUT"
+    monkeypatch.delenv("ILS_TEST_TC_SPIN")
+    u0 = net.infer(f)
     net.check()
     wts, bs = ws.unpack_params(p)
     want, _ = O.warmstart_forward_bf16(f.cpu().numpy(), wts, bs)
