@@ -86,14 +86,23 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
     const int k = k0 + g;
     const bool live = k < M;
     float2* col = spec + (size_t)ch * N * M + (live ? k : 0);
-    // coalesced copy of the tile (G complex per row) into smem, then forward stage 0 (Ns = 1)
+    // coalesced copy of the tile (G complex per row) into smem with every load of a thread
+    // in flight at once (compile-time trip count), then forward stage 0 (Ns = 1)
     {
       const float2* tilep = spec + (size_t)ch * N * M + k0;
-      __syncthreads();
-      for (int w = t; w < N * G; w += blockDim.x) {
-        const int l = w / G;
-        const int gg = w - l * G;
-        sm[smem_idx(w)] = (k0 + gg < M) ? tilep[(size_t)l * M + gg] : c2(0.f, 0.f);
+      constexpr int T = G * PL::TPS, PER = (N * G + T - 1) / T, BATCH = PER < 24 ? PER : 24;
+#pragma unroll
+      for (int q0 = 0; q0 < PER; q0 += BATCH) {
+        float2 ld[BATCH];
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+          const int w = t + (q0 + q) * T;
+          const int l = w / G, gg = w - (w / G) * G;
+          ld[q] = (q0 + q < PER && w < N * G && k0 + gg < M) ? tilep[(size_t)l * M + gg] : c2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q)
+          if (q0 + q < PER && t + (q0 + q) * T < N * G) sm[smem_idx(t + (q0 + q) * T)] = ld[q];
       }
       __syncthreads();
       float2 v[R0];

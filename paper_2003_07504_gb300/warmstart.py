@@ -263,7 +263,29 @@ def main(argv=None):
     ap.add_argument("--n-crops", type=int, default=20000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--smooth", metavar="HxW", default=None,
+                    help="instead of training: warm-started smoothing (1 ILS iteration) of a synthetic RGB "
+                         "frame of this size with the weights in --out, repeated --repeat times")
+    ap.add_argument("--repeat", type=int, default=3)
     a = ap.parse_args(argv)
+    if a.smooth is not None:
+        from . import synth
+        H, W = (int(v) for v in a.smooth.lower().split("x"))
+        f = torch.from_numpy(synth.preset_image(H, W, 3, "hd", a.seed)).cuda()
+        net = WarmStartNet(H * W, load_params(a.out))
+        sm = WarmSmoother(net, H, W, 3, iters=1)
+        times = []
+        for _ in range(a.repeat):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            u, fb, d = sm.smooth(f)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        net.check()
+        print(json.dumps({"frame": [3, H, W], "fallback": fb, "last_change": d, "seconds": times}))
+        sm.close()
+        net.close()
+        return
     t0 = time.time()
     params, losses = train(steps=a.steps, batch=a.batch, crop=a.crop, lr=a.lr, n_crops=a.n_crops, seed=a.seed)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
