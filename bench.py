@@ -52,6 +52,25 @@ def bytes_model(H, W, C, N):
     return per, total
 
 
+def load_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when there is
+    none or the kernel's sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "row_pass_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel") != kernel:
+            return None
+        for src, digest in d["source_sha256"].items():
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return None
+        return d["traffic_bytes_per_launch"] / 1e9
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -390,7 +409,8 @@ def run_ours(args):
                        "l2": "flushed (512 MiB write) between timed steps",
                        "mpix_per_s": fps * hh * ww / 1e6},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": load_traffic(dom),
+                         "traffic_unit": "GB per launch (ncu dram read + write)",
                          "launch_timing": "events around every launch, second loop of the same K steps",
                          "algorithmic_bytes_per_launch": per_kind[dom],
                          "whole_step_gbs": whole, "whole_step_frac": whole / peak},
