@@ -15,6 +15,7 @@ paper's LaTeX source numbers them:
   Eq. 8  the per-iteration least-squares problem (ILS)                                (Sec. 3.2)
   Eq. 9  its periodic-boundary FFT solution                                           (Sec. 3.2)
   Eq. 11 c >= c0 = p*eps^(p/2-1), with c = c0 used throughout                         (Sec. 3.3, App. B)
+  Eq. 18 Welsch penalty phi_W;  Eq. 19 its mu update;  Eq. 20 its c0 = 2              (Sec. 3.5, Sec. 5)
   Algorithm 1: u^0 = f; for n = 0..N-1: mu^n from u^n (Eq. 7), u^{n+1} from Eq. 9.
   Sec. 3.4: colour images are smoothed one RGB channel at a time.
 
@@ -47,6 +48,8 @@ __all__ = [
     "solve_eq9", "ils_iteration", "ils_smooth", "ils_channel", "energy", "ils_backward",
     "conv3x3", "warmstart_cnn_forward", "bf16_round", "warmstart_forward_bf16", "warmstart_backward_bf16",
     "adam_step",
+    "C0_WELSCH", "phi_welsch", "dphi_welsch", "d2phi_welsch", "g2_welsch", "mu_welsch",
+    "ils_channel_welsch", "ils_smooth_welsch", "energy_welsch", "ils_backward_welsch",
 ]
 
 
@@ -238,6 +241,110 @@ def energy(u, f, lam, p, eps):
     return float(np.sum((u - f) ** 2)
                  + lam * np.sum(phi_p(grad_x(u), p, eps))
                  + lam * np.sum(phi_p(grad_y(u), p, eps)))
+
+
+# ----------------------------------------------------------------------------
+# ILS with the Welsch penalty (Sec. 5): the same additive half-quadratic procedure
+# with phi_W in place of phi_p, the mu update of Eq. 19 and c0 = 2 (Eq. 20).
+# ----------------------------------------------------------------------------
+
+C0_WELSCH = 2.0  # Eq. 20 (proof: Appendix B, Eq. 24): c >= h(0) = 2
+
+
+def phi_welsch(x, gamma):
+    """Welsch penalty of Eq. 18, phi_W(x) = 2 gamma^2 (1 - exp(-x^2 / (2 gamma^2))).
+
+    Reading: the exponent is printed without its minus sign in Eq. 18; the derivative the
+    paper uses in Eq. 19, 2 x exp(-x^2/(2 gamma^2)), and the bounded penalty the text
+    describes both fix it as exp(-x^2/(2 gamma^2)).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    return 2.0 * gamma * gamma * (1.0 - np.exp(-x * x / (2.0 * gamma * gamma)))
+
+
+def dphi_welsch(x, gamma):
+    """phi_W'(x) = 2 x exp(-x^2 / (2 gamma^2)), as written out in Eq. 19."""
+    x = np.asarray(x, dtype=np.float64)
+    return 2.0 * x * np.exp(-x * x / (2.0 * gamma * gamma))
+
+
+def d2phi_welsch(x, gamma):
+    """phi_W''(x) = 2 exp(-x^2/(2 gamma^2)) (1 - x^2/gamma^2): the h(x) of Appendix B
+    (written there with kappa for gamma)."""
+    x = np.asarray(x, dtype=np.float64)
+    return 2.0 * np.exp(-x * x / (2.0 * gamma * gamma)) * (1.0 - x * x / (gamma * gamma))
+
+
+def g2_welsch(x, gamma, c):
+    """g''(x) = c - phi_W''(x) (Appendix B), the derivative of the Eq. 19 mu."""
+    return c - d2phi_welsch(x, gamma)
+
+
+def mu_welsch(x, gamma, c):
+    """Eq. 19: mu = c*x - 2 x exp(-x^2 / (2 gamma^2))."""
+    x = np.asarray(x, dtype=np.float64)
+    return c * x - dphi_welsch(x, gamma)
+
+
+def ils_channel_welsch(f, lam, gamma, N, u0=None, c=None, return_iterates=False):
+    """Algorithm 1 with the Welsch penalty on one H x W channel (float64): mu^n by Eq. 19,
+    u^{n+1} by Eq. 9 with c = c0 = 2 (Eq. 20) in the denominator."""
+    f = np.asarray(f, dtype=np.float64)
+    H, W = f.shape
+    if c is None:
+        c = C0_WELSCH
+    Fdx, Fdy = gradient_transfer_functions(H, W)
+    den = denominator(H, W, lam, c, Fdx, Fdy)
+    Ff = dft2(f)
+    u = f.copy() if u0 is None else np.asarray(u0, dtype=np.float64).copy()
+    iterates = [u.copy()]
+    for _ in range(int(N)):
+        mu_x = mu_welsch(grad_x(u), gamma, c)
+        mu_y = mu_welsch(grad_y(u), gamma, c)
+        u = solve_eq9(Ff, mu_x, mu_y, lam, den, Fdx, Fdy)
+        if return_iterates:
+            iterates.append(u.copy())
+    return (u, iterates) if return_iterates else u
+
+
+def ils_smooth_welsch(f, lam=20.0, gamma=10.0 / 255.0, N=10, u0=None, c=None):
+    """Welsch-penalty ILS on a C x H x W (or H x W) image, channels independent (Sec. 3.4)."""
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 2:
+        return ils_channel_welsch(f, lam, gamma, N, u0, c)
+    out = np.empty_like(f)
+    for ch in range(f.shape[0]):
+        out[ch] = ils_channel_welsch(f[ch], lam, gamma, N, None if u0 is None else u0[ch], c)
+    return out
+
+
+def energy_welsch(u, f, lam, gamma):
+    """Eq. 1 with the Welsch penalty phi_W of Eq. 18."""
+    u = np.asarray(u, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    return float(np.sum((u - f) ** 2)
+                 + lam * np.sum(phi_welsch(grad_x(u), gamma))
+                 + lam * np.sum(phi_welsch(grad_y(u), gamma)))
+
+
+def ils_backward_welsch(f, grad_u, lam, gamma, N, c=None, u0=None, split=False):
+    """Gradient of <grad_u, u^N(f)> for the Welsch ILS: the chain rule of ils_backward with
+    g'' = c - phi_W'' (Appendix B)."""
+    f = np.asarray(f, dtype=np.float64)
+    H, W = f.shape
+    if c is None:
+        c = C0_WELSCH
+    _, iterates = ils_channel_welsch(f, lam, gamma, N, u0=u0, c=c, return_iterates=True)
+    den = denominator(H, W, lam, c)
+    g = np.asarray(grad_u, dtype=np.float64).copy()
+    gf = np.zeros_like(f)
+    for n in range(int(N) - 1, -1, -1):
+        r = np.real(idft2(dft2(g) / den))
+        gf += r
+        un = iterates[n]
+        g = (lam / 2.0) * (grad_x_T(g2_welsch(grad_x(un), gamma, c) * grad_x(r))
+                           + grad_y_T(g2_welsch(grad_y(un), gamma, c) * grad_y(r)))
+    return (gf, g) if split else gf + g
 
 
 # ----------------------------------------------------------------------------

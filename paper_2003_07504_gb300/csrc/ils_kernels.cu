@@ -423,6 +423,14 @@ bool pick_geometry(int H, int W, Geometry* g) {
   g->warp_row = nw > 0 ? wv[pick] : -1;
   g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
   g->fixed_col = generic ? -1 : fixed_col_index(H);
+  // ILS_COL_IMPL=<k>: the k-th compile-time column plan of the length (tests, measurements)
+  const char* cimpl = getenv("ILS_COL_IMPL");
+  if (!generic && cimpl != nullptr && cimpl[0] >= '0' && cimpl[0] <= '9') {
+    int cv[16];
+    const int nc = fixed_col_variants(H, cv, 16);
+    const int k = atoi(cimpl);
+    if (k >= 0 && k < nc) g->fixed_col = cv[k];
+  }
   return true;
 }
 

@@ -522,6 +522,7 @@ const ColEntry kCols[] = {
     // alternatives for the autotuner
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
     col_entry<FixedPlan<1080, 30, 36>, 8>(),
+    col_entry<FixedPlan<1080, 36, 30>, 8, 2>(),
     col_entry<FixedPlan<720, 24, 30>, 4, 3>(),
     col_entry<FixedPlan<480, 20, 24>, 4, 4>(),
     col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),

@@ -382,3 +382,97 @@ def test_adam_step_closed_form_first_step():
     w, g = np.array([1.0, -2.0, 3.0]), np.array([0.5, -4.0, 1e-3])
     w1, m, v = O.adam_step(w, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     np.testing.assert_allclose(w1, w - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- Welsch-penalty ILS (Sec. 5)
+
+def fd_dphi_welsch(x, gamma, h=1e-7):
+    return (O.phi_welsch(x + h, gamma) - O.phi_welsch(x - h, gamma)) / (2 * h)
+
+
+def dense_ils_welsch(f, lam, gamma, N, Dx, Dy):
+    """Algorithm 1 with the Welsch penalty, dense operators, phi_W' by finite differences, c = 2."""
+    c = 2.0
+    n = f.size
+    fv = f.reshape(-1)
+    A = 2 * np.eye(n) + lam * c * (Dx.T @ Dx + Dy.T @ Dy)
+    u = fv.copy()
+    for _ in range(N):
+        gx, gy = Dx @ u, Dy @ u
+        mx = c * gx - fd_dphi_welsch(gx, gamma)
+        my = c * gy - fd_dphi_welsch(gy, gamma)
+        u = np.linalg.solve(A, 2 * fv + lam * (Dx.T @ mx + Dy.T @ my))
+    return u.reshape(f.shape)
+
+
+def test_welsch_penalty_is_bounded_quadratic_near_zero():
+    # the reading of Eq. 18: phi_W(0) = 0, phi_W ~ x^2 for |x| << gamma, phi_W -> 2 gamma^2 for |x| >> gamma
+    g = 0.05
+    assert O.phi_welsch(0.0, g) == 0.0
+    np.testing.assert_allclose(O.phi_welsch(1e-4, g), 1e-8, rtol=1e-5)
+    np.testing.assert_allclose(O.phi_welsch(10.0, g), 2 * g * g, rtol=1e-12)
+    assert np.all(np.diff(O.phi_welsch(np.linspace(0, 1, 1001), g)) >= 0)
+
+
+def test_welsch_mu_is_c_x_minus_numerical_derivative_of_penalty():
+    x = np.concatenate([np.linspace(-1, 1, 201), [1e-5, -3e-3, 0.011]])
+    for gamma in (5 / 255, 10 / 255, 0.3):
+        np.testing.assert_allclose(O.mu_welsch(x, gamma, 2.0), 2.0 * x - fd_dphi_welsch(x, gamma),
+                                   rtol=1e-6, atol=1e-9)
+
+
+def test_welsch_c0_is_the_convexity_threshold():
+    # Appendix B (Eq. 24): g = c/2 x^2 - phi_W is convex for c >= 2 and not for any smaller c.
+    x = np.linspace(-1, 1, 400001)
+    for gamma in (5 / 255, 10 / 255, 0.3):
+        assert np.min(O.g2_welsch(x, gamma, O.C0_WELSCH)) >= -1e-12
+        assert np.min(O.g2_welsch(x, gamma, 0.95 * O.C0_WELSCH)) < 0
+        h = 1e-5 * gamma
+        xs = np.array([-0.7, -gamma, 0.3 * gamma, 2 * gamma])
+        g = lambda t: t * t - O.phi_welsch(t, gamma)
+        num = (g(xs + h) - 2 * g(xs) + g(xs - h)) / h ** 2
+        np.testing.assert_allclose(O.g2_welsch(xs, gamma, 2.0), num, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("H,W,lam,gamma,N", [(8, 8, 20.0, 10 / 255, 4), (5, 7, 3.0, 0.2, 3)])
+def test_welsch_algorithm_matches_dense_bruteforce(H, W, lam, gamma, N):
+    f = small_image(H, W, seed=3 * H + W)
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    want = dense_ils_welsch(f, lam, gamma, N, Dx, Dy)
+    np.testing.assert_allclose(O.ils_channel_welsch(f, lam, gamma, N), want, atol=1e-6)
+
+
+def test_welsch_large_gamma_is_the_quadratic_smoother():
+    # gamma -> infinity: phi_W(x) -> x^2, so mu -> 0 and one iteration gives the closed-form
+    # quadratic smoother (I + lam (Dx^T Dx + Dy^T Dy))^{-1} f.
+    H, W, lam = 7, 9, 1.7
+    f = small_image(H, W, seed=5)
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    want = np.linalg.solve(np.eye(H * W) + lam * (Dx.T @ Dx + Dy.T @ Dy), f.reshape(-1)).reshape(H, W)
+    np.testing.assert_allclose(O.ils_channel_welsch(f, lam, 1e4, 1), want, atol=1e-9)
+
+
+def test_welsch_energy_is_non_increasing_and_invariants():
+    f = small_image(24, 20, seed=17)
+    for lam, gamma in ((20.0, 10 / 255), (5.0, 0.1)):
+        _, its = O.ils_channel_welsch(f, lam, gamma, 12, return_iterates=True)
+        E = [O.energy_welsch(u, f, lam, gamma) for u in its]
+        assert all(E[i + 1] <= E[i] * (1 + 1e-12) for i in range(len(E) - 1)), E
+        assert E[-1] < E[0]
+        assert abs(its[-1].mean() - f.mean()) < 1e-12
+    np.testing.assert_allclose(O.ils_channel_welsch(f, 0.0, 0.05, 3), f, atol=1e-13)
+    np.testing.assert_allclose(O.ils_channel_welsch(np.full((6, 8), 0.4), 9.0, 0.05, 3), 0.4, atol=1e-13)
+
+
+def test_welsch_adjoint_matches_finite_differences():
+    H, W, lam, gamma, N = 8, 10, 6.0, 0.08, 3
+    rng = np.random.default_rng(4)
+    f = small_image(H, W, seed=19)
+    gu = rng.normal(size=(H, W))
+    got = O.ils_backward_welsch(f, gu, lam, gamma, N)
+    for _ in range(3):
+        d = rng.normal(size=(H, W))
+        h = 1e-6
+        num = (np.sum(gu * O.ils_channel_welsch(f + h * d, lam, gamma, N))
+               - np.sum(gu * O.ils_channel_welsch(f - h * d, lam, gamma, N))) / (2 * h)
+        assert np.sum(got * d) == pytest.approx(num, rel=1e-6, abs=1e-9)
