@@ -72,6 +72,18 @@ const char* ils_last_error(void);
 ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps, int N,
                            ils_plan** out);
 
+/*
+ * ils_plan_create_welsch - a plan for ILS with the Welsch penalty (Sec. 5 "Model
+ * Extension"): phi_W(x) = 2 gamma^2 (1 - exp(-x^2 / (2 gamma^2))) (Eq. 18), mu update
+ * mu = c x - 2 x exp(-x^2 / (2 gamma^2)) (Eq. 19), c = c0 = 2 (Eq. 20, Appendix B).
+ * Same passes, layout and entry points as a plan from ils_plan_create (smooth,
+ * smooth_from, host, checkpointed, backward); the paper uses it for clip-art artifact
+ * removal (lambda = 20-30, gamma = 5/255-10/255, N = 10) and texture smoothing (N = 15).
+ *   lambda >= 0, gamma > 0 (finite, 1/(2 gamma^2) finite), N >= 0; shapes as for
+ *   ils_plan_create.  Returns ILS_ERR_INVALID_ARG for other parameters.
+ */
+ils_status ils_plan_create_welsch(int H, int W, int C, float lambda, float gamma, int N, ils_plan** out);
+
 /* Free a plan and its device memory.  NULL is accepted.  Synchronizes the device. */
 ils_status ils_plan_destroy(ils_plan* plan);
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "ils_status_string": (ctypes.c_char_p, [c_int]),
     "ils_last_error": (ctypes.c_char_p, []),
     "ils_plan_create": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int, P(c_void_p)]),
+    "ils_plan_create_welsch": (c_int, [c_int, c_int, c_int, c_float, c_float, c_int, c_void_p]),
     "ils_plan_destroy": (c_int, [c_void_p]),
     "ils_plan_c": (c_float, [c_void_p]),
     "ils_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -192,15 +192,18 @@ const char* ils_status_string(ils_status s) {
 
 const char* ils_last_error(void) { return g_last_error.c_str(); }
 
-ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps, int N, ils_plan** out) {
-  if (out == nullptr) return ILS_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (C < 1 || N < 0 || !(lambda >= 0.0f) || !std::isfinite(lambda) || !(eps > 0.0f) || !std::isfinite(eps) ||
-      !((p > 0.0f && p <= 1.0f) || p == 2.0f))
-    return ILS_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Shared by both penalties: validates the shape, allocates and fills the tables.
+// mp holds the penalty's Eq. 7 / Eq. 19 parameters; c (double) builds the Eq. 9 tables and
+// its FP32 rounding goes to the kernels; half_lambda is set here.
+ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, double c, float p, float eps,
+                       ils_plan** out) {
   if (H < 2 || W < 2 || H > 8192 || W > 8192 || (W & 1) || !smooth_235(H) || !smooth_235(W))
     return ILS_ERR_UNSUPPORTED_SIZE;
-  const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);
+  mp.c = (float)c;
   if (!std::isfinite(c) || (size_t)C * H * W > (size_t)1 << 31) return ILS_ERR_UNSUPPORTED_SIZE;
 
   ils_plan* pl = new (std::nothrow) ils_plan();
@@ -214,10 +217,7 @@ ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps
     delete pl;
     return ILS_ERR_UNSUPPORTED_SIZE;
   }
-  pl->mp.c = (float)c;
-  pl->mp.p = p;
-  pl->mp.eps = eps;
-  pl->mp.a = p / 2.0f - 1.0f;
+  pl->mp = mp;
   pl->mp.half_lambda = 0.5f * lambda;
 
   cudaError_t e;
@@ -258,6 +258,41 @@ ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps
   }
   *out = pl;
   return ILS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps, int N, ils_plan** out) {
+  if (out == nullptr) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (C < 1 || N < 0 || !(lambda >= 0.0f) || !std::isfinite(lambda) || !(eps > 0.0f) || !std::isfinite(eps) ||
+      !((p > 0.0f && p <= 1.0f) || p == 2.0f))
+    return ILS_ERR_INVALID_ARG;
+  MuParams mp;
+  mp.p = p;
+  mp.eps = eps;
+  mp.a = p / 2.0f - 1.0f;
+  const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);  // c = c0 (Eq. 11)
+  return create_plan(H, W, C, lambda, N, mp, c, p, eps, out);
+}
+
+ils_status ils_plan_create_welsch(int H, int W, int C, float lambda, float gamma, int N, ils_plan** out) {
+  if (out == nullptr) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (C < 1 || N < 0 || !(lambda >= 0.0f) || !std::isfinite(lambda) || !(gamma > 0.0f) || !std::isfinite(gamma))
+    return ILS_ERR_INVALID_ARG;
+  const double inv2g2 = 1.0 / (2.0 * (double)gamma * (double)gamma);
+  if (!std::isfinite(inv2g2) || inv2g2 > 1e30) return ILS_ERR_INVALID_ARG;
+  MuParams mp;
+  mp.p = 0.0f;
+  mp.eps = 1.0f;
+  mp.a = 0.0f;
+  mp.welsch = 1;
+  mp.wbeta = (float)(inv2g2 / std::log(2.0));  // exp(-x^2/(2 gamma^2)) = 2^(-wbeta x^2)
+  mp.winv2g2 = (float)inv2g2;
+  return create_plan(H, W, C, lambda, N, mp, 2.0, 0.0f, 1.0f, out);  // c = c0 = 2 (Eq. 20)
 }
 
 ils_status ils_plan_destroy(ils_plan* pl) {

@@ -15,6 +15,9 @@ struct MuParams {
   float eps;
   float a;       // p/2 - 1
   float half_lambda;
+  int welsch = 0;    // penalty: 0 = generalized Charbonnier (Eq. 2, Eq. 7), 1 = Welsch (Eq. 18, Eq. 19)
+  float wbeta = 0.0f;   // Welsch: log2(e) / (2 gamma^2)
+  float winv2g2 = 0.0f; // Welsch: 1 / (2 gamma^2)
 };
 
 // 2^x and log2(x) on the special-function unit (PTX ex2.approx / lg2.approx, flush to
@@ -34,6 +37,17 @@ __device__ __forceinline__ float sfu_log2(float x) {
 __device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
   const float t = fmaf(g, g, mp.eps);
   return g * fmaf(-mp.p, sfu_exp2(mp.a * sfu_log2(t)), mp.c);
+}
+
+// Eq. 19 (Welsch penalty): mu = c g - 2 g exp(-g^2 / (2 gamma^2)), c = 2 (Eq. 20).
+__device__ __forceinline__ float mu_welsch(float g, const MuParams& mp) {
+  return g * fmaf(-2.0f, sfu_exp2(-mp.wbeta * g * g), mp.c);
+}
+// mu of the penalty PEN (0: Eq. 7, 1: Eq. 19); the kernels are instantiated per penalty.
+template <int PEN>
+__device__ __forceinline__ float mu_pen(float g, const MuParams& mp) {
+  if constexpr (PEN == 0) return mu_eq7(g, mp);
+  else return mu_welsch(g, mp);
 }
 
 // Launch geometry picked by the host planner (validated before any launch).

@@ -29,7 +29,7 @@ __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (
 // grid = (ceil(H / rows), C); each CTA produces `rows` rows of the r spectrum
 // and needs u on rows y0-1 .. y0+rows (periodic), rebuilt from spec_in (or read
 // from u0 / f on the first iteration).
-template <int EPT, bool FIRST>
+template <int EPT, bool FIRST, int PEN>
 __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_forward_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW, MuParams mp,
                    const float* __restrict__ f, const float* __restrict__ u0,
@@ -90,13 +90,13 @@ row_forward_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
       const float2 up = sm[smem_idx(i * M + m)];
       const float2 dn = sm[smem_idx((i + 2) * M + m)];
       const float2 fv = fc[w];
-      const float mx_l = mu_eq7(c.x - ul, mp);    // mu_x at x0-1
-      const float mx_c = mu_eq7(c.y - c.x, mp);   // mu_x at x0
-      const float mx_r = mu_eq7(ur - c.y, mp);    // mu_x at x0+1
-      const float my0u = mu_eq7(c.x - up.x, mp);  // mu_y at (y-1, x0)
-      const float my0d = mu_eq7(dn.x - c.x, mp);  // mu_y at (y,   x0)
-      const float my1u = mu_eq7(c.y - up.y, mp);
-      const float my1d = mu_eq7(dn.y - c.y, mp);
+      const float mx_l = mu_pen<PEN>(c.x - ul, mp);    // mu_x at x0-1
+      const float mx_c = mu_pen<PEN>(c.y - c.x, mp);   // mu_x at x0
+      const float mx_r = mu_pen<PEN>(ur - c.y, mp);    // mu_x at x0+1
+      const float my0u = mu_pen<PEN>(c.x - up.x, mp);  // mu_y at (y-1, x0)
+      const float my0d = mu_pen<PEN>(dn.x - c.x, mp);  // mu_y at (y,   x0)
+      const float my1u = mu_pen<PEN>(c.y - up.y, mp);
+      const float my1d = mu_pen<PEN>(dn.y - c.y, mp);
       rr[b].x = fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x);
       rr[b].y = fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y);
     }
@@ -189,14 +189,20 @@ col_solve_kernel(int H, int M, int G, FftPlan planH, const float2* __restrict__ 
 //   gbar' = lambda/2 sum_* grad_*^T [ g''(grad_* u^n) * grad_* r ]   (dL/du^n; g'' = dmu/dx, App. B)
 // and gbar' is forward-FFT'd for the next step, or (last step) added to the u^0 gradient.
 // g''(x) = c - p (x^2+eps)^(p/2-2) ((p-1) x^2 + eps).
+// Welsch (Appendix B): g''(x) = c - 2 exp(-x^2/(2 gamma^2)) (1 - x^2/gamma^2).
+template <int PEN>
 __device__ __forceinline__ float g2_appb(float x, const MuParams& mp) {
   const float x2 = x * x;
-  const float t = x2 + mp.eps;
-  const float w = sfu_exp2((mp.a - 1.0f) * sfu_log2(t));
-  return fmaf(-mp.p * w, fmaf(mp.p - 1.0f, x2, mp.eps), mp.c);
+  if constexpr (PEN == 1) {
+    return fmaf(-2.0f * sfu_exp2(-mp.wbeta * x2), fmaf(-2.0f * mp.winv2g2, x2, 1.0f), mp.c);
+  } else {
+    const float t = x2 + mp.eps;
+    const float w = sfu_exp2((mp.a - 1.0f) * sfu_log2(t));
+    return fmaf(-mp.p * w, fmaf(mp.p - 1.0f, x2, mp.eps), mp.c);
+  }
 }
 
-template <int EPT>
+template <int EPT, int PEN>
 __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW, MuParams mp,
                    const float2* __restrict__ spec_in, const float* __restrict__ u_n, float* __restrict__ fbar,
@@ -251,13 +257,13 @@ row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
       const float2 uu = uc[(size_t)wrap_row(y - 1, H) * M + m];
       const float2 ud = uc[(size_t)wrap_row(y + 1, H) * M + m];
       // q_x at x0-1, x0, x0+1 and q_y at (y-1, x) and (y, x)
-      const float qx_l = g2_appb(uc0.x - ul, mp) * (rc.x - rl);
-      const float qx_c = g2_appb(uc0.y - uc0.x, mp) * (rc.y - rc.x);
-      const float qx_r = g2_appb(ur - uc0.y, mp) * (rrt - rc.y);
-      const float qy0u = g2_appb(uc0.x - uu.x, mp) * (rc.x - ru.x);
-      const float qy0d = g2_appb(ud.x - uc0.x, mp) * (rd.x - rc.x);
-      const float qy1u = g2_appb(uc0.y - uu.y, mp) * (rc.y - ru.y);
-      const float qy1d = g2_appb(ud.y - uc0.y, mp) * (rd.y - rc.y);
+      const float qx_l = g2_appb<PEN>(uc0.x - ul, mp) * (rc.x - rl);
+      const float qx_c = g2_appb<PEN>(uc0.y - uc0.x, mp) * (rc.y - rc.x);
+      const float qx_r = g2_appb<PEN>(ur - uc0.y, mp) * (rrt - rc.y);
+      const float qy0u = g2_appb<PEN>(uc0.x - uu.x, mp) * (rc.x - ru.x);
+      const float qy0d = g2_appb<PEN>(ud.x - uc0.x, mp) * (rd.x - rc.x);
+      const float qy1u = g2_appb<PEN>(uc0.y - uu.y, mp) * (rc.y - ru.y);
+      const float qy1d = g2_appb<PEN>(ud.y - uc0.y, mp) * (rd.y - rc.y);
       const float2 gb = make_float2(mp.half_lambda * ((qx_l - qx_c) + (qy0u - qy0d)),
                                     mp.half_lambda * ((qx_c - qx_r) + (qy1u - qy1d)));
       const size_t o = (size_t)y * M + m;
@@ -441,16 +447,22 @@ static cudaError_t allow_smem(K kernel) {
 
 cudaError_t set_kernel_attributes() {
   cudaError_t e;
-  if ((e = allow_smem(row_forward_kernel<16, true>))) return e;
-  if ((e = allow_smem(row_forward_kernel<16, false>))) return e;
-  if ((e = allow_smem(row_forward_kernel<32, true>))) return e;
-  if ((e = allow_smem(row_forward_kernel<32, false>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, true, 0>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, false, 0>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, true, 0>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, false, 0>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, true, 1>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, false, 1>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, true, 1>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, false, 1>))) return e;
   if ((e = allow_smem(col_solve_kernel<16>))) return e;
   if ((e = allow_smem(col_solve_kernel<32>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16>))) return e;
   if ((e = allow_smem(row_inverse_kernel<32>))) return e;
-  if ((e = allow_smem(row_adjoint_kernel<16>))) return e;
-  if ((e = allow_smem(row_adjoint_kernel<32>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<16, 0>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<32, 0>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<16, 1>))) return e;
+  if ((e = allow_smem(row_adjoint_kernel<32, 1>))) return e;
   if ((e = warp_set_attributes())) return e;
   return fixed_set_attributes();
 }
@@ -464,8 +476,11 @@ cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tabl
   const int T = g.threads_row;
   const size_t S = g.smem_fwd;
   const bool first = spec_in == nullptr;
-  auto fn = g.ept_row == 16 ? (first ? row_forward_kernel<16, true> : row_forward_kernel<16, false>)
-                            : (first ? row_forward_kernel<32, true> : row_forward_kernel<32, false>);
+  auto fn = mp.welsch
+                ? (g.ept_row == 16 ? (first ? row_forward_kernel<16, true, 1> : row_forward_kernel<16, false, 1>)
+                                   : (first ? row_forward_kernel<32, true, 1> : row_forward_kernel<32, false, 1>))
+                : (g.ept_row == 16 ? (first ? row_forward_kernel<16, true, 0> : row_forward_kernel<16, false, 0>)
+                                   : (first ? row_forward_kernel<32, true, 0> : row_forward_kernel<32, false, 0>));
   return launch_k(d.pdl, fn, grid, T, S, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, first ? u0 : nullptr,
                   spec_in, spec_out, u_ckpt);
 }
@@ -494,7 +509,8 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream) {
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
-  auto fn = g.ept_row == 16 ? row_adjoint_kernel<16> : row_adjoint_kernel<32>;
+  auto fn = mp.welsch ? (g.ept_row == 16 ? row_adjoint_kernel<16, 1> : row_adjoint_kernel<32, 1>)
+                      : (g.ept_row == 16 ? row_adjoint_kernel<16, 0> : row_adjoint_kernel<32, 0>);
   return launch_k(d.pdl, fn, grid, g.threads_row, g.smem_fwd, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, spec_in,
                   u_n, fbar, (int)fbar_first, gu0, (int)last, spec_out);
 }

@@ -300,7 +300,7 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
 // CTA = (ROWS + 2) x TPS threads.  In the inverse FFT thread (i, j) works on strip row i
 // (i = 0 and ROWS+1 are the halo rows y0-1 and y0+ROWS); the stencil runs over all
 // threads row by row; the forward FFT of output row o runs on threads (o, j).
-template <class PL, int ROWS, bool FIRST>
+template <class PL, int ROWS, bool FIRST, int PEN>
 __global__ void __launch_bounds__((ROWS + 2) * PL::TPS, 1)
 row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                      const float* __restrict__ u0, const float2* __restrict__ spec_in,
@@ -359,13 +359,13 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
             const float2 up = U(o, m);
             const float2 dn = U(o + 2, m);
             const float2 fv = fr[m];
-            const float mx_l = mu_eq7(c.x - ul, mp);
-            const float mx_c = mu_eq7(c.y - c.x, mp);
-            const float mx_r = mu_eq7(ur - c.y, mp);
-            const float my0u = mu_eq7(c.x - up.x, mp);
-            const float my0d = mu_eq7(dn.x - c.x, mp);
-            const float my1u = mu_eq7(c.y - up.y, mp);
-            const float my1d = mu_eq7(dn.y - c.y, mp);
+            const float mx_l = mu_pen<PEN>(c.x - ul, mp);
+            const float mx_c = mu_pen<PEN>(c.y - c.x, mp);
+            const float mx_r = mu_pen<PEN>(ur - c.y, mp);
+            const float my0u = mu_pen<PEN>(c.x - up.x, mp);
+            const float my0d = mu_pen<PEN>(dn.x - c.x, mp);
+            const float my1u = mu_pen<PEN>(c.y - up.y, mp);
+            const float my1d = mu_pen<PEN>(dn.y - c.y, mp);
             rv[q] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x),
                        fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
             if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
@@ -480,7 +480,7 @@ using ColFn = void (*)(int, int, const float2*, const float*, const float*, floa
 
 struct RowEntry {
   int M, tps, rows_fwd, rows_inv;
-  RowFwdFn first, later;
+  RowFwdFn first[2], later[2];  // per penalty (MuParams::welsch)
   RowInvFn inv;
 };
 struct ColEntry {
@@ -490,7 +490,12 @@ struct ColEntry {
 
 template <class PL, int RF, int RI>
 constexpr RowEntry row_entry() {
-  return RowEntry{PL::N, PL::TPS, RF, RI, row_fwd_fixed_kernel<PL, RF, true>, row_fwd_fixed_kernel<PL, RF, false>,
+  return RowEntry{PL::N,
+                  PL::TPS,
+                  RF,
+                  RI,
+                  {row_fwd_fixed_kernel<PL, RF, true, 0>, row_fwd_fixed_kernel<PL, RF, true, 1>},
+                  {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>},
                   row_inv_fixed_kernel<PL, RI>};
 }
 template <class PL, int G, int MINB = 1>
@@ -563,8 +568,10 @@ cudaError_t fixed_set_attributes() {
   cudaError_t e;
   for (const RowEntry& r : kRows) {
     const int sf = (int)row_smem(r.rows_fwd + 2, r.M), si = (int)row_smem(r.rows_inv, r.M);
-    if ((e = cudaFuncSetAttribute(r.first, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
-    if ((e = cudaFuncSetAttribute(r.later, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    for (int pen = 0; pen < 2; ++pen) {
+      if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+      if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    }
     if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   for (const ColEntry& c : kCols) {
@@ -581,7 +588,8 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
   const int threads = (r.rows_fwd + 2) * r.tps;
   const size_t smem = row_smem(r.rows_fwd + 2, r.M);
   const int tiles = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  RowFwdFn fn = spec_in == nullptr ? r.first : r.later;
+  const int pen = mp.welsch ? 1 : 0;
+  RowFwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, tiles, threads, smem, stream, d.H, d.C, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }
 

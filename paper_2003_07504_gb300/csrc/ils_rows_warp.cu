@@ -156,7 +156,7 @@ struct WarpRow {
 // STAGE (with SHARED): the f rows of the output rows are copied to shared memory
 // asynchronously at the start (behind the inverse transforms) instead of being loaded in
 // the stencil.
-template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED>
+template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN>
 __global__ void __launch_bounds__((ROWS + 2) * 32, (ROWS + 2) * 32 <= 256 ? 2 : 1)
 row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                     const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
@@ -228,13 +228,13 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
         const float2 up = U(w - 1, m);
         const float2 dn = U(w + 1, m);
         const float2 fv = fr[m];
-        const float mx_l = mu_eq7(c.x - ul, mp);
-        const float mx_c = mu_eq7(c.y - c.x, mp);
-        const float mx_r = mu_eq7(ur - c.y, mp);
-        const float my0u = mu_eq7(c.x - up.x, mp);
-        const float my0d = mu_eq7(dn.x - c.x, mp);
-        const float my1u = mu_eq7(c.y - up.y, mp);
-        const float my1d = mu_eq7(dn.y - c.y, mp);
+        const float mx_l = mu_pen<PEN>(c.x - ul, mp);
+        const float mx_c = mu_pen<PEN>(c.y - c.x, mp);
+        const float mx_r = mu_pen<PEN>(ur - c.y, mp);
+        const float my0u = mu_pen<PEN>(c.x - up.x, mp);
+        const float my0d = mu_pen<PEN>(dn.x - c.x, mp);
+        const float my1u = mu_pen<PEN>(c.y - up.y, mp);
+        const float my1d = mu_pen<PEN>(dn.y - c.y, mp);
         v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x),
                    fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
         if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
@@ -252,7 +252,7 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
     for (int n2 = 0; n2 < L; ++n2) {
       const int m = lane + 32 * n2;
       const float2 a = U(w, m), b = U(w + 1, m);
-      Y[n2] = c2(mu_eq7(b.x - a.x, mp), mu_eq7(b.y - a.y, mp));
+      Y[n2] = c2(mu_pen<PEN>(b.x - a.x, mp), mu_pen<PEN>(b.y - a.y, mp));
     }
   }
   if (STAGE) cp_async_wait_all();
@@ -275,8 +275,8 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
         const float nx_in = __shfl_down_sync(kFull, c.x, 1);
         const float nx_wrap = __shfl_sync(kFull, n2 + 1 < L ? cn.x : u_first, 0);
         const float nx = lane == 31 ? nx_wrap : nx_in;  // u at pixel 2m+2
-        const float mx_c = mu_eq7(c.y - c.x, mp);     // mu_x at pixel 2m
-        const float mx_r = mu_eq7(nx - c.y, mp);      // mu_x at pixel 2m+1
+        const float mx_c = mu_pen<PEN>(c.y - c.x, mp);     // mu_x at pixel 2m
+        const float mx_r = mu_pen<PEN>(nx - c.y, mp);      // mu_x at pixel 2m+1
         const float up = __shfl_up_sync(kFull, mx_r, 1);
         const float mx_l = lane == 0 ? carry : up;    // mu_x at pixel 2m-1
         carry = __shfl_sync(kFull, mx_r, 31);
@@ -328,7 +328,7 @@ using InvFn = void (*)(int, const float2*, const float2*, float*);
 
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
-  FwdFn first, later;
+  FwdFn first[2], later[2];  // per penalty (MuParams::welsch)
   InvFn inv;
 };
 
@@ -336,8 +336,13 @@ struct WarpRowEntry {
 template <int L, int RF, int RI, bool STAGE, bool SHARED>
 constexpr WarpRowEntry warp_entry() {
   static_assert(SHARED || !STAGE, "f staging is part of the shared-mu stencil");
-  return WarpRowEntry{32 * L, RF, RI, WarpRow<L>::BUF, STAGE ? RF * 32 * L : 0,
-                      row_warp_fwd_kernel<L, RF, true, STAGE, SHARED>, row_warp_fwd_kernel<L, RF, false, STAGE, SHARED>,
+  return WarpRowEntry{32 * L,
+                      RF,
+                      RI,
+                      WarpRow<L>::BUF,
+                      STAGE ? RF * 32 * L : 0,
+                      {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0>, row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1>},
+                      {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0>, row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1>},
                       row_warp_inv_kernel<L, RI>};
 }
 
@@ -368,8 +373,10 @@ cudaError_t warp_set_attributes() {
   for (const WarpRowEntry& r : kWarpRows) {
     const int sf = ((r.rows_fwd + 2) * r.buf + r.stage) * (int)sizeof(float2);
     const int si = r.rows_inv * r.buf * (int)sizeof(float2);
-    if ((e = cudaFuncSetAttribute(r.first, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
-    if ((e = cudaFuncSetAttribute(r.later, cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    for (int pen = 0; pen < 2; ++pen) {
+      if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+      if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+    }
     if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   return cudaSuccess;
@@ -381,7 +388,8 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
   const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage) * sizeof(float2);
-  FwdFn fn = spec_in == nullptr ? r.first : r.later;
+  const int pen = mp.welsch ? 1 : 0;
+  FwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }
 

@@ -27,16 +27,28 @@ def _check_image(t: torch.Tensor, shape, name: str) -> None:
 
 
 class Plan:
-    """An ILS plan for C x H x W float32 images (ils_plan_create)."""
+    """An ILS plan for C x H x W float32 images (ils_plan_create), or with
+    penalty="welsch" an ILS plan with the Welsch penalty of scale gamma
+    (ils_plan_create_welsch; p and eps are then unused)."""
 
     def __init__(self, H: int, W: int, C: int = 1, lam: float = 1.0, p: float = 0.8,
-                 eps: float = 1e-4, N: int = 4):
+                 eps: float = 1e-4, N: int = 4, penalty: str = "lp", gamma: float | None = None):
         self.H, self.W, self.C, self.N = int(H), int(W), int(C), int(N)
         self.lam, self.p, self.eps = float(lam), float(p), float(eps)
+        self.penalty = penalty
         L = _lib.lib()
         h = ctypes.c_void_p()
-        _lib.check(L.ils_plan_create(self.H, self.W, self.C, self.lam, self.p, self.eps, self.N,
-                                     ctypes.byref(h)), "ils_plan_create")
+        if penalty == "welsch":
+            if gamma is None:
+                raise ValueError("the Welsch penalty needs gamma")
+            self.gamma = float(gamma)
+            _lib.check(L.ils_plan_create_welsch(self.H, self.W, self.C, self.lam, self.gamma, self.N,
+                                                ctypes.byref(h)), "ils_plan_create_welsch")
+        elif penalty == "lp":
+            _lib.check(L.ils_plan_create(self.H, self.W, self.C, self.lam, self.p, self.eps, self.N,
+                                         ctypes.byref(h)), "ils_plan_create")
+        else:
+            raise ValueError(f"unknown penalty {penalty!r}")
         self._h = h
 
     @property

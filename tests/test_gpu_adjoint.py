@@ -131,3 +131,16 @@ def test_adjoint_batch_of_512_images_against_fp64_samples(ils):
         want = O.ils_backward(f[ch].astype(np.float64), w[ch].astype(np.float64), 1.0, 0.8, 1e-4, 4)
         assert rel_err(g[ch], want) <= REL_TOL
     np.testing.assert_array_equal(gpu_grad(ils, f[5:6].copy(), w[5:6].copy()), g[5:6])
+
+
+@pytest.mark.parametrize("H,W,lam,gamma,N", [(32, 40, 20.0, 10 / 255, 3), (48, 64, 5.0, 0.1, 4)])
+def test_welsch_adjoint_matches_fp64_reverse_mode(ils, H, W, lam, gamma, N):
+    # Welsch g'' (Appendix B) in the adjoint row kernel; c = 2, so FP32 cancellation is mild
+    import torch
+    f = synth.preset_image(H, W, 1, "small", H * W)
+    w = synth.random_field(f.shape, seed=9)
+    with ils.Plan(H, W, 1, lam, N=N, penalty="welsch", gamma=gamma) as plan:
+        u, ck = plan.smooth_checkpointed(torch.from_numpy(f).cuda())
+        g = plan.backward(ck, torch.from_numpy(w).cuda()).cpu().numpy()
+    want = O.ils_backward_welsch(f[0].astype(np.float64), w[0].astype(np.float64), lam, gamma, N)
+    assert rel_err(g[0], want) <= REL_TOL

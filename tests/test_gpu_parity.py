@@ -247,3 +247,33 @@ def test_column_plan_variants_agree(ils, H, W):
         b.run()
         torch.cuda.synchronize()
         assert_parity(frames[0][1].cpu().numpy(), want)
+
+
+# -------------------------------------------------------------- ILS with the Welsch penalty (Sec. 5)
+
+@pytest.mark.parametrize("H,W,C,lam,gamma,N", [
+    (256, 256, 1, 20.0, 10 / 255, 10),   # warp-per-row kernels, L = 4; the paper's clip-art setting
+    (60, 80, 3, 30.0, 5 / 255, 10),      # generic row kernels (M = 40)
+    (45, 640, 1, 20.0, 10 / 255, 4),     # warp L = 10
+    (40, 1920, 1, 30.0, 10 / 255, 15),   # warp L = 30; texture-smoothing iteration count
+    (16, 3840, 1, 20.0, 10 / 255, 3),    # fixed-plan 1920-point rows
+    (27, 250, 1, 5.0, 0.1, 4),           # odd column length, generic rows
+    (1080, 40, 1, 20.0, 10 / 255, 2),    # 1080-point column plan
+])
+def test_welsch_parity(ils, H, W, C, lam, gamma, N):
+    import torch
+    f = image(H, W, C, seed=H * 31 + W + C)
+    with ils.Plan(H, W, C, lam, N=N, penalty="welsch", gamma=gamma) as plan:
+        assert plan.c == 2.0
+        u = plan.smooth(torch.from_numpy(np.ascontiguousarray(f)).cuda()).cpu().numpy()
+    want = O.ils_smooth_welsch(f.astype(np.float64), lam, gamma, N)
+    assert_parity(u, want)
+
+
+def test_welsch_rejects_bad_parameters(ils):
+    from paper_2003_07504_gb300._lib import ILSError
+    for gamma in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(ILSError):
+            ils.Plan(16, 16, 1, 1.0, N=2, penalty="welsch", gamma=gamma)
+    with pytest.raises(ILSError):
+        ils.Plan(16, 16, 1, -1.0, N=2, penalty="welsch", gamma=0.1)
