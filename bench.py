@@ -209,6 +209,73 @@ def adjoint_leg(ils, torch, dev, steps):
             "images_per_s_fwd_bwd": Ca / ((fwd + bwd) / steps / 1000.0)}
 
 
+def _timed_smooth(plan, f, u, torch, steps, flush, warmup=3):
+    """Mean ms per plan.smooth over `steps` calls, L2 flushed before each (CUDA events)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.smooth(f, out=u)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.smooth(f, out=u)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def gray_leg(ils, torch, dev, steps, flush):
+    """The headline size as one gray channel: 1 x 1080 x 1920, N = 4."""
+    f = torch.from_numpy(make_frame(1, H, W)).to(dev)
+    u = torch.empty_like(f)
+    with ils.Plan(H, W, 1, LAM, P, EPS, N_ITERS) as plan:
+        ms = _timed_smooth(plan, f, u, torch, steps, flush)
+    _, frame_bytes = bytes_model(H, W, 1, N_ITERS)
+    peak, _ = load_peaks()
+    return {"workload": "ILS 1920x1080 gray FP32, N=4, lambda=1, p=0.8, eps=1e-4", "fps": 1000.0 / ms, "ms": ms,
+            "mpix_per_s": H * W / ms / 1e3, "frac_of_hbm_peak": frame_bytes / (ms / 1000.0) / 1e9 / peak}
+
+
+def sweep_4k_leg(ils, torch, dev, steps, flush):
+    """3840 x 2160 RGB: N in {1, 2, 4, 10} x lambda in {0.5, 1, 2} x p in {0.8, 1.0}."""
+    from paper_2003_07504_gb300 import synth
+    Hs, Ws = 2160, 3840
+    f = torch.from_numpy(synth.preset_image(Hs, Ws, 3, "uhd", 3000)).to(dev)
+    u = torch.empty_like(f)
+    peak, _ = load_peaks()
+    points = []
+    for n in (1, 2, 4, 10):
+        _, frame_bytes = bytes_model(Hs, Ws, 3, n)
+        for lam in (0.5, 1.0, 2.0):
+            for p in (0.8, 1.0):
+                with ils.Plan(Hs, Ws, 3, lam, p, EPS, n) as plan:
+                    ms = _timed_smooth(plan, f, u, torch, steps, flush, warmup=2)
+                points.append({"N": n, "lambda": lam, "p": p, "ms": ms, "fps": 1000.0 / ms,
+                               "frac_of_hbm_peak": frame_bytes / (ms / 1000.0) / 1e9 / peak})
+    return {"workload": "ILS 3840x2160 RGB FP32 sweep, eps=1e-4", "points": points}
+
+
+def welsch_leg(ils, torch, dev, steps, flush):
+    """ILS with the Welsch penalty (Sec. 5) at 1920 x 1080 RGB with the paper's clip-art
+    artifact-removal setting (lambda = 20, gamma = 10/255, N = 10) and its texture-smoothing
+    iteration count (lambda = 30, N = 15)."""
+    f = torch.from_numpy(make_frame(C, H, W)).to(dev)
+    u = torch.empty_like(f)
+    peak, _ = load_peaks()
+    out = {}
+    for name, lam, gamma, n in (("clip_art", 20.0, 10 / 255, 10), ("texture", 30.0, 10 / 255, 15)):
+        with ils.Plan(H, W, C, lam, N=n, penalty="welsch", gamma=gamma) as plan:
+            ms = _timed_smooth(plan, f, u, torch, steps, flush)
+        _, frame_bytes = bytes_model(H, W, C, n)
+        out[name] = {"lambda": lam, "gamma": gamma, "N": n, "ms": ms, "fps": 1000.0 / ms,
+                     "frac_of_hbm_peak": frame_bytes / (ms / 1000.0) / 1e9 / peak}
+    out["workload"] = "Welsch-penalty ILS, 1920x1080 RGB FP32"
+    return out
+
+
 BATCH_SIZES = ((480, 640), (720, 1280), (1080, 1920), (1536, 2048))
 
 
@@ -248,19 +315,22 @@ def batch_leg(ils, torch, dev, steps, flush):
             "algorithmic_gbs": nbytes / (ms / 1000.0) / 1e9, "frac_of_hbm_peak": nbytes / (ms / 1000.0) / 1e9 / peak}
 
 
+CNN_FLOP_PER_PX = 2 * 9 * (3 * 32 + 4 * 32 * 32 + 32 * 3)  # 77,184: six 3x3 convolutions per pixel
+
+
 def warm_leg(torch, dev, steps, flush):
     """Learned warm start vs plain ILS at 1920x1080 RGB (lambda=1, p=0.8): fps of the whole
     warm path (network + 1 or 2 ILS iterations + the iterate-change check and fallback
-    decision) against plain N=4, and each result's RMS distance to converged ILS from f
-    (ILS iterated until the largest per-iteration change is < 1e-6, capped at 2000)."""
+    decision) against plain N=4 on one frame, and the RMS distance to converged ILS from f
+    (ILS iterated until the largest per-iteration change is < 1e-6, capped at 2000) averaged
+    over three fresh frames, with the fallback count."""
     from paper_2003_07504_gb300 import ils, synth, warmstart as ws
     path = ws.DEFAULT_WEIGHTS
     if not os.path.exists(path):
         return {"unavailable": "no trained weights file"}
-    f = torch.from_numpy(synth.preset_image(H, W, C, "hd", 90004)).to(dev)
+    seeds = (90004, 90005, 90006)
+    frames = [torch.from_numpy(synth.preset_image(H, W, C, "hd", sd)).to(dev) for sd in seeds]
     net = ws.WarmStartNet(H * W, ws.load_params(path))
-    ustar, its = ws.converged_ils(lambda h, w, c, n: ils.Plan(h, w, c, LAM, P, EPS, n), f, max_iters=2000)
-    rms = lambda u: float(((u - ustar) ** 2).mean().sqrt())
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -278,16 +348,37 @@ def warm_leg(torch, dev, steps, flush):
             tot += a.elapsed_time(b)
         return tot / steps
 
-    out = {"workload": "1920x1080 RGB, lambda=1, p=0.8, eps=1e-4; reference = ILS from f to convergence",
-           "reference_iterations": its, "uses_tcgen05": net.uses_tcgen05}
+    refs = [ws.converged_ils(lambda h, w, c, n: ils.Plan(h, w, c, LAM, P, EPS, n), f, max_iters=2000) for f in frames]
+    rms = lambda u, k: float(((u - refs[k][0]) ** 2).mean().sqrt())
+    f = frames[0]
+    out = {"workload": "1920x1080 RGB, lambda=1, p=0.8, eps=1e-4; reference = ILS from f to convergence; "
+                       "errors averaged over 3 frames, timing on the first",
+           "reference_iterations": [r[1] for r in refs], "uses_tcgen05": net.uses_tcgen05}
+    u0 = torch.empty_like(f).view(1, C, H, W)
+    net_ms = timed(lambda: net.infer(f.view(1, C, H, W), out=u0))
+    tflops = CNN_FLOP_PER_PX * H * W / (net_ms / 1000.0) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    out["network"] = {"ms": net_ms, "flop_per_px": CNN_FLOP_PER_PX, "tflops": tflops,
+                      "frac_of_bf16_peak": tflops / float(peaks["bf16_tflops"]),
+                      "kernels": "two fused tcgen05 kernels (layers 1-3, 4-6)" if net.uses_tcgen05 else "mma.sync"}
     with ils.Plan(H, W, C, LAM, P, EPS, N_ITERS) as p4:
-        u4 = p4.smooth(f)
+        errs = [rms(p4.smooth(fk), k) for k, fk in enumerate(frames)]
+        u4 = torch.empty_like(f)
         ms = timed(lambda: p4.smooth(f, out=u4))
-        out["plain_N4"] = {"fps": 1000.0 / ms, "ms": ms, "rms_to_converged": rms(u4)}
+        out["plain_N4"] = {"fps": 1000.0 / ms, "ms": ms, "rms_to_converged": float(np.mean(errs)),
+                           "rms_per_frame": errs}
     for iters in (1, 2):
         sm = ws.WarmSmoother(net, H, W, C, LAM, P, EPS, iters=iters, n_plain=N_ITERS, tau=ws.DEFAULT_TAU)
-        u, fb, d = sm.smooth(f)
-        res = {"rms_to_converged": rms(u), "fallback": fb, "last_change": d}
+        errs, fbs, deltas = [], 0, []
+        for k, fk in enumerate(frames):
+            u, fb, d = sm.smooth(fk)
+            errs.append(rms(u, k))
+            fbs += int(fb)
+            deltas.append(d)
+        u = torch.empty_like(f)
+        res = {"rms_to_converged": float(np.mean(errs)), "rms_per_frame": errs, "fallbacks": fbs,
+               "frames": len(frames), "last_change": deltas}
         res["ms"] = timed(lambda: sm.smooth(f, out=u))
         res["fps"] = 1000.0 / res["ms"]
         out[f"warm_{iters}_iter"] = res
@@ -363,6 +454,7 @@ def run_ours(args):
         plan.set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
+    pct = np.percentile(step_ms, [10, 50, 90]) if step_ms else [0.0, 0.0, 0.0]
 
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -413,7 +505,10 @@ def run_ours(args):
                          "traffic_unit": "GB per launch (ncu dram read + write)",
                          "launch_timing": "events around every launch, second loop of the same K steps",
                          "algorithmic_bytes_per_launch": per_kind[dom],
-                         "whole_step_gbs": whole, "whole_step_frac": whole / peak},
+                         "whole_step_gbs": whole, "whole_step_frac": whole / peak,
+                         "model": "fused: (20N+4) B per pixel and channel; an unfused stencil / FFT / "
+                                  "solve / IFFT sequence would move ~28 B per pixel, channel and iteration"},
+            "step_ms_p10_p50_p90": [float(v) for v in pct],
             "kernels": {k: {"launches": v[1], "ms_total": v[0], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                         for k, v in prof.items()},
             "e2e": None if e2e_fps is None else {"value": e2e_fps, "unit": "fps",
@@ -423,6 +518,10 @@ def run_ours(args):
             "clocks": clocks,
         }
         if not args.no_extras:
+            ksteps = max(3, min(args.steps, 10))
+            line["gray"] = gray_leg(ils, torch, dev, ksteps, flush)
+            line["welsch"] = welsch_leg(ils, torch, dev, ksteps, flush)
+            line["sweep_4k"] = sweep_4k_leg(ils, torch, dev, 5, flush)
             line["adjoint"] = adjoint_leg(ils, torch, dev, max(3, min(args.steps, 20)))
             line["batch"] = batch_leg(ils, torch, dev, max(3, min(args.steps, 10)), flush)
             line["warm_start"] = warm_leg(torch, dev, max(3, min(args.steps, 10)), flush)
