@@ -50,6 +50,7 @@ __all__ = [
     "adam_step",
     "C0_WELSCH", "phi_welsch", "dphi_welsch", "d2phi_welsch", "g2_welsch", "mu_welsch",
     "ils_channel_welsch", "ils_smooth_welsch", "energy_welsch", "ils_backward_welsch",
+    "LUMA_BT601", "luma", "detail_enhance", "ils_smooth_luma",
 ]
 
 
@@ -345,6 +346,38 @@ def ils_backward_welsch(f, grad_u, lam, gamma, N, c=None, u0=None, split=False):
         g = (lam / 2.0) * (grad_x_T(g2_welsch(grad_x(un), gamma, c) * grad_x(r))
                            + grad_y_T(g2_welsch(grad_y(un), gamma, c) * grad_y(r)))
     return (gf, g) if split else gf + g
+
+
+# ----------------------------------------------------------------------------
+# Colour option (I) of Sec. 3.4 and detail enhancement (the paper's figures: details
+# boosted k = 3 times)
+# ----------------------------------------------------------------------------
+
+LUMA_BT601 = (0.299, 0.587, 0.114)
+
+
+def luma(f_rgb):
+    """Y of an RGB image (3 x H x W): the BT.601 luma weights.  Reading: Sec. 3.4 names the
+    YUV luminance without a matrix."""
+    f = np.asarray(f_rgb, dtype=np.float64)
+    return LUMA_BT601[0] * f[0] + LUMA_BT601[1] * f[1] + LUMA_BT601[2] * f[2]
+
+
+def detail_enhance(f, u, k):
+    """Base u plus k times the detail layer f - u (k = 0: the smoothed image, k = 1: f)."""
+    f = np.asarray(f, dtype=np.float64)
+    return np.asarray(u, dtype=np.float64) + k * (f - np.asarray(u, dtype=np.float64))
+
+
+def ils_smooth_luma(f_rgb, lam=1.0, p=0.8, eps=1e-4, N=4, k=0.0):
+    """Option (I) of Sec. 3.4: ILS on the luminance only.  Y = luma(f); u_Y = ILS(Y), detail
+    enhanced by k; the chroma (colour differences) is kept, so every RGB channel changes by
+    the change of Y:  out_c = f_c + (Y' - Y),  Y' = u_Y + k (Y - u_Y)."""
+    f = np.asarray(f_rgb, dtype=np.float64)
+    Y = luma(f)
+    uY = ils_channel(Y, lam, p, eps, N)
+    Yp = detail_enhance(Y, uY, k)
+    return f + (Yp - Y)[None, :, :]
 
 
 # ----------------------------------------------------------------------------

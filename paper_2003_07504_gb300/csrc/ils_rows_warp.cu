@@ -156,8 +156,8 @@ struct WarpRow {
 // STAGE (with SHARED): the f rows of the output rows are copied to shared memory
 // asynchronously at the start (behind the inverse transforms) instead of being loaded in
 // the stencil.
-template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN>
-__global__ void __launch_bounds__((ROWS + 2) * 32, (ROWS + 2) * 32 <= 256 ? 2 : 1)
+template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN, int MINB>
+__global__ void __launch_bounds__((ROWS + 2) * 32, MINB)
 row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                     const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
                     float* __restrict__ u_ckpt) {
@@ -332,8 +332,9 @@ struct WarpRowEntry {
   InvFn inv;
 };
 
-// STAGE only where the staged rows still leave room for two CTAs per SM.
-template <int L, int RF, int RI, bool STAGE, bool SHARED>
+// STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
+// the register allocation must allow (2 at 256 threads = 128 registers per thread).
+template <int L, int RF, int RI, bool STAGE, bool SHARED, int MINB = ((RF + 2) * 32 <= 256 ? 2 : 1)>
 constexpr WarpRowEntry warp_entry() {
   static_assert(SHARED || !STAGE, "f staging is part of the shared-mu stencil");
   return WarpRowEntry{32 * L,
@@ -341,8 +342,10 @@ constexpr WarpRowEntry warp_entry() {
                       RI,
                       WarpRow<L>::BUF,
                       STAGE ? RF * 32 * L : 0,
-                      {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0>, row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1>},
-                      {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0>, row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1>},
+                      {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0, MINB>,
+                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB>},
+                      {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB>,
+                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>},
                       row_warp_inv_kernel<L, RI>};
 }
 
@@ -357,6 +360,7 @@ const WarpRowEntry kWarpRows[] = {
     warp_entry<30, 6, 8, false, false>(),    // W = 1920, per-pair stencil
     warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
     warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
+    warp_entry<30, 6, 8, false, false, 3>(), // W = 1920, per-pair stencil, 3 CTAs per SM (84 registers)
 };
 
 }  // namespace

@@ -476,3 +476,45 @@ def test_welsch_adjoint_matches_finite_differences():
         num = (np.sum(gu * O.ils_channel_welsch(f + h * d, lam, gamma, N))
                - np.sum(gu * O.ils_channel_welsch(f - h * d, lam, gamma, N))) / (2 * h)
         assert np.sum(got * d) == pytest.approx(num, rel=1e-6, abs=1e-9)
+
+
+# ---------------------------------------------------------------- luminance-only colour mode and detail enhancement
+
+def yuv_from_rgb(f):
+    # a full YUV transform (BT.601 luma; U, V scaled colour differences) and its inverse,
+    # written independently of the oracle's shortcut
+    R, G, B = f
+    Y = 0.299 * R + 0.587 * G + 0.114 * B
+    return Y, 0.492 * (B - Y), 0.877 * (R - Y)
+
+
+def rgb_from_yuv(Y, U, V):
+    R = Y + V / 0.877
+    B = Y + U / 0.492
+    G = (Y - 0.299 * R - 0.114 * B) / 0.587
+    return np.stack([R, G, B])
+
+
+def test_luma_mode_is_smoothing_y_in_yuv_and_converting_back():
+    f = synth.voronoi_texture(20, 24, 3, K=5, A=0.05, Tmin=3, Tmax=5, sigma=0.02, seed=3).astype(np.float64)
+    for k in (0.0, 3.0):
+        Y, U, V = yuv_from_rgb(f)
+        uY = O.ils_channel(Y, 1.0, 0.8, 1e-4, 4)
+        want = rgb_from_yuv(uY + k * (Y - uY), U, V)
+        np.testing.assert_allclose(O.ils_smooth_luma(f, 1.0, 0.8, 1e-4, 4, k), want, atol=1e-12)
+
+
+def test_luma_mode_on_a_gray_image_equals_per_channel_smoothing():
+    g = small_image(16, 20, seed=23)
+    f = np.stack([g, g, g])
+    np.testing.assert_allclose(O.ils_smooth_luma(f, 1.0, 0.8, 1e-4, 4), O.ils_smooth(f, 1.0, 0.8, 1e-4, 4),
+                               atol=1e-12)
+
+
+def test_detail_enhance_limits():
+    f = small_image(10, 12, seed=29)
+    u = O.ils_channel(f, 1.0, 0.8, 1e-4, 4)
+    np.testing.assert_allclose(O.detail_enhance(f, u, 0.0), u, atol=0)
+    np.testing.assert_allclose(O.detail_enhance(f, u, 1.0), f, atol=1e-15)
+    # the detail layer is scaled by k: (out - u) = k (f - u)
+    np.testing.assert_allclose(O.detail_enhance(f, u, 3.0) - u, 3.0 * (f - u), atol=1e-14)
