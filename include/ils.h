@@ -98,6 +98,27 @@ float ils_plan_c(const ils_plan* plan);
 ils_status ils_smooth(ils_plan* plan, const float* f, float* u, void* stream);
 
 /*
+ * ils_smooth_enhance - detail enhancement: out = u + k (f - u) with u = ILS(f) (Algorithm 1
+ * from u^0 = f), fused into the final inverse row pass (which reads f instead of writing u).
+ * k = 0 gives u, k = 1 gives f; the paper's figures boost details with k = 3.
+ *   f, out : device pointers, C x H x W float32, non-overlapping.  k finite.
+ */
+ils_status ils_smooth_enhance(ils_plan* plan, const float* f, float* out, float k, void* stream);
+
+/*
+ * ils_smooth_luma - colour option (I) of Sec. 3.4: smooth only the luminance of an RGB
+ * image.  Y = 0.299 R + 0.587 G + 0.114 B (BT.601 luma; the paper names no matrix),
+ * u_Y = ILS(Y), Y' = u_Y + k (Y - u_Y); the chroma is kept, so every channel changes by
+ * Y' - Y:  out_c = rgb_c + (1 - k)(u_Y - Y), in the final inverse row pass.  One channel
+ * is smoothed instead of three.
+ *   plan : made with C = 1 for the image's H x W (either penalty).
+ *   rgb, out : device pointers, 3 x H x W float32 (planar R, G, B), non-overlapping.
+ * The first call on a plan allocates an H x W float32 luminance buffer that the plan keeps
+ * (make it before any stream capture).  Returns ILS_ERR_INVALID_ARG if C != 1.
+ */
+ils_status ils_smooth_luma(ils_plan* plan, const float* rgb, float* out, float k, void* stream);
+
+/*
  * ils_smooth_from - Algorithm 1 started from a given u^0 instead of f (warm start).
  *   u0 : device pointer, C x H x W float32 (read only); may equal f.
  *   u  : device pointer output; must overlap neither f nor u0.

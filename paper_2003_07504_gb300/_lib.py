@@ -49,6 +49,8 @@ SIGNATURES = {
     "ils_plan_destroy": (c_int, [c_void_p]),
     "ils_plan_c": (c_float, [c_void_p]),
     "ils_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_smooth_enhance": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
+    "ils_smooth_luma": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
     "ils_smooth_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_checkpointed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -2,6 +2,7 @@
 // the iteration driver of Algorithm 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -25,6 +26,7 @@ struct ils_plan {
   float2* spec[2];     // ping-pong row-spectrum workspaces, C*H*(W/2) complex each
   float* stage_f;      // device staging for ils_smooth_host
   float* stage_u;
+  float* luma;         // luminance of ils_smooth_luma (H x W), allocated at its first call
   // optional per-kernel event timing (ils_set_profiling)
   bool profiling;
   std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
@@ -94,6 +96,7 @@ void free_plan_memory(ils_plan* pl) {
   cudaFree(pl->spec[1]);
   cudaFree(pl->stage_f);
   cudaFree(pl->stage_u);
+  cudaFree(pl->luma);
   cudaFree(pl->tab.twW);
   cudaFree(pl->tab.twH);
   cudaFree(pl->tab.ax);
@@ -117,7 +120,14 @@ cudaError_t mark(ils_plan* pl, int slot, int kind, cudaStream_t st) {
   return cudaEventRecord(pl->ev[slot], st);
 }
 
-ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st) {
+// Y = 0.299 R + 0.587 G + 0.114 B (BT.601 luma) of a 3-plane image, n pixels per plane.
+__global__ void luma_kernel(const float* __restrict__ rgb, float* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = fmaf(0.299f, rgb[i], fmaf(0.587f, rgb[n + i], 0.114f * rgb[2 * n + i]));
+}
+
+ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
+                   const Epilogue& epi = Epilogue()) {
   const size_t n = (size_t)pl->C * pl->H * pl->W;
   const size_t bytes = n * sizeof(float);
   cudaError_t e;
@@ -144,7 +154,7 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
   }
   if ((e = mark(pl, slot++, ILS_KERNEL_ROW_INVERSE, st))) return cuda_fail(e, "event");
   d.pdl = chain;
-  if ((e = launch_row_inverse(d, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st)))
+  if ((e = launch_row_inverse(d, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st, epi)))
     return cuda_fail(e, "inverse row pass launch");
   if ((e = mark(pl, slot, -1, st))) return cuda_fail(e, "event");
   if (pl->profiling) {
@@ -407,6 +417,43 @@ ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, fl
 ils_status ils_smooth(ils_plan* pl, const float* f, float* u, void* stream) {
   if (pl == nullptr || f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
   return ils_smooth_from(pl, f, nullptr, u, stream);
+}
+
+ils_status ils_smooth_enhance(ils_plan* pl, const float* f, float* out, float k, void* stream) {
+  if (pl == nullptr || f == nullptr || out == nullptr || !std::isfinite(k)) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  if (overlaps(f, out, bytes)) return ILS_ERR_INVALID_ARG;
+  Epilogue epi;
+  epi.mode = 1;
+  epi.s = 1.0f - k;
+  epi.f = f;
+  return run_ils(pl, f, nullptr, out, nullptr, static_cast<cudaStream_t>(stream), epi);
+}
+
+ils_status ils_smooth_luma(ils_plan* pl, const float* rgb, float* out, float k, void* stream) {
+  if (pl == nullptr || rgb == nullptr || out == nullptr || pl->C != 1 || !std::isfinite(k))
+    return ILS_ERR_INVALID_ARG;
+  const size_t n = (size_t)pl->H * pl->W;
+  if (overlaps(rgb, out, 3 * n * sizeof(float))) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (pl->N == 0) {  // u = Y: out = rgb
+    e = cudaMemcpyAsync(out, rgb, 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
+  }
+  if (pl->luma == nullptr) {
+    ils_status s = dev_alloc((void**)&pl->luma, n * sizeof(float));
+    if (s != ILS_OK) return s;
+  }
+  luma_kernel<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(rgb, pl->luma, n);
+  if ((e = cudaGetLastError())) return cuda_fail(e, "luma kernel launch");
+  Epilogue epi;
+  epi.mode = 2;
+  epi.s = 1.0f - k;
+  epi.f = pl->luma;
+  epi.rgb = rgb;
+  epi.plane2 = n / 2;
+  return run_ils(pl, pl->luma, nullptr, out, nullptr, st, epi);
 }
 
 ils_status ils_smooth_host(ils_plan* pl, const float* f_host, float* u_host, void* stream) {

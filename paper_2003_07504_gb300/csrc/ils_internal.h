@@ -50,6 +50,37 @@ __device__ __forceinline__ float mu_pen(float g, const MuParams& mp) {
   else return mu_welsch(g, mp);
 }
 
+// Output stage of the final inverse row pass (u = the smoothed image, pairs of pixels):
+//   mode 0: out = u;
+//   mode 1: out = f + s (u - f) per channel (detail enhancement: s = 1 - k, k the boost);
+//   mode 2: luminance-only colour (Sec. 3.4, option I): f is the luma Y of the 3-plane image
+//           rgb and out_c = rgb_c + s (u - Y) for the three planes.
+struct Epilogue {
+  int mode = 0;
+  float s = 1.0f;
+  const float* f = nullptr;
+  const float* rgb = nullptr;
+  size_t plane2 = 0;  // mode 2: pixel pairs per plane (H W / 2)
+  __device__ __forceinline__ void store(float2* out, size_t i, float2 u) const {
+    if (mode == 0) {
+      out[i] = u;
+      return;
+    }
+    const float2 fv = reinterpret_cast<const float2*>(f)[i];
+    const float dx = s * (u.x - fv.x), dy = s * (u.y - fv.y);
+    if (mode == 1) {
+      out[i] = make_float2(fv.x + dx, fv.y + dy);
+      return;
+    }
+    const float2* src = reinterpret_cast<const float2*>(rgb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 a = src[c * plane2 + i];
+      out[c * plane2 + i] = make_float2(a.x + dx, a.y + dy);
+    }
+  }
+};
+
 // Launch geometry picked by the host planner (validated before any launch).
 struct Geometry {
   int rows_fwd;      // output rows per CTA in the fused row pass (reads rows_fwd + 2 rows)
@@ -120,7 +151,7 @@ cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tabl
 cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables& t, float2* spec,
                              cudaStream_t stream);
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
-                               float* u, cudaStream_t stream);
+                               float* u, cudaStream_t stream, const Epilogue& epi = Epilogue());
 cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream);
@@ -148,7 +179,7 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
                               const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
                               cudaStream_t stream);
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
-                              cudaStream_t stream);
+                              cudaStream_t stream, const Epilogue& epi);
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream);
 
 // Warp-per-row kernels (ils_rows_warp.cu).
@@ -158,6 +189,6 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
                              const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
                              cudaStream_t stream);
 cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
-                             cudaStream_t stream);
+                             cudaStream_t stream, const Epilogue& epi);
 
 }  // namespace ils

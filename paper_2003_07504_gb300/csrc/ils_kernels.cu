@@ -304,7 +304,7 @@ row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
 template <int EPT>
 __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW,
-                   const float2* __restrict__ spec, float* __restrict__ u) {
+                   const float2* __restrict__ spec, float* __restrict__ u, Epilogue epi) {
   griddep_launch();
   griddep_wait();
   extern __shared__ float2 sm[];
@@ -324,8 +324,8 @@ row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
   }
   __syncthreads();
   fft_smem<EPT, true>(sm, planM, n, 1, M, twW, 2);
-  float2* dst = reinterpret_cast<float2*>(u) + ch * plane + (size_t)y0 * M;
-  for (int w = threadIdx.x; w < n * M; w += T) dst[w] = sm[smem_idx(w)];
+  const size_t rowoff = ch * plane + (size_t)y0 * M;
+  for (int w = threadIdx.x; w < n * M; w += T) epi.store(reinterpret_cast<float2*>(u), rowoff + w, sm[smem_idx(w)]);
 }
 
 // ---------------------------------------------------------------- host side
@@ -497,12 +497,13 @@ cudaError_t launch_col_solve(const ImageDesc& d, const Geometry& g, const Tables
 }
 
 cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tables& t, const float2* spec,
-                               float* u, cudaStream_t stream) {
-  if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream);
-  if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream);
+                               float* u, cudaStream_t stream, const Epilogue& epi) {
+  if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream, epi);
+  if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream, epi);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
   auto fn = g.ept_inv == 16 ? row_inverse_kernel<16> : row_inverse_kernel<32>;
-  return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u);
+  return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u,
+                  epi);
 }
 
 cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,

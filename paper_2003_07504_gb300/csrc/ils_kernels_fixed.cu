@@ -214,7 +214,8 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
 // natural order (complex m holds pixels 2m, 2m+1).  All threads call it (syncs inside).
 template <class PL>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
-                                                      const float2* __restrict__ twW, float2* dst);
+                                                      const float2* __restrict__ twW, float2* out, size_t rowoff,
+                                                      const Epilogue* epi);
 
 // Inverse real row FFT of strip rows 0..nrows-1 (global spectrum rows X(i)) into smem rows
 // 0..nrows-1 in natural order (complex m holds pixels 2m, 2m+1).  Three barrier-separated
@@ -234,14 +235,16 @@ __device__ __forceinline__ void rows_inverse_to_smem(float2* sm, int nrows, int 
   __syncthreads();
   unpack_c2r_rows<M>(sm, nrows, twW);
   __syncthreads();
-  fft_rows_smem_inverse<PL>(sm, i, j, i < nrows, twW, nullptr);
+  fft_rows_smem_inverse<PL>(sm, i, j, i < nrows, twW, nullptr, 0, nullptr);
 }
 
 // The inverse FFT stages on smem row i (input natural order, output natural order, to
-// smem row i, or to the global row `dst` when it is not null).
+// smem row i, or, when out is not null, to pixel pairs rowoff + m of the global output
+// image through the epilogue).
 template <class PL>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
-                                                      const float2* __restrict__ twW, float2* dst) {
+                                                      const float2* __restrict__ twW, float2* out, size_t rowoff,
+                                                      const Epilogue* epi) {
   constexpr int M = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = M / R0, NS1 = M / R1, NSL = M / RL;
   auto U = [&](int m) -> float2& { return sm[smem_idx(i * M + m)]; };
@@ -280,10 +283,10 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
       for (int r = 0; r < RL; ++r) v[r] = U(j + r * NSL);
       bfly<M, RL, NSL, true>(v, j, twW, 2);
     }
-    if (dst != nullptr) {
+    if (out != nullptr) {
       if (live && j < NSL) {
 #pragma unroll
-        for (int r = 0; r < RL; ++r) dst[j + r * NSL] = v[r];
+        for (int r = 0; r < RL; ++r) epi->store(out, rowoff + j + r * NSL, v[r]);
       }
       return;
     }
@@ -445,7 +448,7 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
 template <class PL, int ROWS>
 __global__ void __launch_bounds__(ROWS * PL::TPS, 1)
 row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ spec,
-                     float* __restrict__ u) {
+                     float* __restrict__ u, Epilogue epi) {
   griddep_launch();
   griddep_wait();
   constexpr int M = PL::N, TPS = PL::TPS;
@@ -466,8 +469,8 @@ row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2*
     __syncthreads();
     unpack_c2r_rows<M>(sm, n, twW);
     __syncthreads();
-    float2* dst = reinterpret_cast<float2*>(u) + ch * plane + (size_t)(y0 + (i < n ? i : 0)) * M;
-    fft_rows_smem_inverse<PL>(sm, i, j, i < n, twW, dst);
+    const size_t rowoff = ch * plane + (size_t)(y0 + (i < n ? i : 0)) * M;
+    fft_rows_smem_inverse<PL>(sm, i, j, i < n, twW, reinterpret_cast<float2*>(u), rowoff, &epi);
   }
 }
 
@@ -475,7 +478,7 @@ row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2*
 
 using RowFwdFn = void (*)(int, int, const float2*, MuParams, const float*, const float*, const float2*, float2*,
                           float*);
-using RowInvFn = void (*)(int, int, const float2*, const float2*, float*);
+using RowInvFn = void (*)(int, int, const float2*, const float2*, float*, Epilogue);
 using ColFn = void (*)(int, int, const float2*, const float*, const float*, float, float2*);
 
 struct RowEntry {
@@ -594,12 +597,12 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
 }
 
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, const Epilogue& epi) {
   const RowEntry& r = kRows[idx];
   const int threads = r.rows_inv * r.tps;
   const size_t smem = row_smem(r.rows_inv, r.M);
   const int tiles = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
-  return launch_k(d.pdl, r.inv, tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u);
+  return launch_k(d.pdl, r.inv, tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u, epi);
 }
 
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream) {

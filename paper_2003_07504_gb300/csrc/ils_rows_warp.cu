@@ -88,8 +88,10 @@ struct WarpRow {
     __syncwarp();
   }
 
-  // Inverse real transform of X straight to a global row of u.
-  __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* dst, float2* buf,
+  // Inverse real transform of X straight to global memory through the epilogue (pair
+  // index rowoff + m of the output image).
+  __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* out,
+                                                               size_t rowoff, const Epilogue& epi, float2* buf,
                                                                int lane, const float2* __restrict__ twW) {
     float2 v[L];
 #pragma unroll
@@ -105,11 +107,11 @@ struct WarpRow {
         v[n2] = c2(s.x - t.y, s.y + t.x);
       }
     }
-    float2 out[32];
-    fft<true>(v, out, buf, lane, twW);
+    float2 res[32];
+    fft<true>(v, res, buf, lane, twW);
     if (lane < L) {
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) dst[lane + L * k1] = out[k1];
+      for (int k1 = 0; k1 < 32; ++k1) epi.store(out, rowoff + lane + L * k1, res[k1]);
     }
   }
 
@@ -308,7 +310,8 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
 // Final inverse row pass: one warp per row, ROWS rows per CTA.
 template <int L, int ROWS>
 __global__ void __launch_bounds__(ROWS * 32)
-row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u) {
+row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u,
+                    Epilogue epi) {
   griddep_launch();
   griddep_wait();
   using WR = WarpRow<L>;
@@ -320,11 +323,11 @@ row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restr
   const int y = (blockIdx.x - ch * strips) * ROWS + w;
   if (y >= H) return;  // warp-uniform; no CTA barrier below
   const size_t off = ch * (size_t)H * M + (size_t)y * M;
-  WR::inverse_row_to_global(spec + off, reinterpret_cast<float2*>(u) + off, sm + w * WR::BUF, lane, twW);
+  WR::inverse_row_to_global(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane, twW);
 }
 
 using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
-using InvFn = void (*)(int, const float2*, const float2*, float*);
+using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
@@ -398,11 +401,11 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
 }
 
 cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, const Epilogue& epi) {
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
   const size_t smem = (size_t)r.rows_inv * r.buf * sizeof(float2);
-  return launch_k(d.pdl, r.inv, blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u);
+  return launch_k(d.pdl, r.inv, blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u, epi);
 }
 
 }  // namespace ils

@@ -97,6 +97,30 @@ class Plan:
             _lib.check(st, "ils_smooth_from")
         return out
 
+    def enhance(self, f: torch.Tensor, k: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Detail enhancement u + k (f - u), u = ILS(f), in the final inverse pass."""
+        _check_image(self._as3d(f), self.shape, "f")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_image(self._as3d(out), self.shape, "out")
+        _lib.check(_lib.lib().ils_smooth_enhance(self._h, f.data_ptr(), out.data_ptr(), float(k),
+                                                 _stream_ptr(stream)), "ils_smooth_enhance")
+        return out
+
+    def smooth_luma(self, rgb: torch.Tensor, k: float = 0.0, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+        """Luminance-only smoothing of a 3 x H x W RGB image (plan made with C = 1): every channel
+        changes by the change of Y = 0.299 R + 0.587 G + 0.114 B; k > 0 boosts Y's details."""
+        if self.C != 1:
+            raise ValueError("smooth_luma needs a plan with C = 1")
+        _check_image(rgb, (3, self.H, self.W), "rgb")
+        if out is None:
+            out = torch.empty_like(rgb)
+        _check_image(out, (3, self.H, self.W), "out")
+        _lib.check(_lib.lib().ils_smooth_luma(self._h, rgb.data_ptr(), out.data_ptr(), float(k),
+                                              _stream_ptr(stream)), "ils_smooth_luma")
+        return out
+
     def smooth_checkpointed(self, f: torch.Tensor, out: torch.Tensor | None = None,
                             u0: torch.Tensor | None = None, stream=None):
         """Forward pass that also returns the iterates u^0..u^{N-1} (N x C x H x W) for backward()."""

@@ -277,3 +277,45 @@ def test_welsch_rejects_bad_parameters(ils):
             ils.Plan(16, 16, 1, 1.0, N=2, penalty="welsch", gamma=gamma)
     with pytest.raises(ILSError):
         ils.Plan(16, 16, 1, -1.0, N=2, penalty="welsch", gamma=0.1)
+
+
+# -------------------------------------------------------------- detail enhancement and luminance-only colour (epilogues)
+
+@pytest.mark.parametrize("H,W,C", [(256, 256, 1), (40, 1920, 3), (16, 3840, 1), (60, 80, 2), (27, 250, 1)])
+def test_enhance_matches_oracle(ils, H, W, C):
+    import torch
+    f = image(H, W, C, seed=H + 5 * W + C)
+    ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    u_want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
+    with ils.Plan(H, W, C, 1.0, 0.8, 1e-4, 4) as plan:
+        for k in (0.0, 3.0):
+            out = plan.enhance(ft, k).cpu().numpy()
+            want = O.detail_enhance(f.astype(np.float64), u_want, k)
+            # the detail layer is amplified k times, so is the FP32 error of u
+            assert_parity(out, want, tol_max=MAX_ABS_TOL * max(1.0, abs(1 - k)), tol_rms=RMS_TOL * max(1.0, abs(1 - k)))
+        assert torch.equal(plan.enhance(ft, 1.0), ft)  # s = 0: exactly f
+
+
+@pytest.mark.parametrize("H,W", [(256, 256), (40, 1920), (16, 3840), (27, 250)])
+def test_luma_matches_oracle(ils, H, W):
+    import torch
+    f = image(H, W, 3, seed=7 * H + W)
+    ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    with ils.Plan(H, W, 1, 1.0, 0.8, 1e-4, 4) as plan:
+        for k in (0.0, 3.0):
+            out = plan.smooth_luma(ft, k).cpu().numpy()
+            want = O.ils_smooth_luma(f.astype(np.float64), 1.0, 0.8, 1e-4, 4, k)
+            assert_parity(out, want, tol_max=MAX_ABS_TOL * max(1.0, abs(1 - k)), tol_rms=RMS_TOL * max(1.0, abs(1 - k)))
+        with pytest.raises(ValueError):
+            plan.smooth_luma(ft[:2].contiguous())
+
+
+def test_luma_with_the_welsch_penalty(ils):
+    import torch
+    H, W, lam, gamma, N = 48, 64, 20.0, 10 / 255, 6
+    f = image(H, W, 3, seed=77)
+    Y = O.luma(f.astype(np.float64))
+    want = f.astype(np.float64) + (O.ils_channel_welsch(Y, lam, gamma, N) - Y)[None]
+    with ils.Plan(H, W, 1, lam, N=N, penalty="welsch", gamma=gamma) as plan:
+        out = plan.smooth_luma(torch.from_numpy(np.ascontiguousarray(f)).cuda()).cpu().numpy()
+    assert_parity(out, want)
