@@ -61,14 +61,16 @@ struct Epilogue {
   const float* f = nullptr;
   const float* rgb = nullptr;
   size_t plane2 = 0;  // mode 2: pixel pairs per plane (H W / 2)
+  // MODE is the kernel's compile-time copy of `mode` (one instantiation per mode)
+  template <int MODE>
   __device__ __forceinline__ void store(float2* out, size_t i, float2 u) const {
-    if (mode == 0) {
+    if constexpr (MODE == 0) {
       out[i] = u;
       return;
     }
     const float2 fv = reinterpret_cast<const float2*>(f)[i];
     const float dx = s * (u.x - fv.x), dy = s * (u.y - fv.y);
-    if (mode == 1) {
+    if constexpr (MODE == 1) {
       out[i] = make_float2(fv.x + dx, fv.y + dy);
       return;
     }

@@ -301,7 +301,7 @@ row_adjoint_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
 }
 
 // ---------------------------------------------------------------- (3) final inverse row pass
-template <int EPT>
+template <int EPT, int EPI>
 __global__ void __launch_bounds__(512, EPT <= 16 ? 2 : 1)
 row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restrict__ twW,
                    const float2* __restrict__ spec, float* __restrict__ u, Epilogue epi) {
@@ -325,7 +325,8 @@ row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
   __syncthreads();
   fft_smem<EPT, true>(sm, planM, n, 1, M, twW, 2);
   const size_t rowoff = ch * plane + (size_t)y0 * M;
-  for (int w = threadIdx.x; w < n * M; w += T) epi.store(reinterpret_cast<float2*>(u), rowoff + w, sm[smem_idx(w)]);
+  for (int w = threadIdx.x; w < n * M; w += T)
+    epi.template store<EPI>(reinterpret_cast<float2*>(u), rowoff + w, sm[smem_idx(w)]);
 }
 
 // ---------------------------------------------------------------- host side
@@ -457,8 +458,12 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(row_forward_kernel<32, false, 1>))) return e;
   if ((e = allow_smem(col_solve_kernel<16>))) return e;
   if ((e = allow_smem(col_solve_kernel<32>))) return e;
-  if ((e = allow_smem(row_inverse_kernel<16>))) return e;
-  if ((e = allow_smem(row_inverse_kernel<32>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 0>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 0>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 1>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 1>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 2>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 2>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<32, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 1>))) return e;
@@ -501,7 +506,9 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
   if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream, epi);
   if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream, epi);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
-  auto fn = g.ept_inv == 16 ? row_inverse_kernel<16> : row_inverse_kernel<32>;
+  auto fn = epi.mode == 0   ? (g.ept_inv == 16 ? row_inverse_kernel<16, 0> : row_inverse_kernel<32, 0>)
+            : epi.mode == 1 ? (g.ept_inv == 16 ? row_inverse_kernel<16, 1> : row_inverse_kernel<32, 1>)
+                            : (g.ept_inv == 16 ? row_inverse_kernel<16, 2> : row_inverse_kernel<32, 2>);
   return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u,
                   epi);
 }

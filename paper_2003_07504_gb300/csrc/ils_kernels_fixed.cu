@@ -212,7 +212,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
 // ---------------------------------------------------------------- row passes
 // Inverse real row FFT of row `i` of the strip (global spectrum row X) into smem row i,
 // natural order (complex m holds pixels 2m, 2m+1).  All threads call it (syncs inside).
-template <class PL>
+template <class PL, int EPI = 0>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
                                                       const float2* __restrict__ twW, float2* out, size_t rowoff,
                                                       const Epilogue* epi);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void rows_inverse_to_smem(float2* sm, int nrows, int 
 // The inverse FFT stages on smem row i (input natural order, output natural order, to
 // smem row i, or, when out is not null, to pixel pairs rowoff + m of the global output
 // image through the epilogue).
-template <class PL>
+template <class PL, int EPI>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
                                                       const float2* __restrict__ twW, float2* out, size_t rowoff,
                                                       const Epilogue* epi) {
@@ -286,7 +286,7 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
     if (out != nullptr) {
       if (live && j < NSL) {
 #pragma unroll
-        for (int r = 0; r < RL; ++r) epi->store(out, rowoff + j + r * NSL, v[r]);
+        for (int r = 0; r < RL; ++r) epi->template store<EPI>(out, rowoff + j + r * NSL, v[r]);
       }
       return;
     }
@@ -445,7 +445,7 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
 }
 
 // Final inverse row pass: strips of ROWS rows, last stage written straight to u.
-template <class PL, int ROWS>
+template <class PL, int ROWS, int EPI>
 __global__ void __launch_bounds__(ROWS * PL::TPS, 1)
 row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ spec,
                      float* __restrict__ u, Epilogue epi) {
@@ -470,7 +470,7 @@ row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2*
     unpack_c2r_rows<M>(sm, n, twW);
     __syncthreads();
     const size_t rowoff = ch * plane + (size_t)(y0 + (i < n ? i : 0)) * M;
-    fft_rows_smem_inverse<PL>(sm, i, j, i < n, twW, reinterpret_cast<float2*>(u), rowoff, &epi);
+    fft_rows_smem_inverse<PL, EPI>(sm, i, j, i < n, twW, reinterpret_cast<float2*>(u), rowoff, &epi);
   }
 }
 
@@ -484,7 +484,7 @@ using ColFn = void (*)(int, int, const float2*, const float*, const float*, floa
 struct RowEntry {
   int M, tps, rows_fwd, rows_inv;
   RowFwdFn first[2], later[2];  // per penalty (MuParams::welsch)
-  RowInvFn inv;
+  RowInvFn inv[3];              // per epilogue mode
 };
 struct ColEntry {
   int H, tps, G;
@@ -499,7 +499,7 @@ constexpr RowEntry row_entry() {
                   RI,
                   {row_fwd_fixed_kernel<PL, RF, true, 0>, row_fwd_fixed_kernel<PL, RF, true, 1>},
                   {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>},
-                  row_inv_fixed_kernel<PL, RI>};
+                  {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>}};
 }
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
@@ -575,7 +575,8 @@ cudaError_t fixed_set_attributes() {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
-    if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
+    for (int m = 0; m < 3; ++m)
+      if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   for (const ColEntry& c : kCols) {
     const int s = (int)((size_t)smem_elems(c.H * c.G) * sizeof(float2));
@@ -602,7 +603,7 @@ cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, cons
   const int threads = r.rows_inv * r.tps;
   const size_t smem = row_smem(r.rows_inv, r.M);
   const int tiles = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
-  return launch_k(d.pdl, r.inv, tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u, epi);
+  return launch_k(d.pdl, r.inv[epi.mode], tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u, epi);
 }
 
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream) {

@@ -90,6 +90,7 @@ struct WarpRow {
 
   // Inverse real transform of X straight to global memory through the epilogue (pair
   // index rowoff + m of the output image).
+  template <int EPI>
   __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* out,
                                                                size_t rowoff, const Epilogue& epi, float2* buf,
                                                                int lane, const float2* __restrict__ twW) {
@@ -111,7 +112,7 @@ struct WarpRow {
     fft<true>(v, res, buf, lane, twW);
     if (lane < L) {
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) epi.store(out, rowoff + lane + L * k1, res[k1]);
+      for (int k1 = 0; k1 < 32; ++k1) epi.template store<EPI>(out, rowoff + lane + L * k1, res[k1]);
     }
   }
 
@@ -307,8 +308,8 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   }
 }
 
-// Final inverse row pass: one warp per row, ROWS rows per CTA.
-template <int L, int ROWS>
+// Final inverse row pass: one warp per row, ROWS rows per CTA; EPI: the epilogue mode.
+template <int L, int ROWS, int EPI>
 __global__ void __launch_bounds__(ROWS * 32)
 row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u,
                     Epilogue epi) {
@@ -323,7 +324,8 @@ row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restr
   const int y = (blockIdx.x - ch * strips) * ROWS + w;
   if (y >= H) return;  // warp-uniform; no CTA barrier below
   const size_t off = ch * (size_t)H * M + (size_t)y * M;
-  WR::inverse_row_to_global(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane, twW);
+  WR::template inverse_row_to_global<EPI>(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane,
+                                          twW);
 }
 
 using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
@@ -332,7 +334,7 @@ using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
   FwdFn first[2], later[2];  // per penalty (MuParams::welsch)
-  InvFn inv;
+  InvFn inv[3];              // per epilogue mode
 };
 
 // STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
@@ -349,7 +351,7 @@ constexpr WarpRowEntry warp_entry() {
                        row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB>},
                       {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB>,
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>},
-                      row_warp_inv_kernel<L, RI>};
+                      {row_warp_inv_kernel<L, RI, 0>, row_warp_inv_kernel<L, RI, 1>, row_warp_inv_kernel<L, RI, 2>}};
 }
 
 // The first entry of a length is its default; the others are autotune alternatives.
@@ -384,7 +386,8 @@ cudaError_t warp_set_attributes() {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
-    if ((e = cudaFuncSetAttribute(r.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
+    for (int m = 0; m < 3; ++m)
+      if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   return cudaSuccess;
 }
@@ -405,7 +408,7 @@ cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
   const size_t smem = (size_t)r.rows_inv * r.buf * sizeof(float2);
-  return launch_k(d.pdl, r.inv, blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u, epi);
+  return launch_k(d.pdl, r.inv[epi.mode], blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u, epi);
 }
 
 }  // namespace ils
