@@ -15,6 +15,7 @@ paper's LaTeX source numbers them:
   Eq. 8  the per-iteration least-squares problem (ILS)                                (Sec. 3.2)
   Eq. 9  its periodic-boundary FFT solution                                           (Sec. 3.2)
   Eq. 11 c >= c0 = p*eps^(p/2-1), with c = c0 used throughout                         (Sec. 3.3, App. B)
+  Eq. 12-14 half-quadratic splitting (the comparison method), Eq. 15-17 its Huber view  (Sec. 3.5)
   Eq. 18 Welsch penalty phi_W;  Eq. 19 its mu update;  Eq. 20 its c0 = 2              (Sec. 3.5, Sec. 5)
   Algorithm 1: u^0 = f; for n = 0..N-1: mu^n from u^n (Eq. 7), u^{n+1} from Eq. 9.
   Sec. 3.4: colour images are smoothed one RGB channel at a time.
@@ -51,6 +52,7 @@ __all__ = [
     "C0_WELSCH", "phi_welsch", "dphi_welsch", "d2phi_welsch", "g2_welsch", "mu_welsch",
     "ils_channel_welsch", "ils_smooth_welsch", "energy_welsch", "ils_backward_welsch",
     "LUMA_BT601", "luma", "detail_enhance", "ils_smooth_luma",
+    "hqs_shrink_l1", "hqs_channel", "hqs_smooth",
 ]
 
 
@@ -346,6 +348,52 @@ def ils_backward_welsch(f, grad_u, lam, gamma, N, c=None, u0=None, split=False):
         g = (lam / 2.0) * (grad_x_T(g2_welsch(grad_x(un), gamma, c) * grad_x(r))
                            + grad_y_T(g2_welsch(grad_y(un), gamma, c) * grad_y(r)))
     return (gf, g) if split else gf + g
+
+
+# ----------------------------------------------------------------------------
+# Half-quadratic splitting (Sec. 3.5, Eq. 12-14): the comparison method.  With the L1
+# penalty phi(x) = |x| (anisotropic total variation, the case Sec. 3.5 analyses), Q1 is the
+# soft threshold of grad u at lam / (2 beta_n) (Eq. 15-17, Appendix C) and Q2 is Eq. 9's FFT
+# solve with weight beta_n in place of lam c / 2; beta_n = kappa beta_{n-1}.
+# ----------------------------------------------------------------------------
+
+def hqs_shrink_l1(x, lam, beta):
+    """Q1 of Eq. 14 for phi = |x|: argmin_mu beta (x - mu)^2 + lam |mu| = soft threshold at lam/(2 beta)."""
+    x = np.asarray(x, dtype=np.float64)
+    t = lam / (2.0 * beta)
+    return np.sign(x) * np.maximum(np.abs(x) - t, 0.0)
+
+
+def hqs_channel(f, lam, N, beta0=None, kappa=2.0, u0=None, return_iterates=False):
+    """Eq. 14 on one H x W channel (float64), phi = |x|: u^0 = f; for n = 0..N-1:
+    mu^n = shrink(grad u^n, lam / (2 beta_n)), u^{n+1} = argmin (u - f)^2 + beta_n (grad u - mu^n)^2
+    (Q2, solved by the periodic FFT as Eq. 9), beta_{n+1} = kappa beta_n.  beta0 defaults to 2 lam
+    (the setting the paper uses in Fig. 11); kappa = 2 is a reading (the paper only requires kappa > 1)."""
+    f = np.asarray(f, dtype=np.float64)
+    H, W = f.shape
+    beta = 2.0 * lam if beta0 is None else float(beta0)
+    Fdx, Fdy = gradient_transfer_functions(H, W)
+    Ff = dft2(f)
+    u = f.copy() if u0 is None else np.asarray(u0, dtype=np.float64).copy()
+    iterates = [u.copy()]
+    for _ in range(int(N)):
+        mu_x = hqs_shrink_l1(grad_x(u), lam, beta)
+        mu_y = hqs_shrink_l1(grad_y(u), lam, beta)
+        den = 1.0 + beta * (np.abs(Fdx) ** 2 + np.abs(Fdy) ** 2)
+        num = Ff + beta * (np.conj(Fdx) * dft2(mu_x) + np.conj(Fdy) * dft2(mu_y))
+        u = np.real(idft2(num / den))
+        beta *= kappa
+        if return_iterates:
+            iterates.append(u.copy())
+    return (u, iterates) if return_iterates else u
+
+
+def hqs_smooth(f, lam=0.25, N=4, beta0=None, kappa=2.0):
+    """Half-quadratic splitting (phi = |x|) on a C x H x W (or H x W) image, channels independent."""
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 2:
+        return hqs_channel(f, lam, N, beta0, kappa)
+    return np.stack([hqs_channel(f[c], lam, N, beta0, kappa) for c in range(f.shape[0])])
 
 
 # ----------------------------------------------------------------------------

@@ -518,3 +518,50 @@ def test_detail_enhance_limits():
     np.testing.assert_allclose(O.detail_enhance(f, u, 1.0), f, atol=1e-15)
     # the detail layer is scaled by k: (out - u) = k (f - u)
     np.testing.assert_allclose(O.detail_enhance(f, u, 3.0) - u, 3.0 * (f - u), atol=1e-14)
+
+
+# ---------------------------------------------------------------- half-quadratic splitting (Sec. 3.5)
+
+def test_hqs_q1_is_the_argmin_and_matches_huber():
+    # Q1 of Eq. 14 by brute force over mu, and Eq. 17: min_mu g_H = the Huber penalty of Eq. 16
+    lam, beta = 0.25, 0.7
+    mus = np.linspace(-2, 2, 400001)
+    alpha = lam / (2 * beta)          # 1/(2 alpha) = beta / lam
+    for x in (-0.9, -0.2, -0.05, 0.0, 0.03, 0.17, 0.6):
+        obj = beta * (x - mus) ** 2 + lam * np.abs(mus)
+        assert abs(mus[np.argmin(obj)] - O.hqs_shrink_l1(x, lam, beta)) <= 2e-5
+        gH = (x - mus) ** 2 / (2 * alpha) + np.abs(mus)
+        huber = x * x / (2 * alpha) if abs(x) <= alpha else abs(x) - alpha / 2
+        assert gH.min() == pytest.approx(huber, abs=1e-9)
+
+
+@pytest.mark.parametrize("H,W,lam,N", [(8, 8, 0.25, 4), (5, 7, 0.1, 3)])
+def test_hqs_matches_dense_bruteforce(H, W, lam, N):
+    f = small_image(H, W, seed=5 * H + W)
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    u = f.reshape(-1).copy()
+    beta = 2 * lam
+    for _ in range(N):
+        gx, gy = Dx @ u, Dy @ u
+        # Q1 by a per-element brute force over mu (no closed form used)
+        grid = np.linspace(-1.5, 1.5, 300001)
+        mx = np.array([grid[np.argmin(beta * (g - grid) ** 2 + lam * np.abs(grid))] for g in gx])
+        my = np.array([grid[np.argmin(beta * (g - grid) ** 2 + lam * np.abs(grid))] for g in gy])
+        A = np.eye(H * W) + beta * (Dx.T @ Dx + Dy.T @ Dy)
+        u = np.linalg.solve(A, f.reshape(-1) + beta * (Dx.T @ mx + Dy.T @ my))
+        beta *= 2.0
+    np.testing.assert_allclose(O.hqs_channel(f, lam, N), u.reshape(H, W), atol=3e-5)
+
+
+def test_hqs_limits():
+    f = small_image(12, 10, seed=31)
+    np.testing.assert_allclose(O.hqs_channel(f, 0.0, 4, beta0=1.0), f, atol=1e-13)  # no threshold: mu = grad f
+    np.testing.assert_allclose(O.hqs_channel(np.full((6, 8), 0.3), 0.5, 3), 0.3, atol=1e-13)
+    u = O.hqs_channel(f, 0.25, 4)
+    assert abs(u.mean() - f.mean()) < 1e-13
+    # a huge threshold (lam >> gradients) zeroes mu: one step is the quadratic smoother with weight beta0
+    H, W = f.shape
+    Dx, Dy = dense_forward_difference(H, W, "x"), dense_forward_difference(H, W, "y")
+    b0 = 3.0
+    want = np.linalg.solve(np.eye(H * W) + b0 * (Dx.T @ Dx + Dy.T @ Dy), f.reshape(-1)).reshape(H, W)
+    np.testing.assert_allclose(O.hqs_channel(f, 1e3, 1, beta0=b0), want, atol=1e-12)
