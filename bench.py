@@ -276,6 +276,17 @@ def welsch_leg(ils, torch, dev, steps, flush):
     return out
 
 
+def hqs_leg(ils, torch, dev, steps, flush):
+    """The comparison method of Sec. 3.5, half-quadratic splitting with phi = |x|, at 1920 x 1080
+    RGB in the paper's Fig. 11 setting (lambda = 0.25, beta0 = 2 lambda, N = 4; kappa = 2)."""
+    f = torch.from_numpy(make_frame(C, H, W)).to(dev)
+    u = torch.empty_like(f)
+    with ils.Plan(H, W, C, 0.25, N=4, penalty="hqs", kappa=2.0) as plan:
+        ms = _timed_smooth(plan, f, u, torch, steps, flush)
+    return {"workload": "half-quadratic splitting, phi=|x|, 1920x1080 RGB FP32, lambda=0.25, N=4",
+            "ms": ms, "fps": 1000.0 / ms}
+
+
 def colour_leg(ils, torch, dev, steps, flush):
     """1920 x 1080 RGB, N = 4: luminance-only smoothing (Sec. 3.4 option I: one channel) and
     per-channel detail enhancement with k = 3 (the paper's figures), each in one call."""
@@ -553,6 +564,7 @@ def run_ours(args):
             line["gray"] = gray_leg(ils, torch, dev, ksteps, flush)
             line["welsch"] = welsch_leg(ils, torch, dev, ksteps, flush)
             line["colour"] = colour_leg(ils, torch, dev, ksteps, flush)
+            line["hqs"] = hqs_leg(ils, torch, dev, ksteps, flush)
             line["sweep_4k"] = sweep_4k_leg(ils, torch, dev, 5, flush)
             line["adjoint"] = adjoint_leg(ils, torch, dev, max(3, min(args.steps, 20)))
             line["batch"] = batch_leg(ils, torch, dev, max(3, min(args.steps, 10)), flush)

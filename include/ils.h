@@ -84,6 +84,20 @@ ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps
  */
 ils_status ils_plan_create_welsch(int H, int W, int C, float lambda, float gamma, int N, ils_plan** out);
 
+/*
+ * ils_plan_create_hqs - the comparison method of Sec. 3.5: half-quadratic splitting
+ * (Eq. 12-14) with the L1 penalty phi(x) = |x| (anisotropic total variation).  Iteration n:
+ * Q1 mu^n = soft threshold of grad u^n at lambda / (2 beta_n); Q2 u^{n+1} =
+ * argmin (u - f)^2 + beta_n (grad u - mu^n)^2, solved by the same FFT passes with the
+ * weight beta_n; beta_n = kappa^n beta0.  The paper's Fig. 11 setting: lambda = 0.25,
+ * beta0 = 2 lambda, N = 4.
+ *   lambda > 0; beta0 > 0, or <= 0 for the paper's 2 lambda; kappa >= 1 (the paper requires
+ *   kappa > 1 without a value; 2 is a common choice); N >= 0.
+ * Smooth / warm start / host / checkpointed calls work as for any plan; ils_backward returns
+ * ILS_ERR_INVALID_ARG (no adjoint of the splitting).
+ */
+ils_status ils_plan_create_hqs(int H, int W, int C, float lambda, float beta0, float kappa, int N, ils_plan** out);
+
 /* Free a plan and its device memory.  NULL is accepted.  Synchronizes the device. */
 ils_status ils_plan_destroy(ils_plan* plan);
 

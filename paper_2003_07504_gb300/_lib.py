@@ -46,6 +46,7 @@ SIGNATURES = {
     "ils_last_error": (ctypes.c_char_p, []),
     "ils_plan_create": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int, P(c_void_p)]),
     "ils_plan_create_welsch": (c_int, [c_int, c_int, c_int, c_float, c_float, c_int, c_void_p]),
+    "ils_plan_create_hqs": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int, c_void_p]),
     "ils_plan_destroy": (c_int, [c_void_p]),
     "ils_plan_c": (c_float, [c_void_p]),
     "ils_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

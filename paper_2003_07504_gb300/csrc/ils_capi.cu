@@ -27,6 +27,10 @@ struct ils_plan {
   float* stage_f;      // device staging for ils_smooth_host
   float* stage_u;
   float* luma;         // luminance of ils_smooth_luma (H x W), allocated at its first call
+  // half-quadratic splitting: per-iteration Eq. 14 parameters and denominator tables
+  // (iteration n: ax at iter_tab + n (M + 1 + H), by right after it)
+  std::vector<MuParams> mp_iter;
+  float* iter_tab;
   // optional per-kernel event timing (ils_set_profiling)
   bool profiling;
   std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
@@ -97,6 +101,7 @@ void free_plan_memory(ils_plan* pl) {
   cudaFree(pl->stage_f);
   cudaFree(pl->stage_u);
   cudaFree(pl->luma);
+  cudaFree(pl->iter_tab);
   cudaFree(pl->tab.twW);
   cudaFree(pl->tab.twH);
   cudaFree(pl->tab.ax);
@@ -126,6 +131,18 @@ __global__ void luma_kernel(const float* __restrict__ rgb, float* __restrict__ y
     y[i] = fmaf(0.299f, rgb[i], fmaf(0.587f, rgb[n + i], 0.114f * rgb[2 * n + i]));
 }
 
+// Parameters and tables of iteration `it` (the same for every iteration unless the plan is a
+// half-quadratic-splitting one, whose weight beta_n changes).
+const MuParams& iter_mp(const ils_plan* pl, int it) { return pl->mp_iter.empty() ? pl->mp : pl->mp_iter[it]; }
+Tables iter_tab(const ils_plan* pl, int it) {
+  Tables t = pl->tab;
+  if (pl->iter_tab != nullptr) {
+    t.ax = pl->iter_tab + (size_t)it * (pl->W / 2 + 1 + pl->H);
+    t.by = t.ax + pl->W / 2 + 1;
+  }
+  return t;
+}
+
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
                    const Epilogue& epi = Epilogue()) {
   const size_t n = (size_t)pl->C * pl->H * pl->W;
@@ -146,11 +163,12 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
     float* ck = ckpt ? ckpt + (size_t)it * n : nullptr;
     if ((e = mark(pl, slot++, it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW, st))) return cuda_fail(e, "event");
     d.pdl = chain && it > 0;
-    if ((e = launch_row_forward(d, pl->geo, pl->tab, pl->mp, f, it == 0 ? u0 : nullptr, in, out, ck, st)))
+    const Tables tn = iter_tab(pl, it);
+    if ((e = launch_row_forward(d, pl->geo, tn, iter_mp(pl, it), f, it == 0 ? u0 : nullptr, in, out, ck, st)))
       return cuda_fail(e, "row pass launch");
     if ((e = mark(pl, slot++, ILS_KERNEL_COLUMN, st))) return cuda_fail(e, "event");
     d.pdl = chain;
-    if ((e = launch_col_solve(d, pl->geo, pl->tab, out, st))) return cuda_fail(e, "column pass launch");
+    if ((e = launch_col_solve(d, pl->geo, tn, out, st))) return cuda_fail(e, "column pass launch");
   }
   if ((e = mark(pl, slot++, ILS_KERNEL_ROW_INVERSE, st))) return cuda_fail(e, "event");
   d.pdl = chain;
@@ -288,6 +306,48 @@ ils_status ils_plan_create(int H, int W, int C, float lambda, float p, float eps
   return create_plan(H, W, C, lambda, N, mp, c, p, eps, out);
 }
 
+ils_status ils_plan_create_hqs(int H, int W, int C, float lambda, float beta0, float kappa, int N, ils_plan** out) {
+  if (out == nullptr) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (beta0 <= 0.0f) beta0 = 2.0f * lambda;  // the paper's beta_0 = 2 lambda
+  if (C < 1 || N < 0 || !(lambda > 0.0f) || !std::isfinite(lambda) || !(beta0 > 0.0f) || !std::isfinite(beta0) ||
+      !(kappa >= 1.0f) || !std::isfinite(kappa) || !std::isfinite((double)beta0 * std::pow((double)kappa, N)))
+    return ILS_ERR_INVALID_ARG;
+  MuParams mp;
+  mp.pen = 2;
+  mp.p = 0.0f;
+  mp.eps = 1.0f;
+  ils_status s = create_plan(H, W, C, lambda, N, mp, 0.0, 0.0f, 1.0f, out);
+  if (s != ILS_OK) return s;
+  ils_plan* pl = *out;
+  const int M = W / 2;
+  const size_t per = (size_t)M + 1 + H;
+  std::vector<float> tabs(per * (size_t)(N > 0 ? N : 1));
+  double beta = beta0;
+  for (int n = 0; n < N; ++n, beta *= kappa) {
+    MuParams m = pl->mp;
+    m.half_lambda = (float)beta;              // Q2 of Eq. 14: u = A_n^{-1}(f + beta_n D^T mu)
+    m.thr = (float)(lambda / (2.0 * beta));   // Q1: soft threshold at lambda / (2 beta_n)
+    pl->mp_iter.push_back(m);
+    for (int k = 0; k <= M; ++k) {
+      const double s1 = std::sin(M_PI * (double)k / (double)W);
+      tabs[n * per + k] = (float)(4.0 * beta * s1 * s1);  // beta_n |F grad_x|^2
+    }
+    for (int l = 0; l < H; ++l) {
+      const double s1 = std::sin(M_PI * (double)l / (double)H);
+      tabs[n * per + M + 1 + l] = (float)(4.0 * beta * s1 * s1);
+    }
+  }
+  cudaError_t e;
+  if ((s = dev_alloc((void**)&pl->iter_tab, tabs.size() * sizeof(float))) ||
+      (e = cudaMemcpy(pl->iter_tab, tabs.data(), tabs.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    ils_plan_destroy(pl);
+    *out = nullptr;
+    return s != ILS_OK ? s : cuda_fail(e, "cudaMemcpy tables");
+  }
+  return ILS_OK;
+}
+
 ils_status ils_plan_create_welsch(int H, int W, int C, float lambda, float gamma, int N, ils_plan** out) {
   if (out == nullptr) return ILS_ERR_INVALID_ARG;
   *out = nullptr;
@@ -299,7 +359,7 @@ ils_status ils_plan_create_welsch(int H, int W, int C, float lambda, float gamma
   mp.p = 0.0f;
   mp.eps = 1.0f;
   mp.a = 0.0f;
-  mp.welsch = 1;
+  mp.pen = 1;
   mp.wbeta = (float)(inv2g2 / std::log(2.0));  // exp(-x^2/(2 gamma^2)) = 2^(-wbeta x^2)
   mp.winv2g2 = (float)inv2g2;
   return create_plan(H, W, C, lambda, N, mp, 2.0, 0.0f, 1.0f, out);  // c = c0 = 2 (Eq. 20)
@@ -372,7 +432,8 @@ ils_status ils_smooth_checkpointed(ils_plan* pl, const float* f, const float* u0
 
 ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
                         void* stream) {
-  if (pl == nullptr || grad_u == nullptr || grad_f == nullptr || (ckpt == nullptr && pl->N > 0))
+  if (pl == nullptr || grad_u == nullptr || grad_f == nullptr || (ckpt == nullptr && pl->N > 0) ||
+      !pl->mp_iter.empty())  // no adjoint for half-quadratic splitting
     return ILS_ERR_INVALID_ARG;
   const size_t n = (size_t)pl->C * pl->H * pl->W;
   const size_t bytes = n * sizeof(float);

@@ -15,9 +15,12 @@ struct MuParams {
   float eps;
   float a;       // p/2 - 1
   float half_lambda;
-  int welsch = 0;    // penalty: 0 = generalized Charbonnier (Eq. 2, Eq. 7), 1 = Welsch (Eq. 18, Eq. 19)
-  float wbeta = 0.0f;   // Welsch: log2(e) / (2 gamma^2)
-  float winv2g2 = 0.0f; // Welsch: 1 / (2 gamma^2)
+  // 0 = generalized Charbonnier (Eq. 2, Eq. 7), 1 = Welsch (Eq. 18, Eq. 19), 2 = half-quadratic
+  // splitting with phi = |x| (Eq. 14: Q1 is a soft threshold at thr; half_lambda holds beta_n)
+  int pen = 0;
+  float wbeta = 0.0f;    // Welsch: log2(e) / (2 gamma^2)
+  float winv2g2 = 0.0f;  // Welsch: 1 / (2 gamma^2)
+  float thr = 0.0f;      // half-quadratic splitting: lambda / (2 beta_n)
 };
 
 // 2^x and log2(x) on the special-function unit (PTX ex2.approx / lg2.approx, flush to
@@ -43,12 +46,19 @@ __device__ __forceinline__ float mu_eq7(float g, const MuParams& mp) {
 __device__ __forceinline__ float mu_welsch(float g, const MuParams& mp) {
   return g * fmaf(-2.0f, sfu_exp2(-mp.wbeta * g * g), mp.c);
 }
-// mu of the penalty PEN (0: Eq. 7, 1: Eq. 19); the kernels are instantiated per penalty.
+// Q1 of Eq. 14 for phi = |x|: argmin_mu beta (g - mu)^2 + lambda |mu| = soft threshold.
+__device__ __forceinline__ float mu_hqs_l1(float g, const MuParams& mp) {
+  const float a = fabsf(g) - mp.thr;
+  return a > 0.0f ? copysignf(a, g) : 0.0f;
+}
+// mu of the penalty PEN (MuParams::pen); the kernels are instantiated per penalty.
 template <int PEN>
 __device__ __forceinline__ float mu_pen(float g, const MuParams& mp) {
   if constexpr (PEN == 0) return mu_eq7(g, mp);
-  else return mu_welsch(g, mp);
+  else if constexpr (PEN == 1) return mu_welsch(g, mp);
+  else return mu_hqs_l1(g, mp);
 }
+constexpr int kPenalties = 3;
 
 // Output stage of the final inverse row pass (u = the smoothed image, pairs of pixels):
 //   mode 0: out = u;

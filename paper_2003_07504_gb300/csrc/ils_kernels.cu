@@ -456,6 +456,10 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(row_forward_kernel<16, false, 1>))) return e;
   if ((e = allow_smem(row_forward_kernel<32, true, 1>))) return e;
   if ((e = allow_smem(row_forward_kernel<32, false, 1>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, true, 2>))) return e;
+  if ((e = allow_smem(row_forward_kernel<16, false, 2>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, true, 2>))) return e;
+  if ((e = allow_smem(row_forward_kernel<32, false, 2>))) return e;
   if ((e = allow_smem(col_solve_kernel<16>))) return e;
   if ((e = allow_smem(col_solve_kernel<32>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16, 0>))) return e;
@@ -481,11 +485,15 @@ cudaError_t launch_row_forward(const ImageDesc& d, const Geometry& g, const Tabl
   const int T = g.threads_row;
   const size_t S = g.smem_fwd;
   const bool first = spec_in == nullptr;
-  auto fn = mp.welsch
-                ? (g.ept_row == 16 ? (first ? row_forward_kernel<16, true, 1> : row_forward_kernel<16, false, 1>)
-                                   : (first ? row_forward_kernel<32, true, 1> : row_forward_kernel<32, false, 1>))
-                : (g.ept_row == 16 ? (first ? row_forward_kernel<16, true, 0> : row_forward_kernel<16, false, 0>)
-                                   : (first ? row_forward_kernel<32, true, 0> : row_forward_kernel<32, false, 0>));
+  using Fn = decltype(&row_forward_kernel<16, true, 0>);
+  static const Fn table[kPenalties][2][2] = {
+      {{row_forward_kernel<16, true, 0>, row_forward_kernel<16, false, 0>},
+       {row_forward_kernel<32, true, 0>, row_forward_kernel<32, false, 0>}},
+      {{row_forward_kernel<16, true, 1>, row_forward_kernel<16, false, 1>},
+       {row_forward_kernel<32, true, 1>, row_forward_kernel<32, false, 1>}},
+      {{row_forward_kernel<16, true, 2>, row_forward_kernel<16, false, 2>},
+       {row_forward_kernel<32, true, 2>, row_forward_kernel<32, false, 2>}}};
+  Fn fn = table[mp.pen][g.ept_row == 16 ? 0 : 1][first ? 0 : 1];
   return launch_k(d.pdl, fn, grid, T, S, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, f, first ? u0 : nullptr,
                   spec_in, spec_out, u_ckpt);
 }
@@ -517,7 +525,8 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream) {
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
-  auto fn = mp.welsch ? (g.ept_row == 16 ? row_adjoint_kernel<16, 1> : row_adjoint_kernel<32, 1>)
+  if (mp.pen == 2) return cudaErrorInvalidValue;  // no adjoint for half-quadratic splitting
+  auto fn = mp.pen == 1 ? (g.ept_row == 16 ? row_adjoint_kernel<16, 1> : row_adjoint_kernel<32, 1>)
                       : (g.ept_row == 16 ? row_adjoint_kernel<16, 0> : row_adjoint_kernel<32, 0>);
   return launch_k(d.pdl, fn, grid, g.threads_row, g.smem_fwd, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, spec_in,
                   u_n, fbar, (int)fbar_first, gu0, (int)last, spec_out);

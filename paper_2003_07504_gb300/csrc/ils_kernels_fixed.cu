@@ -483,7 +483,7 @@ using ColFn = void (*)(int, int, const float2*, const float*, const float*, floa
 
 struct RowEntry {
   int M, tps, rows_fwd, rows_inv;
-  RowFwdFn first[2], later[2];  // per penalty (MuParams::welsch)
+  RowFwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
   RowInvFn inv[3];              // per epilogue mode
 };
 struct ColEntry {
@@ -497,8 +497,10 @@ constexpr RowEntry row_entry() {
                   PL::TPS,
                   RF,
                   RI,
-                  {row_fwd_fixed_kernel<PL, RF, true, 0>, row_fwd_fixed_kernel<PL, RF, true, 1>},
-                  {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>},
+                  {row_fwd_fixed_kernel<PL, RF, true, 0>, row_fwd_fixed_kernel<PL, RF, true, 1>,
+                   row_fwd_fixed_kernel<PL, RF, true, 2>},
+                  {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>,
+                   row_fwd_fixed_kernel<PL, RF, false, 2>},
                   {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>}};
 }
 template <class PL, int G, int MINB = 1>
@@ -571,7 +573,7 @@ cudaError_t fixed_set_attributes() {
   cudaError_t e;
   for (const RowEntry& r : kRows) {
     const int sf = (int)row_smem(r.rows_fwd + 2, r.M), si = (int)row_smem(r.rows_inv, r.M);
-    for (int pen = 0; pen < 2; ++pen) {
+    for (int pen = 0; pen < kPenalties; ++pen) {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
@@ -592,7 +594,7 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
   const int threads = (r.rows_fwd + 2) * r.tps;
   const size_t smem = row_smem(r.rows_fwd + 2, r.M);
   const int tiles = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  const int pen = mp.welsch ? 1 : 0;
+  const int pen = mp.pen;
   RowFwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, tiles, threads, smem, stream, d.H, d.C, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }

@@ -333,7 +333,7 @@ using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
-  FwdFn first[2], later[2];  // per penalty (MuParams::welsch)
+  FwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
   InvFn inv[3];              // per epilogue mode
 };
 
@@ -348,9 +348,11 @@ constexpr WarpRowEntry warp_entry() {
                       WarpRow<L>::BUF,
                       STAGE ? RF * 32 * L : 0,
                       {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0, MINB>,
-                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB>},
+                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB>,
+                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 2, MINB>},
                       {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB>,
-                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>},
+                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>,
+                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB>},
                       {row_warp_inv_kernel<L, RI, 0>, row_warp_inv_kernel<L, RI, 1>, row_warp_inv_kernel<L, RI, 2>}};
 }
 
@@ -382,7 +384,7 @@ cudaError_t warp_set_attributes() {
   for (const WarpRowEntry& r : kWarpRows) {
     const int sf = ((r.rows_fwd + 2) * r.buf + r.stage) * (int)sizeof(float2);
     const int si = r.rows_inv * r.buf * (int)sizeof(float2);
-    for (int pen = 0; pen < 2; ++pen) {
+    for (int pen = 0; pen < kPenalties; ++pen) {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
@@ -398,7 +400,7 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
   const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage) * sizeof(float2);
-  const int pen = mp.welsch ? 1 : 0;
+  const int pen = mp.pen;
   FwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
 }

@@ -27,12 +27,14 @@ def _check_image(t: torch.Tensor, shape, name: str) -> None:
 
 
 class Plan:
-    """An ILS plan for C x H x W float32 images (ils_plan_create), or with
-    penalty="welsch" an ILS plan with the Welsch penalty of scale gamma
-    (ils_plan_create_welsch; p and eps are then unused)."""
+    """An ILS plan for C x H x W float32 images (ils_plan_create).  penalty="welsch": ILS with
+    the Welsch penalty of scale gamma (ils_plan_create_welsch); penalty="hqs": the
+    half-quadratic-splitting comparison method with phi = |x|, weights beta0 kappa^n
+    (ils_plan_create_hqs; beta0=None means 2 lam).  p and eps are unused by both."""
 
     def __init__(self, H: int, W: int, C: int = 1, lam: float = 1.0, p: float = 0.8,
-                 eps: float = 1e-4, N: int = 4, penalty: str = "lp", gamma: float | None = None):
+                 eps: float = 1e-4, N: int = 4, penalty: str = "lp", gamma: float | None = None,
+                 beta0: float | None = None, kappa: float = 2.0):
         self.H, self.W, self.C, self.N = int(H), int(W), int(C), int(N)
         self.lam, self.p, self.eps = float(lam), float(p), float(eps)
         self.penalty = penalty
@@ -44,6 +46,10 @@ class Plan:
             self.gamma = float(gamma)
             _lib.check(L.ils_plan_create_welsch(self.H, self.W, self.C, self.lam, self.gamma, self.N,
                                                 ctypes.byref(h)), "ils_plan_create_welsch")
+        elif penalty == "hqs":
+            _lib.check(L.ils_plan_create_hqs(self.H, self.W, self.C, self.lam,
+                                             0.0 if beta0 is None else float(beta0), float(kappa), self.N,
+                                             ctypes.byref(h)), "ils_plan_create_hqs")
         elif penalty == "lp":
             _lib.check(L.ils_plan_create(self.H, self.W, self.C, self.lam, self.p, self.eps, self.N,
                                          ctypes.byref(h)), "ils_plan_create")

@@ -319,3 +319,36 @@ def test_luma_with_the_welsch_penalty(ils):
     with ils.Plan(H, W, 1, lam, N=N, penalty="welsch", gamma=gamma) as plan:
         out = plan.smooth_luma(torch.from_numpy(np.ascontiguousarray(f)).cuda()).cpu().numpy()
     assert_parity(out, want)
+
+
+# -------------------------------------------------------------- half-quadratic splitting (Sec. 3.5, the comparison method)
+
+@pytest.mark.parametrize("H,W,C,lam,N", [
+    (256, 256, 1, 0.25, 4),   # warp kernels; the paper's Fig. 11(c) setting
+    (40, 1920, 3, 0.25, 4),   # warp L = 30
+    (16, 3840, 1, 0.1, 3),    # fixed 1920-point rows
+    (60, 80, 2, 0.25, 6),     # generic rows
+    (1080, 40, 1, 0.25, 2),   # 1080-point column plan
+])
+def test_hqs_parity(ils, H, W, C, lam, N):
+    import torch
+    f = image(H, W, C, seed=13 * H + W + C)
+    with ils.Plan(H, W, C, lam, N=N, penalty="hqs") as plan:
+        u = plan.smooth(torch.from_numpy(np.ascontiguousarray(f)).cuda()).cpu().numpy()
+    want = O.hqs_smooth(f.astype(np.float64), lam, N)
+    # the soft threshold is not differentiable at |g| = thr: an FP32 gradient on the other side of
+    # the kink moves mu by up to its rounding error, which the solve does not amplify; same bar
+    assert_parity(u, want)
+
+
+def test_hqs_has_no_adjoint_and_checks_parameters(ils):
+    import torch
+    from paper_2003_07504_gb300._lib import ILSError
+    with ils.Plan(16, 16, 1, 0.25, N=2, penalty="hqs") as plan:
+        f = torch.rand(1, 16, 16, device="cuda")
+        u, ck = plan.smooth_checkpointed(f)
+        with pytest.raises(ILSError):
+            plan.backward(ck, torch.ones_like(f))
+    for lam, kappa in ((0.0, 2.0), (0.25, 0.5), (-1.0, 2.0)):
+        with pytest.raises(ILSError):
+            ils.Plan(16, 16, 1, lam, N=2, penalty="hqs", kappa=kappa)
