@@ -429,6 +429,14 @@ bool pick_geometry(int H, int W, Geometry* g) {
   }
   g->warp_row = nw > 0 ? wv[pick] : -1;
   g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
+  // ILS_ROW_IMPL=fixed<k>: the k-th compile-time row plan of the length
+  if (!no_fixed && impl != nullptr && impl[0] == 'f' && impl[1] == 'i' && impl[2] == 'x' && impl[3] == 'e' &&
+      impl[4] == 'd' && impl[5] >= '0' && impl[5] <= '9') {
+    int rv[16];
+    const int nr = fixed_row_variants(M, rv, 16);
+    const int k = atoi(impl + 5);
+    if (k >= 0 && k < nr) g->fixed_row = rv[k];
+  }
   g->fixed_col = generic ? -1 : fixed_col_index(H);
   // ILS_COL_IMPL=<k>: the k-th compile-time column plan of the length (tests, measurements)
   const char* cimpl = getenv("ILS_COL_IMPL");

@@ -493,6 +493,7 @@ struct ColEntry {
 
 template <class PL, int RF, int RI>
 constexpr RowEntry row_entry() {
+  static_assert((RF + 2) * PL::TPS <= 1024 && RI * PL::TPS <= 1024, "at most 1024 threads per CTA");
   return RowEntry{PL::N,
                   PL::TPS,
                   RF,

@@ -37,10 +37,13 @@ struct WarpRow {
   static constexpr int STRIDE = 33;                       // complex per transposed line
   static constexpr int BUF = (L * STRIDE > M ? L * STRIDE : M);  // complex per row buffer
 
-  // v: lane holds x[lane + 32 n2]; out (lanes < L): X[lane + L k1].  buf: this warp's buffer.
-  // twW[t] = exp(-2 pi i t / (2M)).
+  static constexpr int K2P = (L + 31) / 32;  // 32-point transforms per lane (k2 = lane + 32 j < L)
+
+  // v: lane holds x[lane + 32 n2]; out[j] (where k2 = lane + 32 j < L): X[k2 + L k1].  buf: this
+  // warp's buffer.  twW[t] = exp(-2 pi i t / (2M)).  L > 32 (a 1920-point row) runs two
+  // 32-point transforms per lane.
   template <bool INV>
-  __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[32], float2* buf, int lane,
+  __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[K2P][32], float2* buf, int lane,
                                              const float2* __restrict__ twW) {
     dft_reg<L, INV>(v);
 #pragma unroll
@@ -52,10 +55,14 @@ struct WarpRow {
 #pragma unroll
     for (int k2 = 0; k2 < L; ++k2) buf[k2 * STRIDE + lane] = v[k2];
     __syncwarp();
-    if (lane < L) {
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) out[n1] = buf[lane * STRIDE + n1];
-      dft_reg<32, INV>(out);
+    for (int j = 0; j < K2P; ++j) {
+      const int k2 = lane + 32 * j;
+      if (k2 < L) {
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) out[j][n1] = buf[k2 * STRIDE + n1];
+        dft_reg<32, INV>(out[j]);
+      }
     }
     __syncwarp();
   }
@@ -79,11 +86,14 @@ struct WarpRow {
         v[n2] = c2(s.x - t.y, s.y + t.x);
       }
     }
-    float2 out[32];
+    float2 out[K2P][32];
     fft<true>(v, out, buf, lane, twW);
-    if (lane < L) {
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) buf[lane + L * k1] = out[k1];
+    for (int j = 0; j < K2P; ++j) {
+      if (lane + 32 * j < L) {
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) buf[lane + 32 * j + L * k1] = out[j][k1];
+      }
     }
     __syncwarp();
   }
@@ -108,11 +118,14 @@ struct WarpRow {
         v[n2] = c2(s.x - t.y, s.y + t.x);
       }
     }
-    float2 res[32];
+    float2 res[K2P][32];
     fft<true>(v, res, buf, lane, twW);
-    if (lane < L) {
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) epi.template store<EPI>(out, rowoff + lane + L * k1, res[k1]);
+    for (int j = 0; j < K2P; ++j) {
+      if (lane + 32 * j < L) {
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) epi.template store<EPI>(out, rowoff + lane + 32 * j + L * k1, res[j][k1]);
+      }
     }
   }
 
@@ -120,11 +133,14 @@ struct WarpRow {
   // half spectrum in the global row dst (slot 0 = (X[0], X[M])).
   __device__ __forceinline__ static void forward_row_to_global(float2 (&v)[L], float2* dst, float2* buf, int lane,
                                                                const float2* __restrict__ twW) {
-    float2 out[32];
+    float2 out[K2P][32];
     fft<false>(v, out, buf, lane, twW);
-    if (lane < L) {
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) buf[lane + L * k1] = out[k1];
+    for (int j = 0; j < K2P; ++j) {
+      if (lane + 32 * j < L) {
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) buf[lane + 32 * j + L * k1] = out[j][k1];
+      }
     }
     __syncwarp();
     // pairs (k, M-k), k = 0..M/2
