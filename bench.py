@@ -360,6 +360,43 @@ def batch_leg(ils, torch, dev, steps, flush):
 CNN_FLOP_PER_PX = 2 * 9 * (3 * 32 + 4 * 32 * 32 + 32 * 3)  # 77,184: six 3x3 convolutions per pixel
 
 
+def training_leg(torch, dev, steps):
+    """One training step of the warm-start network on 16 RGB 256 x 256 crops: targets by plain
+    ILS N=4 (this library), forward, MSE, backward (input and weight gradients), Adam.  The
+    network FLOPs are 3 x 77,184 per pixel (forward, input gradients, weight gradients)."""
+    from paper_2003_07504_gb300 import ils, synth, warmstart as ws
+    B, S = 16, 256
+    f = torch.from_numpy(synth.preset_image(S, S, 3 * B, "small", 6000).reshape(B, 3, S, S)).to(dev)
+    target, grad = torch.empty_like(f), torch.empty_like(f)
+    loss = torch.zeros(1, device=dev)
+    net = ws.WarmStartNet(B * S * S, ws.init_params(seed=1))
+    stream = torch.cuda.current_stream()
+    with ils.Plan(S, S, 3 * B, LAM, P, EPS, N_ITERS) as plan:
+        def step():
+            plan.smooth(f.view(3 * B, S, S), out=target.view(3 * B, S, S))
+            loss.zero_()
+            u0 = net.forward(f)
+            ws.mse(u0, target, grad, loss)
+            net.zero_grad()
+            net.backward(f, grad)
+            net.adam_step(1e-4)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        net.check()
+    net.close()
+    tflops = 3 * CNN_FLOP_PER_PX * B * S * S / (ms / 1000.0) / 1e12
+    return {"workload": "16 x 3 x 256 x 256 crops: ILS N=4 targets + network forward/backward + Adam",
+            "ms_per_step": ms, "crops_per_s": B / (ms / 1000.0), "network_tflops_incl_targets": tflops}
+
+
 def warm_leg(torch, dev, steps, flush):
     """Learned warm start vs plain ILS at 1920x1080 RGB (lambda=1, p=0.8): fps of the whole
     warm path (network + 1 or 2 ILS iterations + the iterate-change check and fallback
@@ -569,6 +606,7 @@ def run_ours(args):
             line["adjoint"] = adjoint_leg(ils, torch, dev, max(3, min(args.steps, 20)))
             line["batch"] = batch_leg(ils, torch, dev, max(3, min(args.steps, 10)), flush)
             line["warm_start"] = warm_leg(torch, dev, max(3, min(args.steps, 10)), flush)
+            line["training"] = training_leg(torch, dev, max(3, min(args.steps, 10)))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)

@@ -352,3 +352,26 @@ def test_hqs_has_no_adjoint_and_checks_parameters(ils):
     for lam, kappa in ((0.0, 2.0), (0.25, 0.5), (-1.0, 2.0)):
         with pytest.raises(ILSError):
             ils.Plan(16, 16, 1, lam, N=2, penalty="hqs", kappa=kappa)
+
+
+def test_programmatic_launch_chaining_gives_the_same_result(ils, tmp_path):
+    # ILS_PDL=1 (read once per process) chains a call's kernels by programmatic dependent
+    # launch; the result must be bit-identical to plain stream order
+    import os
+    import subprocess
+    import sys
+    import torch
+    f = image(96, 160, 3, seed=5)
+    np.save(tmp_path / "f.npy", f)
+    code = (
+        "import sys, numpy as np, torch; sys.path.insert(0, %r)\n"
+        "from paper_2003_07504_gb300 import ils\n"
+        "f = torch.from_numpy(np.load(%r)).cuda()\n"
+        "with ils.Plan(96, 160, 3, 1.0, 0.8, 1e-4, 4) as p:\n"
+        "    np.save(%r, p.smooth(f).cpu().numpy())\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), str(tmp_path / "f.npy"), str(tmp_path / "u.npy"))
+    env = dict(os.environ, ILS_PDL="1")
+    subprocess.run([sys.executable, "-c", code], env=env, check=True, timeout=300)
+    with ils.Plan(96, 160, 3, 1.0, 0.8, 1e-4, 4) as plan:
+        want = plan.smooth(torch.from_numpy(f).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(np.load(tmp_path / "u.npy"), want)
