@@ -31,6 +31,11 @@ struct ils_plan {
   // (iteration n: ax at iter_tab + n (M + 1 + H), by right after it)
   std::vector<MuParams> mp_iter;
   float* iter_tab;
+  // channels run on `nsplit` internal streams forked from and joined back to the caller's
+  // stream, so that the small per-pass grids of a frame overlap each other's fill and drain
+  int nsplit;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of side stream s
   // optional per-kernel event timing (ils_set_profiling)
   bool profiling;
   std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
@@ -96,6 +101,10 @@ void destroy_events(ils_plan* pl) {
 
 void free_plan_memory(ils_plan* pl) {
   destroy_events(pl);
+  for (cudaStream_t x : pl->side) cudaStreamDestroy(x);
+  for (cudaEvent_t x : pl->fork_join) cudaEventDestroy(x);
+  pl->side.clear();
+  pl->fork_join.clear();
   cudaFree(pl->spec[0]);
   cudaFree(pl->spec[1]);
   cudaFree(pl->stage_f);
@@ -143,6 +152,45 @@ Tables iter_tab(const ils_plan* pl, int it) {
   return t;
 }
 
+// The 2N+1 launches of Algorithm 1 for channels [c0, c0 + cn) of the plan on `st` (pointers
+// are those of channel 0; each channel's image, spectrum and checkpoint slices are disjoint).
+// `slot` (profiling) counts the event marks between launches, or is null.
+ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float* u0, float* u, float* ckpt,
+                       cudaStream_t st, const Epilogue& epi_in, int* slot) {
+  const size_t hw = (size_t)pl->H * pl->W, n = (size_t)pl->C * hw, off = (size_t)c0 * hw;
+  ImageDesc d = pl->desc;
+  d.C = cn;
+  Epilogue epi = epi_in;
+  if (epi.mode == 1) epi.f += off;
+  f += off;
+  u += off;
+  if (u0 != nullptr) u0 += off;
+  float2* spec[2] = {pl->spec[0] + off / 2, pl->spec[1] + off / 2};
+  cudaError_t e;
+  auto mark_if = [&](int kind) -> cudaError_t { return slot ? mark(pl, (*slot)++, kind, st) : cudaSuccess; };
+  // programmatic dependent launch between this call's own kernels (not after the caller's
+  // work, and not when profiling events sit between the launches)
+  const bool chain = slot == nullptr && pdl_enabled();
+  for (int it = 0; it < pl->N; ++it) {
+    float2* out = spec[it & 1];
+    const float2* in = it == 0 ? nullptr : spec[(it - 1) & 1];
+    float* ck = ckpt ? ckpt + (size_t)it * n + off : nullptr;
+    if ((e = mark_if(it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW))) return cuda_fail(e, "event");
+    d.pdl = chain && it > 0;
+    const Tables tn = iter_tab(pl, it);
+    if ((e = launch_row_forward(d, pl->geo, tn, iter_mp(pl, it), f, it == 0 ? u0 : nullptr, in, out, ck, st)))
+      return cuda_fail(e, "row pass launch");
+    if ((e = mark_if(ILS_KERNEL_COLUMN))) return cuda_fail(e, "event");
+    d.pdl = chain;
+    if ((e = launch_col_solve(d, pl->geo, tn, out, st))) return cuda_fail(e, "column pass launch");
+  }
+  if ((e = mark_if(ILS_KERNEL_ROW_INVERSE))) return cuda_fail(e, "event");
+  d.pdl = chain;
+  if ((e = launch_row_inverse(d, pl->geo, pl->tab, spec[(pl->N - 1) & 1], u, st, epi)))
+    return cuda_fail(e, "inverse row pass launch");
+  return ILS_OK;
+}
+
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
                    const Epilogue& epi = Epilogue()) {
   const size_t n = (size_t)pl->C * pl->H * pl->W;
@@ -152,28 +200,21 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
     e = cudaMemcpyAsync(u, u0 ? u0 : f, bytes, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
   }
-  int slot = 0;
-  // programmatic dependent launch between this call's own kernels (not after the caller's
-  // work, and not when profiling events sit between the launches)
-  ImageDesc d = pl->desc;
-  const bool chain = !pl->profiling && pdl_enabled();
-  for (int it = 0; it < pl->N; ++it) {
-    float2* out = pl->spec[it & 1];
-    const float2* in = it == 0 ? nullptr : pl->spec[(it - 1) & 1];
-    float* ck = ckpt ? ckpt + (size_t)it * n : nullptr;
-    if ((e = mark(pl, slot++, it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW, st))) return cuda_fail(e, "event");
-    d.pdl = chain && it > 0;
-    const Tables tn = iter_tab(pl, it);
-    if ((e = launch_row_forward(d, pl->geo, tn, iter_mp(pl, it), f, it == 0 ? u0 : nullptr, in, out, ck, st)))
-      return cuda_fail(e, "row pass launch");
-    if ((e = mark(pl, slot++, ILS_KERNEL_COLUMN, st))) return cuda_fail(e, "event");
-    d.pdl = chain;
-    if ((e = launch_col_solve(d, pl->geo, tn, out, st))) return cuda_fail(e, "column pass launch");
+  ils_status s;
+  if (!pl->profiling && pl->nsplit > 1) {
+    if ((e = cudaEventRecord(pl->fork_join[0], st))) return cuda_fail(e, "event");
+    for (int k = 0; k < pl->nsplit; ++k) {
+      const int c0 = k * pl->C / pl->nsplit, c1 = (k + 1) * pl->C / pl->nsplit;
+      if ((e = cudaStreamWaitEvent(pl->side[k], pl->fork_join[0], 0))) return cuda_fail(e, "stream wait");
+      if ((s = enqueue_ils(pl, c0, c1 - c0, f, u0, u, ckpt, pl->side[k], epi, nullptr))) return s;
+      if ((e = cudaEventRecord(pl->fork_join[1 + k], pl->side[k])) ||
+          (e = cudaStreamWaitEvent(st, pl->fork_join[1 + k], 0)))
+        return cuda_fail(e, "join");
+    }
+    return ILS_OK;
   }
-  if ((e = mark(pl, slot++, ILS_KERNEL_ROW_INVERSE, st))) return cuda_fail(e, "event");
-  d.pdl = chain;
-  if ((e = launch_row_inverse(d, pl->geo, pl->tab, pl->spec[(pl->N - 1) & 1], u, st, epi)))
-    return cuda_fail(e, "inverse row pass launch");
+  int slot = 0;
+  if ((s = enqueue_ils(pl, 0, pl->C, f, u0, u, ckpt, st, epi, pl->profiling ? &slot : nullptr))) return s;
   if ((e = mark(pl, slot, -1, st))) return cuda_fail(e, "event");
   if (pl->profiling) {
     // accumulate this call's launch durations (waits for the call to finish)
@@ -283,6 +324,27 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
     free_plan_memory(pl);
     delete pl;
     return cuda_fail(e, "cudaMemcpy tables");
+  }
+  // 2..8 channels: one internal stream per channel (at most 4); ILS_SPLIT=0 keeps one stream
+  const char* split = std::getenv("ILS_SPLIT");
+  pl->nsplit = (C >= 2 && C <= 8 && !(split != nullptr && split[0] == '0')) ? std::min(C, 4) : 1;
+  for (int k = 0; k < pl->nsplit; ++k) {
+    cudaStream_t x;
+    if ((e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking))) {
+      free_plan_memory(pl);
+      delete pl;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    pl->side.push_back(x);
+  }
+  for (int k = 0; k < (pl->nsplit > 1 ? pl->nsplit + 1 : 0); ++k) {
+    cudaEvent_t x;
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming))) {
+      free_plan_memory(pl);
+      delete pl;
+      return cuda_fail(e, "cudaEventCreate");
+    }
+    pl->fork_join.push_back(x);
   }
   *out = pl;
   return ILS_OK;
