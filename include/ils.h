@@ -133,6 +133,43 @@ ils_status ils_smooth_enhance(ils_plan* plan, const float* f, float* out, float 
 ils_status ils_smooth_luma(ils_plan* plan, const float* rgb, float* out, float k, void* stream);
 
 /*
+ * ils_smooth_hwc - ils_smooth on pixel-interleaved images (H x W x C float32, the channels of
+ * a pixel adjacent, as most image libraries store them).  A gather kernel writes the planar
+ * copy that every iteration re-reads (Algorithm 1 re-reads f in each right-hand side) into
+ * a plan-owned C x H x W buffer, and the final inverse row pass writes u interleaved, so
+ * no planar u is materialised.  Same results as ils_smooth on the transposed image.
+ *   f_hwc, u_hwc : device pointers, H x W x C float32, non-overlapping.
+ * The first call allocates the planar buffer (C x H x W float32, shared with
+ * ils_smooth_host's input staging) that the plan keeps (make it before any stream capture).
+ * Returns ILS_ERR_UNSUPPORTED_SIZE when C H W / 2 >= 2^32.
+ */
+ils_status ils_smooth_hwc(ils_plan* plan, const float* f_hwc, float* u_hwc, void* stream);
+
+/*
+ * ils_log_luma - l = ln max(Y, 1e-12) with Y = 0.299 R + 0.587 G + 0.114 B: the logarithm
+ * of the luminance on which Sec. 4.2 performs the smoothing for HDR tone mapping (the input
+ * of ils_smooth for a base / detail split b = ILS(l), d = l - b).
+ *   rgb : device pointer, 3 x H x W float32 (planar R, G, B, linear radiance).
+ *   l   : device pointer, H x W float32, not overlapping rgb.
+ */
+ils_status ils_log_luma(const float* rgb, float* l, int H, int W, void* stream);
+
+/*
+ * ils_tonemap_log - single-scale HDR tone mapping of Sec. 4.2: the base layer
+ * b = ILS(l) of the log-luminance l (ils_log_luma), detail d = l - b, new log-luminance
+ * l' = s b + k d, and the colour ratios kept: out_c = rgb_c exp(l' - l + o)
+ *   = rgb_c exp((k - 1) l + (s - k) b + o),
+ * written by the final inverse row pass (no b or d is materialised).  s < 1 compresses
+ * the base contrast, k > 1 boosts details, o shifts the exposure (log units).  The paper's
+ * single-scale setting is p = 1, lambda = 10.
+ *   plan : made with C = 1 for the image's H x W.
+ *   rgb, out : device pointers, 3 x H x W float32 (planar), non-overlapping.
+ * The first call allocates an H x W float32 buffer for l that the plan keeps (shared with
+ * ils_smooth_luma).  Returns ILS_ERR_INVALID_ARG if C != 1 or s, k, o are not finite.
+ */
+ils_status ils_tonemap_log(ils_plan* plan, const float* rgb, float* out, float s, float k, float o, void* stream);
+
+/*
  * ils_smooth_from - Algorithm 1 started from a given u^0 instead of f (warm start).
  *   u0 : device pointer, C x H x W float32 (read only); may equal f.
  *   u  : device pointer output; must overlap neither f nor u0.

@@ -52,6 +52,7 @@ __all__ = [
     "C0_WELSCH", "phi_welsch", "dphi_welsch", "d2phi_welsch", "g2_welsch", "mu_welsch",
     "ils_channel_welsch", "ils_smooth_welsch", "energy_welsch", "ils_backward_welsch",
     "LUMA_BT601", "luma", "detail_enhance", "ils_smooth_luma",
+    "LUMA_FLOOR", "log_luma", "tonemap_log", "hwc_to_planar", "planar_to_hwc", "ils_smooth_hwc",
     "hqs_shrink_l1", "hqs_channel", "hqs_smooth",
 ]
 
@@ -426,6 +427,47 @@ def ils_smooth_luma(f_rgb, lam=1.0, p=0.8, eps=1e-4, N=4, k=0.0):
     uY = ils_channel(Y, lam, p, eps, N)
     Yp = detail_enhance(Y, uY, k)
     return f + (Yp - Y)[None, :, :]
+
+
+LUMA_FLOOR = 1e-12  # reading: the log of a black pixel is taken at this luminance
+
+
+def log_luma(f_rgb):
+    """l = ln max(Y, LUMA_FLOOR) of a linear-radiance RGB image: Sec. 4.2 compresses only the
+    luminance of an HDR image and smooths its logarithm.  Readings: natural log, BT.601 luma."""
+    return np.log(np.maximum(luma(f_rgb), LUMA_FLOOR))
+
+
+def tonemap_log(f_rgb, s, k=1.0, o=0.0, lam=10.0, p=1.0, eps=1e-4, N=4):
+    """Single-scale HDR tone mapping in the base / detail form of Sec. 4.2 (the paper's
+    single-scale setting: p = 1, lambda = 10).  The log-luminance l is split into the base
+    layer b = ILS(l) and the detail d = l - b; the new log-luminance is l' = s b + k d (s < 1
+    compresses the base, k boosts details) and every colour channel is scaled by the change of
+    luminance, exp(l' - l), times exp(o) (exposure).  Returns (out, b, d).  Readings: the
+    paper runs these steps inside a third-party framework whose compression is not stated;
+    this is the linear base compression with colour ratios kept."""
+    f = np.asarray(f_rgb, dtype=np.float64)
+    l = log_luma(f)
+    b = ils_channel(l, lam, p, eps, N)
+    d = l - b
+    lp = s * b + k * d
+    return f * np.exp(lp - l + o)[None, :, :], b, d
+
+
+def hwc_to_planar(x):
+    """H x W x C (channels of a pixel adjacent) to C x H x W."""
+    return np.ascontiguousarray(np.transpose(np.asarray(x), (2, 0, 1)))
+
+
+def planar_to_hwc(x):
+    """C x H x W to H x W x C."""
+    return np.ascontiguousarray(np.transpose(np.asarray(x), (1, 2, 0)))
+
+
+def ils_smooth_hwc(f_hwc, lam=1.0, p=0.8, eps=1e-4, N=4):
+    """ILS of a pixel-interleaved image: the channels are independent (Sec. 3.4, option II),
+    so it is ILS of each channel plane, stored back interleaved."""
+    return planar_to_hwc(ils_smooth(hwc_to_planar(f_hwc), lam, p, eps, N))
 
 
 # ----------------------------------------------------------------------------

@@ -140,6 +140,29 @@ __global__ void luma_kernel(const float* __restrict__ rgb, float* __restrict__ y
     y[i] = fmaf(0.299f, rgb[i], fmaf(0.587f, rgb[n + i], 0.114f * rgb[2 * n + i]));
 }
 
+// l = ln max(Y, kLumaFloor) with Y the BT.601 luma of a 3-plane image (the log-luminance
+// that Sec. 4.2 smooths for HDR tone mapping; the floor keeps l finite on black pixels).
+constexpr float kLumaFloor = 1e-12f;
+__global__ void log_luma_kernel(const float* __restrict__ rgb, float* __restrict__ l, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    l[i] = logf(fmaxf(fmaf(0.299f, rgb[i], fmaf(0.587f, rgb[n + i], 0.114f * rgb[2 * n + i])), kLumaFloor));
+}
+
+// Pixel-interleaved (H x W x C) to planar (C x H x W); one thread per pixel.
+__global__ void hwc_to_planar_kernel(const float* __restrict__ src, float* __restrict__ dst, int C, size_t hw) {
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += (size_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < C; ++c) dst[c * hw + p] = src[p * C + c];
+}
+
+// The output stage alone, with u = f (a plan with N = 0: u^0 = f is the result).
+template <int MODE>
+__global__ void epilogue_only_kernel(Epilogue epi, const float* __restrict__ f, float* out, size_t pairs) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += (size_t)gridDim.x * blockDim.x)
+    epi.template store<MODE>(reinterpret_cast<float2*>(out), i, reinterpret_cast<const float2*>(f)[i]);
+}
+
+int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 4096)); }
+
 // Parameters and tables of iteration `it` (the same for every iteration unless the plan is a
 // half-quadratic-splitting one, whose weight beta_n changes).
 const MuParams& iter_mp(const ils_plan* pl, int it) { return pl->mp_iter.empty() ? pl->mp : pl->mp_iter[it]; }
@@ -162,6 +185,7 @@ ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float
   d.C = cn;
   Epilogue epi = epi_in;
   if (epi.mode == 1) epi.f += off;
+  if (epi.mode == 3) epi.c0 += c0;
   f += off;
   u += off;
   if (u0 != nullptr) u0 += off;
@@ -197,6 +221,13 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
   const size_t bytes = n * sizeof(float);
   cudaError_t e;
   if (pl->N == 0) {
+    if (epi.mode == 3 || epi.mode == 4) {  // u = f through the output stage
+      const size_t pairs = n / 2;
+      if (epi.mode == 3) epilogue_only_kernel<3><<<grid_for(pairs), 256, 0, st>>>(epi, f, u, pairs);
+      else epilogue_only_kernel<4><<<grid_for(pairs), 256, 0, st>>>(epi, f, u, pairs);
+      e = cudaGetLastError();
+      return e == cudaSuccess ? ILS_OK : cuda_fail(e, "output stage launch");
+    }
     e = cudaMemcpyAsync(u, u0 ? u0 : f, bytes, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
   }
@@ -573,6 +604,67 @@ ils_status ils_smooth_luma(ils_plan* pl, const float* rgb, float* out, float k, 
   Epilogue epi;
   epi.mode = 2;
   epi.s = 1.0f - k;
+  epi.f = pl->luma;
+  epi.rgb = rgb;
+  epi.plane2 = n / 2;
+  return run_ils(pl, pl->luma, nullptr, out, nullptr, st, epi);
+}
+
+ils_status ils_smooth_hwc(ils_plan* pl, const float* f_hwc, float* u_hwc, void* stream) {
+  if (pl == nullptr || f_hwc == nullptr || u_hwc == nullptr) return ILS_ERR_INVALID_ARG;
+  const size_t hw = (size_t)pl->H * pl->W, n = (size_t)pl->C * hw;
+  if (n / 2 >= ((size_t)1 << 32)) return ILS_ERR_UNSUPPORTED_SIZE;  // 32-bit pair index of the output stage
+  if (overlaps(f_hwc, u_hwc, n * sizeof(float))) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (pl->N == 0) {
+    e = cudaMemcpyAsync(u_hwc, f_hwc, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
+  }
+  if (pl->stage_f == nullptr) {
+    ils_status s = dev_alloc((void**)&pl->stage_f, n * sizeof(float));
+    if (s != ILS_OK) return s;
+  }
+  hwc_to_planar_kernel<<<grid_for(hw), 256, 0, st>>>(f_hwc, pl->stage_f, pl->C, hw);
+  if ((e = cudaGetLastError())) return cuda_fail(e, "interleaved load launch");
+  Epilogue epi;
+  epi.mode = 3;
+  epi.dst = u_hwc;
+  epi.C = pl->C;
+  epi.plane2 = hw / 2;
+  // the planar image is the only planar buffer; the output stage writes u_hwc instead of it
+  return run_ils(pl, pl->stage_f, nullptr, pl->stage_f, nullptr, st, epi);
+}
+
+ils_status ils_log_luma(const float* rgb, float* l, int H, int W, void* stream) {
+  if (rgb == nullptr || l == nullptr || H < 1 || W < 1) return ILS_ERR_INVALID_ARG;
+  const size_t n = (size_t)H * W;
+  if (overlaps2(rgb, 3 * n * sizeof(float), l, n * sizeof(float))) return ILS_ERR_INVALID_ARG;
+  log_luma_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(rgb, l, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ILS_OK : cuda_fail(e, "log-luminance launch");
+}
+
+ils_status ils_tonemap_log(ils_plan* pl, const float* rgb, float* out, float s, float k, float o, void* stream) {
+  if (pl == nullptr || rgb == nullptr || out == nullptr || pl->C != 1 || !std::isfinite(s) || !std::isfinite(k) ||
+      !std::isfinite(o))
+    return ILS_ERR_INVALID_ARG;
+  const size_t n = (size_t)pl->H * pl->W;
+  if (overlaps(rgb, out, 3 * n * sizeof(float))) return ILS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->luma == nullptr) {
+    ils_status r = dev_alloc((void**)&pl->luma, n * sizeof(float));
+    if (r != ILS_OK) return r;
+  }
+  log_luma_kernel<<<grid_for(n), 256, 0, st>>>(rgb, pl->luma, n);
+  cudaError_t e;
+  if ((e = cudaGetLastError())) return cuda_fail(e, "log-luminance launch");
+  // l' = s b + k (l - b) and out_c = rgb_c exp(l' - l + o) = rgb_c exp((k - 1) l + (s - k) b + o)
+  Epilogue epi;
+  epi.mode = 4;
+  epi.a = k - 1.0f;
+  epi.s = s - k;
+  epi.o = o;
   epi.f = pl->luma;
   epi.rgb = rgb;
   epi.plane2 = n / 2;

@@ -64,34 +64,60 @@ constexpr int kPenalties = 3;
 //   mode 0: out = u;
 //   mode 1: out = f + s (u - f) per channel (detail enhancement: s = 1 - k, k the boost);
 //   mode 2: luminance-only colour (Sec. 3.4, option I): f is the luma Y of the 3-plane image
-//           rgb and out_c = rgb_c + s (u - Y) for the three planes.
+//           rgb and out_c = rgb_c + s (u - Y) for the three planes;
+//   mode 3: pixel-interleaved output: channel c0 + i / plane2 of pair i goes to dst, whose
+//           pixels hold C channels each (out is not written);
+//   mode 4: log-luminance tone mapping (Sec. 4.2: smoothing on the logarithm of the
+//           luminance): f is l = ln Y of the 3-plane image rgb, u the base layer b, and
+//           out_c = rgb_c exp(a l + s b + o) for the three planes.
 struct Epilogue {
   int mode = 0;
   float s = 1.0f;
+  float a = 0.0f, o = 0.0f;  // mode 4
   const float* f = nullptr;
   const float* rgb = nullptr;
-  size_t plane2 = 0;  // mode 2: pixel pairs per plane (H W / 2)
+  float* dst = nullptr;      // mode 3
+  int C = 1, c0 = 0;         // mode 3: channels per pixel of dst, channel of the first plane
+  size_t plane2 = 0;         // modes 2-4: pixel pairs per plane (H W / 2)
   // MODE is the kernel's compile-time copy of `mode` (one instantiation per mode)
   template <int MODE>
   __device__ __forceinline__ void store(float2* out, size_t i, float2 u) const {
     if constexpr (MODE == 0) {
       out[i] = u;
-      return;
-    }
-    const float2 fv = reinterpret_cast<const float2*>(f)[i];
-    const float dx = s * (u.x - fv.x), dy = s * (u.y - fv.y);
-    if constexpr (MODE == 1) {
-      out[i] = make_float2(fv.x + dx, fv.y + dy);
-      return;
-    }
-    const float2* src = reinterpret_cast<const float2*>(rgb);
+    } else if constexpr (MODE == 3) {
+      // 32-bit split of the pair index (the host limits interleaved images to < 2^32 pairs)
+      const unsigned ii = (unsigned)i, p2 = (unsigned)plane2;
+      const unsigned c = ii / p2, q = ii - c * p2;
+      float* px = dst + (size_t)2 * q * C + c0 + c;
+      px[0] = u.x;
+      px[C] = u.y;
+    } else {
+      const float2 fv = reinterpret_cast<const float2*>(f)[i];
+      if constexpr (MODE == 4) {
+        const float gx = expf(fmaf(a, fv.x, fmaf(s, u.x, o))), gy = expf(fmaf(a, fv.y, fmaf(s, u.y, o)));
+        const float2* src = reinterpret_cast<const float2*>(rgb);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2 a = src[c * plane2 + i];
-      out[c * plane2 + i] = make_float2(a.x + dx, a.y + dy);
+        for (int c = 0; c < 3; ++c) {
+          const float2 v = src[c * plane2 + i];
+          out[c * plane2 + i] = make_float2(v.x * gx, v.y * gy);
+        }
+      } else {
+        const float dx = s * (u.x - fv.x), dy = s * (u.y - fv.y);
+        if constexpr (MODE == 1) {
+          out[i] = make_float2(fv.x + dx, fv.y + dy);
+        } else {
+          const float2* src = reinterpret_cast<const float2*>(rgb);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float2 v = src[c * plane2 + i];
+            out[c * plane2 + i] = make_float2(v.x + dx, v.y + dy);
+          }
+        }
+      }
     }
   }
 };
+constexpr int kEpilogues = 5;
 
 // Launch geometry picked by the host planner (validated before any launch).
 struct Geometry {

@@ -476,6 +476,10 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(row_inverse_kernel<32, 1>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16, 2>))) return e;
   if ((e = allow_smem(row_inverse_kernel<32, 2>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 3>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 3>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 4>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 4>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<32, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 1>))) return e;
@@ -522,9 +526,13 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
   if (g.warp_row >= 0) return warp_row_inverse(g.warp_row, d, t, spec, u, stream, epi);
   if (g.fixed_row >= 0) return fixed_row_inverse(g.fixed_row, d, t, spec, u, stream, epi);
   dim3 grid((d.H + g.rows_inv - 1) / g.rows_inv, d.C);
-  auto fn = epi.mode == 0   ? (g.ept_inv == 16 ? row_inverse_kernel<16, 0> : row_inverse_kernel<32, 0>)
-            : epi.mode == 1 ? (g.ept_inv == 16 ? row_inverse_kernel<16, 1> : row_inverse_kernel<32, 1>)
-                            : (g.ept_inv == 16 ? row_inverse_kernel<16, 2> : row_inverse_kernel<32, 2>);
+  using InvFn = void (*)(int, int, int, FftPlan, const float2*, const float2*, float*, Epilogue);
+  static const InvFn fns[2][kEpilogues] = {
+      {row_inverse_kernel<16, 0>, row_inverse_kernel<16, 1>, row_inverse_kernel<16, 2>, row_inverse_kernel<16, 3>,
+       row_inverse_kernel<16, 4>},
+      {row_inverse_kernel<32, 0>, row_inverse_kernel<32, 1>, row_inverse_kernel<32, 2>, row_inverse_kernel<32, 3>,
+       row_inverse_kernel<32, 4>}};
+  const InvFn fn = fns[g.ept_inv == 16 ? 0 : 1][epi.mode];
   return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u,
                   epi);
 }

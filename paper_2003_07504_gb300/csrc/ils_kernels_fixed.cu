@@ -484,7 +484,7 @@ using ColFn = void (*)(int, int, const float2*, const float*, const float*, floa
 struct RowEntry {
   int M, tps, rows_fwd, rows_inv;
   RowFwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
-  RowInvFn inv[3];              // per epilogue mode
+  RowInvFn inv[kEpilogues];     // per epilogue mode
 };
 struct ColEntry {
   int H, tps, G;
@@ -502,7 +502,8 @@ constexpr RowEntry row_entry() {
                    row_fwd_fixed_kernel<PL, RF, true, 2>},
                   {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>,
                    row_fwd_fixed_kernel<PL, RF, false, 2>},
-                  {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>}};
+                  {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>,
+                   row_inv_fixed_kernel<PL, RI, 3>, row_inv_fixed_kernel<PL, RI, 4>}};
 }
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
@@ -578,7 +579,7 @@ cudaError_t fixed_set_attributes() {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
-    for (int m = 0; m < 3; ++m)
+    for (int m = 0; m < kEpilogues; ++m)
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   for (const ColEntry& c : kCols) {

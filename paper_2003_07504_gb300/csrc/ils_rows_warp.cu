@@ -350,7 +350,7 @@ using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
   FwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
-  InvFn inv[3];              // per epilogue mode
+  InvFn inv[kEpilogues];     // per epilogue mode
 };
 
 // STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
@@ -369,7 +369,8 @@ constexpr WarpRowEntry warp_entry() {
                       {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB>,
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>,
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB>},
-                      {row_warp_inv_kernel<L, RI, 0>, row_warp_inv_kernel<L, RI, 1>, row_warp_inv_kernel<L, RI, 2>}};
+                      {row_warp_inv_kernel<L, RI, 0>, row_warp_inv_kernel<L, RI, 1>, row_warp_inv_kernel<L, RI, 2>,
+                       row_warp_inv_kernel<L, RI, 3>, row_warp_inv_kernel<L, RI, 4>}};
 }
 
 // The first entry of a length is its default; the others are autotune alternatives.
@@ -404,7 +405,7 @@ cudaError_t warp_set_attributes() {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
-    for (int m = 0; m < 3; ++m)
+    for (int m = 0; m < kEpilogues; ++m)
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   return cudaSuccess;

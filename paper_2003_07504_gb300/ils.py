@@ -127,6 +127,31 @@ class Plan:
                                               _stream_ptr(stream)), "ils_smooth_luma")
         return out
 
+    def smooth_hwc(self, f: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """u = ILS(f) for a pixel-interleaved H x W x C image (the planar copy Algorithm 1 re-reads
+        is made by a gather kernel; the final inverse pass writes u interleaved)."""
+        _check_image(f, (self.H, self.W, self.C), "f")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_image(out, (self.H, self.W, self.C), "out")
+        _lib.check(_lib.lib().ils_smooth_hwc(self._h, f.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+                   "ils_smooth_hwc")
+        return out
+
+    def tonemap(self, rgb: torch.Tensor, s: float, k: float = 1.0, o: float = 0.0,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Single-scale HDR tone mapping of a 3 x H x W linear-radiance image (plan made with C = 1):
+        b = ILS(l) of l = ln Y, l' = s b + k (l - b), out_c = rgb_c exp(l' - l + o)."""
+        if self.C != 1:
+            raise ValueError("tonemap needs a plan with C = 1")
+        _check_image(rgb, (3, self.H, self.W), "rgb")
+        if out is None:
+            out = torch.empty_like(rgb)
+        _check_image(out, (3, self.H, self.W), "out")
+        _lib.check(_lib.lib().ils_tonemap_log(self._h, rgb.data_ptr(), out.data_ptr(), float(s), float(k), float(o),
+                                              _stream_ptr(stream)), "ils_tonemap_log")
+        return out
+
     def smooth_checkpointed(self, f: torch.Tensor, out: torch.Tensor | None = None,
                             u0: torch.Tensor | None = None, stream=None):
         """Forward pass that also returns the iterates u^0..u^{N-1} (N x C x H x W) for backward()."""
@@ -287,3 +312,17 @@ def smooth(f: torch.Tensor, lam: float = 1.0, p: float = 0.8, eps: float = 1e-4,
             plan = Plan(H, W, C, lam, p, eps, N)
         _plans[key] = plan
     return plan.smooth(f, u0=u0)
+
+
+def log_luma(rgb: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """l = ln max(Y, 1e-12), Y = 0.299 R + 0.587 G + 0.114 B, of a 3 x H x W CUDA tensor: the
+    log-luminance whose smoothing b = ILS(l) splits an HDR image into base b and detail l - b."""
+    if rgb.dim() != 3 or rgb.shape[0] != 3:
+        raise ValueError(f"rgb: expected shape (3, H, W), got {tuple(rgb.shape)}")
+    H, W = int(rgb.shape[1]), int(rgb.shape[2])
+    _check_image(rgb, (3, H, W), "rgb")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=rgb.device)
+    _check_image(out, (H, W), "out")
+    _lib.check(_lib.lib().ils_log_luma(rgb.data_ptr(), out.data_ptr(), H, W, _stream_ptr(stream)), "ils_log_luma")
+    return out

@@ -91,6 +91,35 @@ def test_autotuned_batch_at_the_serving_sizes(ils, tmp_path, monkeypatch):
         assert [b2.choice(i)[1:] for i in range(len(frames))] == [c[1:] for c in choices]
 
 
+def energy64(u, f, lam, p, eps):
+    """Eq. 1 with the Eq. 2 penalty, periodic forward differences, float64 (test-side)."""
+    gx = np.roll(u, -1, axis=-1) - u
+    gy = np.roll(u, -1, axis=-2) - u
+    return float(((u - f) ** 2).sum() + lam * (((gx ** 2 + eps) ** (p / 2)).sum() + ((gy ** 2 + eps) ** (p / 2)).sum()))
+
+
+def test_batch_of_4k_frames_with_large_iteration_counts(ils):
+    # 3840 x 2160 frames with N = 10 and 15 in one graph launch: the same bits as the plan path,
+    # the mean of every channel kept (the DC denominator is 1), and Eq. 1's energy below that
+    # of fewer iterations (Appendix A: it decreases monotonically)
+    import torch
+    specs = [(3, 2160, 3840, 1.0, 0.8, 10), (3, 2160, 3840, 2.0, 1.0, 15), (1, 2160, 3840, 0.5, 0.8, 15),
+             (3, 1080, 1920, 1.5, 0.8, 10)]
+    frames = make_frames(specs, seed0=300)
+    with ils.Batch(frames) as b:
+        b.run()
+        torch.cuda.synchronize()
+    for (f, u, lam, p, eps, N) in frames:
+        assert bool(torch.isfinite(u).all())
+        assert torch.equal(u, plan_result(ils, f, lam, p, N))
+        dm = (u.double().mean(dim=(1, 2)) - f.double().mean(dim=(1, 2))).abs().max().item()
+        assert dm <= 1e-5, dm
+        f64 = f.cpu().numpy().astype(np.float64)
+        e_n = energy64(u.cpu().numpy().astype(np.float64), f64, lam, p, eps)
+        e_fewer = energy64(plan_result(ils, f, lam, p, N - 6).cpu().numpy().astype(np.float64), f64, lam, p, eps)
+        assert e_n < e_fewer, (f.shape, N, e_n, e_fewer)
+
+
 def test_batch_rejects_bad_frames(ils):
     import torch
     from paper_2003_07504_gb300._lib import ILSError

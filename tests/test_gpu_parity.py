@@ -321,6 +321,67 @@ def test_luma_with_the_welsch_penalty(ils):
     assert_parity(out, want)
 
 
+# -------------------------------------------------------------- pixel-interleaved images (H x W x C)
+
+@pytest.mark.parametrize("H,W,C", [(256, 256, 3), (40, 1920, 3), (16, 3840, 2), (27, 250, 1), (60, 80, 4)])
+def test_hwc_matches_oracle_and_planar_path(ils, H, W, C):
+    import torch
+    f = image(H, W, C, seed=3 * H + W + C)
+    fh = np.ascontiguousarray(O.planar_to_hwc(f))
+    fht = torch.from_numpy(fh).cuda()
+    with ils.Plan(H, W, C, 1.0, 0.8, 1e-4, 4) as plan:
+        uh = plan.smooth_hwc(fht)
+        # the same kernels on the planar copy: bit-identical to the planar entry point
+        up = plan.smooth(torch.from_numpy(np.ascontiguousarray(f)).cuda())
+        assert torch.equal(uh.permute(2, 0, 1), up)
+        uh2 = plan.smooth_hwc(fht)  # a second call reuses the plan's planar buffer
+        assert torch.equal(uh2, uh)
+    assert_parity(uh.cpu().numpy(), O.ils_smooth_hwc(fh.astype(np.float64), 1.0, 0.8, 1e-4, 4))
+    with ils.Plan(H, W, C, 1.0, 0.8, 1e-4, 0) as plan0:   # N = 0: u = f
+        assert torch.equal(plan0.smooth_hwc(fht), fht)
+
+
+# -------------------------------------------------------------- log-luminance HDR tone mapping (Sec. 4.2)
+
+def hdr_image(H, W, seed, stops=12.0):
+    """Linear radiance over 2^stops: exp2 of a scaled synthetic texture per channel."""
+    g = image(H, W, 3, seed=seed).astype(np.float64)
+    return np.exp2(stops * (g - 0.5)).astype(np.float32)
+
+
+@pytest.mark.parametrize("H,W", [(256, 256), (40, 1920), (16, 3840), (27, 250)])
+def test_tonemap_matches_oracle(ils, H, W):
+    import torch
+    f = hdr_image(H, W, seed=11 * H + W)
+    ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    f64 = f.astype(np.float64)
+    lam, p, N = 10.0, 1.0, 4
+    # l = ln Y: FP32 log of an FP32 luma against FP64 (a few ulp of |l| <= 4.2)
+    l_gpu = ils.log_luma(ft).cpu().numpy()
+    l_want = O.log_luma(f64)
+    assert np.abs(l_gpu - l_want).max() <= 4e-6
+    scale = max(1.0, float(np.abs(l_want).max()))   # FP32 rounding grows with |l|
+    with ils.Plan(H, W, 1, lam, p, 1e-4, N) as plan:
+        b_gpu = plan.smooth(torch.from_numpy(l_gpu).cuda()).cpu().numpy()
+        b_want = O.ils_channel(l_gpu.astype(np.float64), lam, p, 1e-4, N)
+        assert_parity(b_gpu, b_want, tol_max=MAX_ABS_TOL * scale, tol_rms=RMS_TOL * scale)
+        for s_, k_, o_ in ((0.35, 1.0, 0.0), (0.5, 2.0, -0.3)):
+            out = plan.tonemap(ft, s_, k_, o_).cpu().numpy().astype(np.float64)
+            want, _, _ = O.tonemap_log(f64, s_, k_, o_, lam, p, 1e-4, N)
+            # relative error = error of the exponent (k - 1) l + (s - k) b + o
+            rel = np.abs(out / want - 1.0)
+            amp = abs(s_ - k_)
+            assert rel.max() <= MAX_ABS_TOL * scale * amp + 2e-5, f"max rel {rel.max():.3g}"
+            assert np.sqrt(np.mean(rel ** 2)) <= RMS_TOL * scale * amp + 2e-6
+    with ils.Plan(H, W, 1, lam, p, 1e-4, 0) as plan0:   # N = 0: b = l, out_c = rgb_c Y^(s-1) e^o
+        out = plan0.tonemap(ft, 0.5, 2.0, 0.1).cpu().numpy().astype(np.float64)
+        want, _, _ = O.tonemap_log(f64, 0.5, 2.0, 0.1, lam, p, 1e-4, 0)
+        assert np.abs(out / want - 1.0).max() <= 2e-5
+    with ils.Plan(H, W, 3, lam, p, 1e-4, N) as plan3:
+        with pytest.raises(ValueError):
+            plan3.tonemap(ft, 0.5)
+
+
 # -------------------------------------------------------------- half-quadratic splitting (Sec. 3.5, the comparison method)
 
 @pytest.mark.parametrize("H,W,C,lam,N", [

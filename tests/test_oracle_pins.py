@@ -520,6 +520,85 @@ def test_detail_enhance_limits():
     np.testing.assert_allclose(O.detail_enhance(f, u, 3.0) - u, 3.0 * (f - u), atol=1e-14)
 
 
+# ---------------------------------------------------------------- HDR tone mapping (Sec. 4.2)
+
+def hdr_image(H, W, seed, stops=12.0):
+    """Linear radiance spanning 2^stops: exp2 of a scaled synthetic texture per channel."""
+    g = synth.voronoi_texture(H, W, 3, K=5, A=0.05, Tmin=3, Tmax=5, sigma=0.02, seed=seed).astype(np.float64)
+    return np.exp2(stops * (g - 0.5))
+
+
+def test_log_luma_floor_and_value():
+    f = hdr_image(6, 8, seed=41)
+    f[:, 2, 3] = 0.0                      # a black pixel
+    l = O.log_luma(f)
+    assert l[2, 3] == pytest.approx(np.log(1e-12), abs=1e-12)
+    y = 0.299 * f[0, 1, 1] + 0.587 * f[1, 1, 1] + 0.114 * f[2, 1, 1]
+    assert l[1, 1] == pytest.approx(np.log(y), abs=1e-13)
+
+
+def test_tonemap_identity_and_lambda_zero_closed_form():
+    f = hdr_image(10, 12, seed=43)
+    out, b, d = O.tonemap_log(f, s=1.0, k=1.0, o=0.0, lam=10.0, N=4)
+    np.testing.assert_allclose(out, f, rtol=1e-12)
+    # lambda = 0: the base is l itself (u = f for every N), so out_c = f_c Y^(s - 1) e^o
+    s_, o_ = 0.4, 0.3
+    Y = 0.299 * f[0] + 0.587 * f[1] + 0.114 * f[2]
+    out0, b0, d0 = O.tonemap_log(f, s=s_, k=2.0, o=o_, lam=0.0, N=3)
+    np.testing.assert_allclose(out0, f * np.power(Y, s_ - 1.0)[None] * np.exp(o_), rtol=1e-12)
+    np.testing.assert_allclose(d0, 0.0, atol=1e-12)
+
+
+def test_tonemap_output_log_luminance_is_compressed_base_plus_boosted_detail():
+    # ln Y(out) = s b + k d + o, with b + d = ln Y(f): the colour scaling applies exactly the
+    # intended change of log-luminance (luminance is linear in the channels)
+    f = hdr_image(12, 16, seed=47)
+    s_, k_, o_ = 0.35, 1.5, -0.2
+    out, b, d = O.tonemap_log(f, s=s_, k=k_, o=o_, lam=10.0, N=4)
+    Yf = 0.299 * f[0] + 0.587 * f[1] + 0.114 * f[2]
+    Yo = 0.299 * out[0] + 0.587 * out[1] + 0.114 * out[2]
+    np.testing.assert_allclose(b + d, np.log(Yf), atol=1e-12)
+    np.testing.assert_allclose(np.log(Yo), s_ * b + k_ * d + o_, atol=1e-11)
+    # colour ratios are kept
+    np.testing.assert_allclose(out[0] / out[1], f[0] / f[1], rtol=1e-12)
+    np.testing.assert_allclose(out[2] / out[1], f[2] / f[1], rtol=1e-12)
+    # the smoothing keeps the mean (the DC denominator is 1), so the detail layer has zero mean
+    assert abs(d.mean()) < 1e-12
+
+
+def test_tonemap_exposure_equivariance():
+    # ILS commutes with adding a constant (gradients ignore it; the DC denominator is 1), so
+    # scaling the radiance by g scales the tone-mapped image by g^s
+    f = hdr_image(8, 10, seed=53)
+    s_, k_ = 0.5, 1.2
+    a, _, _ = O.tonemap_log(f, s=s_, k=k_, lam=10.0, N=4)
+    g = 37.0
+    bb, _, _ = O.tonemap_log(g * f, s=s_, k=k_, lam=10.0, N=4)
+    np.testing.assert_allclose(bb, g ** s_ * a, rtol=1e-9)
+
+
+# ---------------------------------------------------------------- interleaved (H x W x C) images
+
+def test_hwc_layout_by_explicit_indexing():
+    H, W, C = 3, 4, 3
+    x = np.arange(H * W * C, dtype=np.float64).reshape(H, W, C)
+    p = O.hwc_to_planar(x)
+    flat = x.ravel()
+    for c in range(C):
+        for y in range(H):
+            for xx in range(W):
+                assert p[c, y, xx] == flat[(y * W + xx) * C + c]
+    np.testing.assert_array_equal(O.planar_to_hwc(p), x)
+
+
+def test_ils_smooth_hwc_is_per_channel_smoothing():
+    f = synth.voronoi_texture(10, 12, 3, K=5, A=0.05, Tmin=3, Tmax=5, sigma=0.02, seed=59).astype(np.float64)
+    fh = np.stack([f[0], f[1], f[2]], axis=-1)
+    uh = O.ils_smooth_hwc(fh, 1.0, 0.8, 1e-4, 4)
+    for c in range(3):
+        np.testing.assert_allclose(uh[:, :, c], O.ils_channel(f[c], 1.0, 0.8, 1e-4, 4), atol=1e-14)
+
+
 # ---------------------------------------------------------------- half-quadratic splitting (Sec. 3.5)
 
 def test_hqs_q1_is_the_argmin_and_matches_huber():
