@@ -364,7 +364,7 @@ ils_status ils_get_profile(const ils_plan* plan, double* ms, long long* launches
  *
  * Limits: C*H*W <= ILS_NOALLOC_MAX_ELEMS (2^21 floats, e.g. one 1920 x 1080
  * channel) and H, W <= ILS_NOALLOC_MAX_SIDE; larger images return
- * ILS_ERR_UNSUPPORTED_SIZE.  The array (about 16.2 MiB) is part of the library:
+ * ILS_ERR_UNSUPPORTED_SIZE.  The array (about 16.3 MiB) is part of the library:
  * every GPU that loads libils.so holds it until the process exits.
  *
  * The first call on a device looks up the array's device address with that

@@ -350,7 +350,10 @@ ils_status ils_batch_create(const ils_frame* frames, int count, int flags, ils_b
       }
       B->cls.push_back(c);
       ci = (int)B->cls.size() - 1;
-      if ((e = upload(&B->cls[ci].twW, roots(f.W))) || (e = upload(&B->cls[ci].twH, roots(f.H)))) {
+      std::vector<float2> th = roots(f.H);
+      th.resize(col_twiddle_count(f.H));  // stage tables, gathered on the device below
+      if ((e = upload(&B->cls[ci].twW, row_twiddles(f.W))) || (e = upload(&B->cls[ci].twH, th)) ||
+          (e = build_col_twiddles(f.H, B->cls[ci].twH, 0)) || (e = cudaStreamSynchronize(0))) {
         s = fail(e, "class tables");
         break;
       }

@@ -263,6 +263,17 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
 }  // namespace
 
 namespace ils {
+std::vector<float2> row_twiddles(int W) {
+  const int M = W / 2;
+  std::vector<float2> v = roots(W);
+  v.resize((size_t)W + M);
+  for (int t = 0; t < M; ++t) {
+    const int k2 = t / 32, n1 = t % 32;
+    v[(size_t)W + t] = v[(size_t)(2 * n1 * k2) % W];  // exp(-2 pi i n1 k2 / M)
+  }
+  return v;
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("ILS_PDL");
@@ -328,8 +339,8 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
   ils_status s;
   if ((s = dev_alloc((void**)&pl->spec[0], plane * sizeof(float2))) ||
       (s = dev_alloc((void**)&pl->spec[1], plane * sizeof(float2))) ||
-      (s = dev_alloc((void**)&pl->tab.twW, (size_t)W * sizeof(float2))) ||
-      (s = dev_alloc((void**)&pl->tab.twH, (size_t)H * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.twW, (size_t)(W + M) * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.twH, col_twiddle_count(H) * sizeof(float2))) ||
       (s = dev_alloc((void**)&pl->tab.ax, (size_t)(M + 1) * sizeof(float))) ||
       (s = dev_alloc((void**)&pl->tab.by, (size_t)H * sizeof(float)))) {
     free_plan_memory(pl);
@@ -347,14 +358,15 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
     const double s1 = std::sin(M_PI * (double)l / (double)H);
     by[l] = (float)(2.0 * (double)lambda * c * s1 * s1);
   }
-  std::vector<float2> tw = roots(W), th = roots(H);
+  std::vector<float2> tw = row_twiddles(W), th = roots(H);
   if ((e = cudaMemcpy(pl->tab.twW, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.twH, th.data(), th.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.ax, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(pl->tab.by, by.data(), by.size() * sizeof(float), cudaMemcpyHostToDevice))) {
+      (e = cudaMemcpy(pl->tab.by, by.data(), by.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = build_col_twiddles(H, pl->tab.twH, 0)) || (e = cudaStreamSynchronize(0))) {
     free_plan_memory(pl);
     delete pl;
-    return cuda_fail(e, "cudaMemcpy tables");
+    return cuda_fail(e, "tables");
   }
   // 2..8 channels: one internal stream per channel (at most 4); ILS_SPLIT=0 keeps one stream
   const char* split = std::getenv("ILS_SPLIT");

@@ -51,6 +51,36 @@ __device__ __forceinline__ void bfly(float2 (&v)[R], int j, const float2* __rest
   dft_reg<R, INV>(v);
 }
 
+// Stage twiddle tables of a plan, r-major so that threads with consecutive k read
+// consecutive entries: a stage with stride NS and radix R keeps w_N^{k (N/(NS R)) r} at
+// tab[(r - 1) NS + k], r = 1..R-1, k < NS.  Order: forward middle stage (three-stage plans),
+// forward last stage, inverse middle stage, inverse last stage (the inverse conjugates).
+template <class PL>
+struct StageTw {
+  static constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
+  static constexpr bool MID = PL::STAGES == 3;
+  static constexpr int FWD_MID = 0;                                    // NS = R0, R = R1
+  static constexpr int FWD_LAST = FWD_MID + (MID ? (R1 - 1) * R0 : 0);   // NS = N / RL, R = RL
+  static constexpr int INV_MID = FWD_LAST + (RL - 1) * (N / RL);       // NS = RL, R = R1
+  static constexpr int INV_LAST = INV_MID + (MID ? (R1 - 1) * RL : 0);   // NS = N / R0, R = R0
+  static constexpr int SIZE = INV_LAST + (R0 - 1) * (N / R0);
+};
+
+// bfly with the twiddles of a StageTw table (the same values as root(), read coalesced).
+template <int R, int NS, bool INV>
+__device__ __forceinline__ void bfly_tab(float2 (&v)[R], int j, const float2* __restrict__ tab) {
+  if constexpr (NS > 1) {
+    const int k = j % NS;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = __ldg(&tab[(r - 1) * NS + k]);
+      if (INV) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+  }
+  dft_reg<R, INV>(v);
+}
+
 // Output position of butterfly j's element r in a stage with radix R and stride NS.
 template <int R, int NS>
 __device__ __forceinline__ int out_pos(int j, int r) {

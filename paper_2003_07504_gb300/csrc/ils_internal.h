@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <utility>
+#include <vector>
 
 #include "ils_fft.cuh"
 
@@ -135,11 +136,17 @@ struct Geometry {
 
 // Device tables for one (H, W, lambda, c).
 struct Tables {
-  float2* twW;   // W entries: exp(-2 pi i t / W)
-  float2* twH;   // H entries: exp(-2 pi i t / H)
+  // W + W/2 entries: exp(-2 pi i t / W) for t < W, then the four-step twiddles of the
+  // warp-per-row transforms, k2-major so that a warp's 32 lanes read 32 consecutive
+  // entries: twW[W + 32 k2 + n1] = exp(-2 pi i n1 k2 / (W/2))  (row_twiddles builds it)
+  float2* twW;
+  float2* twH;   // exp(-2 pi i t / H) for t < H, then stage tables (col_twiddle_count)
   float* ax;     // M+1 entries: lambda c (1 - cos(2 pi k / W)),  k = 0..M
   float* by;     // H entries:   lambda c (1 - cos(2 pi l / H)),  l = 0..H-1
 };
+
+// The row twiddle table of Tables::twW for row length W (host, double precision, rounded once).
+std::vector<float2> row_twiddles(int W);
 
 struct ImageDesc {
   int H, W, C;
@@ -219,6 +226,10 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
                               cudaStream_t stream, const Epilogue& epi);
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream);
+// Tables::twH holds col_twiddle_count(H) entries: the H roots, then the stage twiddle tables
+// of the compile-time column plans of H, gathered from the roots by build_col_twiddles.
+size_t col_twiddle_count(int H);
+cudaError_t build_col_twiddles(int H, float2* twH, cudaStream_t st);
 
 // Warp-per-row kernels (ils_rows_warp.cu).
 int warp_row_variants(int M, int* idx, int max);

@@ -67,12 +67,13 @@ __device__ __forceinline__ float2 r2c_x(float2 a, float2 b, int k, const float2*
 // ---------------------------------------------------------------- column pass
 template <class PL, int G, int MINB>
 __global__ void __launch_bounds__(G * PL::TPS, MINB)
-col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __restrict__ ax,
+col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __restrict__ ax,
                  const float* __restrict__ by, float scale, float2* __restrict__ spec) {
   griddep_launch();
   griddep_wait();
   constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = N / R0, NS1 = N / R1, NSL = N / RL;
+  using TW = StageTw<PL>;  // twc: this plan's stage twiddle tables
   extern __shared__ float2 sm[];
   const int tiles_per_ch = (M + G - 1) / G;
   const int ntiles = tiles_per_ch * C;
@@ -123,7 +124,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly<N, R1, R0, false>(v, j, twH, 1);
+        bfly_tab<R1, R0, false>(v, j, twc + TW::FWD_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -138,7 +139,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
       if (j < NSL) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[r] = S(j + r * NSL);
-        bfly<N, RL, NSL, false>(v, j, twH, 1);
+        bfly_tab<RL, NSL, false>(v, j, twc + TW::FWD_LAST);
       }
       if (k0 == 0) {
         // Column 0 packs two real columns: Z = A + iB with A = F(X[:,0]), B = F(X[:,M]).
@@ -184,7 +185,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly<N, R1, RL, true>(v, j, twH, 1);
+        bfly_tab<R1, RL, true>(v, j, twc + TW::INV_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -199,7 +200,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twH, const float* __re
       if (j < NS0) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) v[r] = S(j + r * NS0);
-        bfly<N, R0, NS0, true>(v, j, twH, 1);
+        bfly_tab<R0, NS0, true>(v, j, twc + TW::INV_LAST);
         if (live) {
 #pragma unroll
           for (int r = 0; r < R0; ++r) col[(size_t)(j + r * NS0) * M] = v[r];
@@ -489,6 +490,7 @@ struct RowEntry {
 struct ColEntry {
   int H, tps, G;
   ColFn fn;
+  int R0, R1, R2, tw;  // radices (R2 = 1: two stages) and StageTw size
 };
 
 template <class PL, int RF, int RI>
@@ -507,7 +509,7 @@ constexpr RowEntry row_entry() {
 }
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
-  return ColEntry{PL::N, PL::TPS, G, col_fixed_kernel<PL, G, MINB>};
+  return ColEntry{PL::N, PL::TPS, G, col_fixed_kernel<PL, G, MINB>, PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE};
 }
 
 // Several entries may share a length: the first is the default, the others are
@@ -569,6 +571,54 @@ int fixed_col_variants(int H, int* idx, int max) {
   return n;
 }
 
+// Twiddle entries of a column table (Tables::twH) for length H: the H roots, then the
+// StageTw tables of every compile-time plan of H in kCols order.
+size_t col_twiddle_count(int H) {
+  size_t n = H;
+  for (const ColEntry& c : kCols)
+    if (c.H == H) n += c.tw;
+  return n;
+}
+
+namespace {
+size_t col_tw_offset(int idx) {
+  size_t off = kCols[idx].H;
+  for (int i = 0; i < idx; ++i)
+    if (kCols[i].H == kCols[idx].H) off += kCols[i].tw;
+  return off;
+}
+
+// One StageTw table gathered from the roots tw[0..N): stage (R, NS) entries
+// tab[(r - 1) NS + k] = tw[k (N / (NS R)) r].
+__global__ void stage_tw_kernel(int N, int R0, int R1, int R2, const float2* __restrict__ tw, float2* __restrict__ tab) {
+  const bool mid = R2 > 1;
+  const int RL = mid ? R2 : R1;
+  // (NS, R) of the four stage tables in StageTw order; zero-size where absent
+  const int ns[4] = {R0, N / RL, RL, N / R0};
+  const int rr[4] = {mid ? R1 : 1, RL, mid ? R1 : 1, R0};
+  int base = 0;
+  for (int s = 0; s < 4; ++s) {
+    const int n = (rr[s] - 1) * ns[s];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const int r = 1 + i / ns[s], k = i % ns[s];
+      tab[base + i] = tw[k * (N / (ns[s] * rr[s])) * r];
+    }
+    base += n;
+  }
+}
+}  // namespace
+
+cudaError_t build_col_twiddles(int H, float2* twH, cudaStream_t st) {
+  for (int i = 0; i < (int)(sizeof(kCols) / sizeof(kCols[0])); ++i) {
+    const ColEntry& c = kCols[i];
+    if (c.H != H) continue;
+    stage_tw_kernel<<<(c.tw + 255) / 256, 256, 0, st>>>(c.H, c.R0, c.R1, c.R2, twH, twH + col_tw_offset(i));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static size_t row_smem(int rows, int M) { return (size_t)smem_elems(rows * M) * sizeof(float2); }
 
 cudaError_t fixed_set_attributes() {
@@ -617,7 +667,8 @@ cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2
   const size_t smem = (size_t)smem_elems(c.H * c.G) * sizeof(float2);
   const int tiles = (M + c.G - 1) / c.G * d.C;
   const float scale = 1.0f / ((float)d.H * (float)d.W);
-  return launch_k(d.pdl, c.fn, tiles, threads, smem, stream, M, d.C, t.twH, t.ax, t.by, scale, spec);
+  return launch_k(d.pdl, c.fn, tiles, threads, smem, stream, M, d.C, t.twH + col_tw_offset(idx), t.ax, t.by, scale,
+                  spec);
 }
 
 }  // namespace ils

@@ -23,8 +23,10 @@ namespace {
 
 constexpr int kSideMax = ILS_NOALLOC_MAX_SIDE;
 constexpr size_t kElemsMax = ILS_NOALLOC_MAX_ELEMS;  // floats per image (C*H*W)
-// table floats: twW (2*side) + twH (2*side) + ax (side/2+1, padded) + by (side)
-constexpr size_t kTableFloats = 2 * kSideMax + 2 * kSideMax + (kSideMax / 2 + 64) + kSideMax;
+// table floats: twW (3*side: W + W/2 complex) + twH (2*(side + kColTw): H roots and the column
+// plans' stage tables) + ax (side/2+1, padded) + by (side)
+constexpr size_t kColTw = 16384;  // complex; at least col_twiddle_count(H) - H for every H
+constexpr size_t kTableFloats = 3 * kSideMax + 2 * (kSideMax + kColTw) + (kSideMax / 2 + 64) + kSideMax;
 constexpr size_t kScratchFloats = 2 * kElemsMax + kTableFloats;
 
 // Shared by every call on a device and kept until the process exits.
@@ -63,6 +65,11 @@ __global__ void noalloc_tables_kernel(int H, int W, double lc, float2* twW, floa
     if (i < W) {
       sincospi(-2.0 * (double)i / (double)W, &s, &c);
       twW[i] = make_float2((float)c, (float)s);
+    }
+    if (i < M) {  // the four-step entries (layout of Tables::twW): the same values as twW[2 n1 k2 mod W]
+      const int k2 = i / 32, n1 = i % 32;
+      sincospi(-2.0 * (double)((2 * n1 * k2) % W) / (double)W, &s, &c);
+      twW[W + i] = make_float2((float)c, (float)s);
     }
     if (i < H) {
       sincospi(-2.0 * (double)i / (double)H, &s, &c);
@@ -120,9 +127,10 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
   float* tab = base + 2 * kElemsMax;
   Tables t;
   t.twW = reinterpret_cast<float2*>(tab);
-  t.twH = reinterpret_cast<float2*>(tab + 2 * kSideMax);
-  t.ax = tab + 4 * kSideMax;
-  t.by = tab + 4 * kSideMax + (kSideMax / 2 + 64);
+  t.twH = reinterpret_cast<float2*>(tab + 3 * kSideMax);
+  t.ax = tab + 5 * kSideMax + 2 * kColTw;
+  t.by = t.ax + (kSideMax / 2 + 64);
+  if (col_twiddle_count(H) > (size_t)kSideMax + kColTw) return ILS_ERR_UNSUPPORTED_SIZE;
 
   const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);
   MuParams mp;
@@ -134,6 +142,7 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
 
   noalloc_tables_kernel<<<(kSideMax + 255) / 256, 256, 0, st>>>(H, W, (double)lambda * c, t.twW, t.twH, t.ax, t.by);
   if ((e = cudaGetLastError())) return ILS_ERR_CUDA;
+  if ((e = build_col_twiddles(H, t.twH, st))) return ILS_ERR_CUDA;
   for (int it = 0; it < N; ++it) {
     float2* out = spec[it & 1];
     const float2* in = it == 0 ? nullptr : spec[(it - 1) & 1];

@@ -48,7 +48,7 @@ struct WarpRow {
     dft_reg<L, INV>(v);
 #pragma unroll
     for (int k2 = 1; k2 < L; ++k2) {
-      float2 w = __ldg(&twW[2 * lane * k2]);
+      float2 w = __ldg(&twW[2 * M + 32 * k2 + lane]);  // w_M^{lane k2}, coalesced (Tables::twW)
       if (INV) w.y = -w.y;
       v[k2] = cmul(v[k2], w);
     }
@@ -67,25 +67,58 @@ struct WarpRow {
     __syncwarp();
   }
 
+  // Hermitian unpacking of the packed half spectrum X for the inverse real transform:
+  // v[n2] = Z[k], k = lane + 32 n2, with Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/(2M)}
+  // (X[k] - conj X[M-k]) and Z[0] from slot 0 = (X[0], X[M]).  SPEC: the row is first copied
+  // into buf with 16-byte asynchronous copies (one request per 16 bytes instead of two 8-byte
+  // loads per pair, off the register scoreboard) and unpacked from shared memory.
+  template <bool SPEC>
+  __device__ __forceinline__ static void load_c2r(const float2* __restrict__ X, float2 (&v)[L], float2* buf, int lane,
+                                                  const float2* __restrict__ twW) {
+    static_assert(!SPEC || L % 2 == 0, "16-byte copies of a 32 L-point row need L even");
+    if constexpr (SPEC) {
+#pragma unroll
+      for (int q = 0; q < L / 2; ++q) cp_async16(buf + 2 * (lane + 32 * q), X + 2 * (lane + 32 * q));
+      cp_async_wait_all();
+      __syncwarp();
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) {
+        const int k = lane + 32 * n2;
+        if (k == 0) {
+          const float2 x = buf[0];
+          v[n2] = c2(x.x + x.y, x.x - x.y);
+        } else {
+          const float2 a = buf[k], b = cconj(buf[M - k]);
+          const float2 s = cadd(a, b), d = csub(a, b);
+          const float2 t = cmul(cconj(__ldg(&twW[k])), d);
+          v[n2] = c2(s.x - t.y, s.y + t.x);
+        }
+      }
+      __syncwarp();  // every lane has read buf before the transform writes it
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) {
+        const int k = lane + 32 * n2;
+        if (k == 0) {
+          const float2 x = X[0];
+          v[n2] = c2(x.x + x.y, x.x - x.y);
+        } else {
+          const float2 a = X[k], b = cconj(X[M - k]);
+          const float2 s = cadd(a, b), d = csub(a, b);
+          const float2 t = cmul(cconj(__ldg(&twW[k])), d);
+          v[n2] = c2(s.x - t.y, s.y + t.x);
+        }
+      }
+    }
+  }
+
   // Inverse real transform of the packed half spectrum X (global row) into buf in natural
   // order: buf[m] = (x[2m], x[2m+1]) * (the unnormalized factor 2M; the column pass divides).
+  template <bool SPEC>
   __device__ __forceinline__ static void inverse_row_to_buf(const float2* __restrict__ X, float2* buf, int lane,
                                                             const float2* __restrict__ twW) {
     float2 v[L];
-#pragma unroll
-    for (int n2 = 0; n2 < L; ++n2) {
-      const int k = lane + 32 * n2;
-      if (k == 0) {
-        const float2 x = X[0];
-        v[n2] = c2(x.x + x.y, x.x - x.y);
-      } else {
-        // Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/(2M)} (X[k] - conj X[M-k])
-        const float2 a = X[k], b = cconj(X[M - k]);
-        const float2 s = cadd(a, b), d = csub(a, b);
-        const float2 t = cmul(cconj(__ldg(&twW[k])), d);
-        v[n2] = c2(s.x - t.y, s.y + t.x);
-      }
-    }
+    load_c2r<SPEC>(X, v, buf, lane, twW);
     float2 out[K2P][32];
     fft<true>(v, out, buf, lane, twW);
 #pragma unroll
@@ -100,24 +133,12 @@ struct WarpRow {
 
   // Inverse real transform of X straight to global memory through the epilogue (pair
   // index rowoff + m of the output image).
-  template <int EPI>
+  template <int EPI, bool SPEC>
   __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* out,
                                                                size_t rowoff, const Epilogue& epi, float2* buf,
                                                                int lane, const float2* __restrict__ twW) {
     float2 v[L];
-#pragma unroll
-    for (int n2 = 0; n2 < L; ++n2) {
-      const int k = lane + 32 * n2;
-      if (k == 0) {
-        const float2 x = X[0];
-        v[n2] = c2(x.x + x.y, x.x - x.y);
-      } else {
-        const float2 a = X[k], b = cconj(X[M - k]);
-        const float2 s = cadd(a, b), d = csub(a, b);
-        const float2 t = cmul(cconj(__ldg(&twW[k])), d);
-        v[n2] = c2(s.x - t.y, s.y + t.x);
-      }
-    }
+    load_c2r<SPEC>(X, v, buf, lane, twW);
     float2 res[K2P][32];
     fft<true>(v, res, buf, lane, twW);
 #pragma unroll
@@ -175,7 +196,7 @@ struct WarpRow {
 // STAGE (with SHARED): the f rows of the output rows are copied to shared memory
 // asynchronously at the start (behind the inverse transforms) instead of being loaded in
 // the stencil.
-template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN, int MINB>
+template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN, int MINB, bool SPEC>
 __global__ void __launch_bounds__((ROWS + 2) * 32, MINB)
 row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
                     const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
@@ -213,7 +234,7 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) buf[lane + 32 * n2] = src[lane + 32 * n2];
     } else {
-      WR::inverse_row_to_buf(spec_in + ch * plane + (size_t)yy * M, buf, lane, twW);
+      WR::template inverse_row_to_buf<SPEC>(spec_in + ch * plane + (size_t)yy * M, buf, lane, twW);
     }
   }
   __syncthreads();
@@ -325,7 +346,7 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
 }
 
 // Final inverse row pass: one warp per row, ROWS rows per CTA; EPI: the epilogue mode.
-template <int L, int ROWS, int EPI>
+template <int L, int ROWS, int EPI, bool SPEC>
 __global__ void __launch_bounds__(ROWS * 32)
 row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u,
                     Epilogue epi) {
@@ -340,7 +361,7 @@ row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restr
   const int y = (blockIdx.x - ch * strips) * ROWS + w;
   if (y >= H) return;  // warp-uniform; no CTA barrier below
   const size_t off = ch * (size_t)H * M + (size_t)y * M;
-  WR::template inverse_row_to_global<EPI>(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane,
+  WR::template inverse_row_to_global<EPI, SPEC>(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane,
                                           twW);
 }
 
@@ -355,7 +376,8 @@ struct WarpRowEntry {
 
 // STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
 // the register allocation must allow (2 at 256 threads = 128 registers per thread).
-template <int L, int RF, int RI, bool STAGE, bool SHARED, int MINB = ((RF + 2) * 32 <= 256 ? 2 : 1)>
+// SPEC: the inverse transforms stage their spectrum rows in shared memory (load_c2r).
+template <int L, int RF, int RI, bool STAGE, bool SHARED, int MINB = ((RF + 2) * 32 <= 256 ? 2 : 1), bool SPEC = false>
 constexpr WarpRowEntry warp_entry() {
   static_assert(SHARED || !STAGE, "f staging is part of the shared-mu stencil");
   return WarpRowEntry{32 * L,
@@ -363,14 +385,15 @@ constexpr WarpRowEntry warp_entry() {
                       RI,
                       WarpRow<L>::BUF,
                       STAGE ? RF * 32 * L : 0,
-                      {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0, MINB>,
-                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB>,
-                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 2, MINB>},
-                      {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB>,
-                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB>,
-                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB>},
-                      {row_warp_inv_kernel<L, RI, 0>, row_warp_inv_kernel<L, RI, 1>, row_warp_inv_kernel<L, RI, 2>,
-                       row_warp_inv_kernel<L, RI, 3>, row_warp_inv_kernel<L, RI, 4>}};
+                      {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0, MINB, SPEC>,
+                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB, SPEC>,
+                       row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 2, MINB, SPEC>},
+                      {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB, SPEC>,
+                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB, SPEC>,
+                       row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB, SPEC>},
+                      {row_warp_inv_kernel<L, RI, 0, SPEC>, row_warp_inv_kernel<L, RI, 1, SPEC>,
+                       row_warp_inv_kernel<L, RI, 2, SPEC>, row_warp_inv_kernel<L, RI, 3, SPEC>,
+                       row_warp_inv_kernel<L, RI, 4, SPEC>}};
 }
 
 // The first entry of a length is its default; the others are autotune alternatives.
@@ -378,13 +401,14 @@ const WarpRowEntry kWarpRows[] = {
     warp_entry<4, 14, 16, true, true>(),     // W = 256
     warp_entry<10, 14, 16, true, true>(),    // W = 640
     warp_entry<20, 6, 8, true, true>(),      // W = 1280
-    warp_entry<30, 6, 8, true, true>(),      // W = 1920
+    warp_entry<30, 6, 8, true, true, 2, true>(),  // W = 1920 (spectrum rows staged: 2 % faster at 1080p)
     warp_entry<32, 6, 8, false, true>(),     // W = 2048
     warp_entry<30, 14, 8, false, true>(),    // W = 1920, taller strips
     warp_entry<30, 6, 8, false, false>(),    // W = 1920, per-pair stencil
     warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
     warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
     warp_entry<30, 6, 8, false, false, 3>(), // W = 1920, per-pair stencil, 3 CTAs per SM (84 registers)
+    warp_entry<30, 6, 8, true, true>(),      // W = 1920, spectrum rows read straight from global memory
 };
 
 }  // namespace
