@@ -525,18 +525,21 @@ const RowEntry kRows[] = {
     row_entry<FixedPlan<640, 8, 8, 10>, 2, 4>(),
 };
 // Defaults are the fastest shapes measured by the batch autotuner on GB300 at
-// 640x480, 1280x720, 1920x1080, 2048x1536 and 3840x2160 RGB.
+// 640x480, 1280x720, 1920x1080, 2048x1536 and 3840x2160 RGB.  One default per length, whatever
+// the channel count, so that a channel's result does not depend on the other channels of
+// the call (at 1080 rows: 36 x 30 with 8 columns per CTA, 1920 x 1080 RGB 265 us per frame
+// against 270 for 12 x 10 x 9 and 272-276 for 4 columns per CTA; gray 178 against 173 / 176).
 const ColEntry kCols[] = {
     col_entry<FixedPlan<256, 16, 16>, 16>(),
     col_entry<FixedPlan<480, 8, 6, 10>, 4, 2>(),
     col_entry<FixedPlan<720, 8, 9, 10>, 4, 2>(),
-    col_entry<FixedPlan<1080, 36, 30>, 4, 3>(),
+    col_entry<FixedPlan<1080, 36, 30>, 8, 2>(),
     col_entry<FixedPlan<1536, 32, 48>, 4, 2>(),
     col_entry<FixedPlan<2160, 45, 48>, 4, 2>(),
     // alternatives for the autotuner
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
+    col_entry<FixedPlan<1080, 36, 30>, 4, 3>(),
     col_entry<FixedPlan<1080, 30, 36>, 8>(),
-    col_entry<FixedPlan<1080, 36, 30>, 8, 2>(),
     col_entry<FixedPlan<720, 24, 30>, 4, 3>(),
     col_entry<FixedPlan<480, 20, 24>, 4, 4>(),
     col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),

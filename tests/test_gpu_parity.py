@@ -233,20 +233,33 @@ def test_row_implementations_agree(ils, monkeypatch, H, W, C):
 
 
 @pytest.mark.parametrize("H,W", [(1080, 64), (720, 64), (480, 64), (1536, 32), (2160, 16)])
-def test_column_plan_variants_agree(ils, H, W):
-    # every compile-time column plan for H (the batch autotuner's candidates) against the oracle
-    import ctypes
+def test_column_plan_variants_agree(ils, monkeypatch, H, W):
+    # every compile-time column plan for H (each with its own stage-twiddle table; the batch
+    # autotuner's candidates), one and three channels, against the oracle
     import torch
-    from paper_2003_07504_gb300 import _lib
-    f = image(H, W, 1, seed=H + 7, preset="hd")
+    for C in (1, 3):
+        f = image(H, W, C, seed=H + 7 + C, preset="hd")
+        want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
+        for k in range(6):   # ILS_COL_IMPL=k beyond the plans of H selects the default
+            monkeypatch.setenv("ILS_COL_IMPL", str(k))
+            assert_parity(run_gpu(ils, f), want)
+        monkeypatch.delenv("ILS_COL_IMPL")
+        ft = torch.from_numpy(f).cuda()
+        frames = [(ft, torch.empty_like(ft), 1.0, 0.8, 1e-4, 4)]
+        with ils.Batch(frames, autotune=True) as b:   # exercises the timing of every candidate
+            b.run()
+            torch.cuda.synchronize()
+            assert_parity(frames[0][1].cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840)])
+def test_row_plan_variants_agree(ils, monkeypatch, H, W):
+    # every warp-per-row and fixed-plan row variant of the length against the oracle
+    f = image(H, W, 2, seed=W + H, preset="hd")
     want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
-    L = _lib.lib()
-    ft = torch.from_numpy(f).cuda()
-    frames = [(ft, torch.empty_like(ft), 1.0, 0.8, 1e-4, 4)]
-    with ils.Batch(frames, autotune=True) as b:   # exercises the timing of every candidate
-        b.run()
-        torch.cuda.synchronize()
-        assert_parity(frames[0][1].cpu().numpy(), want)
+    for impl in [f"warp{k}" for k in range(6)] + [f"fixed{k}" for k in range(3)]:
+        monkeypatch.setenv("ILS_ROW_IMPL", impl)
+        assert_parity(run_gpu(ils, f), want)
 
 
 # -------------------------------------------------------------- ILS with the Welsch penalty (Sec. 5)
