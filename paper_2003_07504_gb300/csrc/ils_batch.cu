@@ -353,7 +353,8 @@ ils_status ils_batch_create(const ils_frame* frames, int count, int flags, ils_b
       std::vector<float2> th = roots(f.H);
       th.resize(col_twiddle_count(f.H));  // stage tables, gathered on the device below
       if ((e = upload(&B->cls[ci].twW, row_twiddles(f.W))) || (e = upload(&B->cls[ci].twH, th)) ||
-          (e = build_col_twiddles(f.H, B->cls[ci].twH, 0)) || (e = cudaStreamSynchronize(0))) {
+          (e = build_col_twiddles(f.H, B->cls[ci].twH, 0)) || (e = build_row_twiddles(f.W, B->cls[ci].twW, 0)) ||
+          (e = cudaStreamSynchronize(0))) {
         s = fail(e, "class tables");
         break;
       }

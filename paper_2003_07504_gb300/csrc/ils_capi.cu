@@ -266,7 +266,7 @@ namespace ils {
 std::vector<float2> row_twiddles(int W) {
   const int M = W / 2;
   std::vector<float2> v = roots(W);
-  v.resize((size_t)W + M);
+  v.resize(row_twiddle_count(W), make_float2(0.0f, 0.0f));
   for (int t = 0; t < M; ++t) {
     const int k2 = t / 32, n1 = t % 32;
     v[(size_t)W + t] = v[(size_t)(2 * n1 * k2) % W];  // exp(-2 pi i n1 k2 / M)
@@ -339,7 +339,7 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
   ils_status s;
   if ((s = dev_alloc((void**)&pl->spec[0], plane * sizeof(float2))) ||
       (s = dev_alloc((void**)&pl->spec[1], plane * sizeof(float2))) ||
-      (s = dev_alloc((void**)&pl->tab.twW, (size_t)(W + M) * sizeof(float2))) ||
+      (s = dev_alloc((void**)&pl->tab.twW, row_twiddle_count(W) * sizeof(float2))) ||
       (s = dev_alloc((void**)&pl->tab.twH, col_twiddle_count(H) * sizeof(float2))) ||
       (s = dev_alloc((void**)&pl->tab.ax, (size_t)(M + 1) * sizeof(float))) ||
       (s = dev_alloc((void**)&pl->tab.by, (size_t)H * sizeof(float)))) {
@@ -363,7 +363,8 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
       (e = cudaMemcpy(pl->tab.twH, th.data(), th.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.ax, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.by, by.data(), by.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
-      (e = build_col_twiddles(H, pl->tab.twH, 0)) || (e = cudaStreamSynchronize(0))) {
+      (e = build_col_twiddles(H, pl->tab.twH, 0)) || (e = build_row_twiddles(W, pl->tab.twW, 0)) ||
+      (e = cudaStreamSynchronize(0))) {
     free_plan_memory(pl);
     delete pl;
     return cuda_fail(e, "tables");

@@ -136,16 +136,18 @@ struct Geometry {
 
 // Device tables for one (H, W, lambda, c).
 struct Tables {
-  // W + W/2 entries: exp(-2 pi i t / W) for t < W, then the four-step twiddles of the
-  // warp-per-row transforms, k2-major so that a warp's 32 lanes read 32 consecutive
-  // entries: twW[W + 32 k2 + n1] = exp(-2 pi i n1 k2 / (W/2))  (row_twiddles builds it)
+  // exp(-2 pi i t / W) for t < W, then the W/2 four-step twiddles of the warp-per-row
+  // transforms, k2-major so that a warp's 32 lanes read 32 consecutive entries:
+  // twW[W + 32 k2 + n1] = exp(-2 pi i n1 k2 / (W/2)) (row_twiddles), then stage tables
+  // (row_twiddle_count)
   float2* twW;
   float2* twH;   // exp(-2 pi i t / H) for t < H, then stage tables (col_twiddle_count)
   float* ax;     // M+1 entries: lambda c (1 - cos(2 pi k / W)),  k = 0..M
   float* by;     // H entries:   lambda c (1 - cos(2 pi l / H)),  l = 0..H-1
 };
 
-// The row twiddle table of Tables::twW for row length W (host, double precision, rounded once).
+// The first W + W/2 entries of Tables::twW for row length W (host, double precision, rounded
+// once), padded with zeros to row_twiddle_count(W) for build_row_twiddles.
 std::vector<float2> row_twiddles(int W);
 
 struct ImageDesc {
@@ -230,6 +232,11 @@ cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2
 // of the compile-time column plans of H, gathered from the roots by build_col_twiddles.
 size_t col_twiddle_count(int H);
 cudaError_t build_col_twiddles(int H, float2* twH, cudaStream_t st);
+// Tables::twW holds row_twiddle_count(W) entries: the W roots, the W/2 four-step entries
+// (row_twiddles), then the stage twiddle tables of the compile-time row plans of W/2,
+// gathered from the roots by build_row_twiddles.
+size_t row_twiddle_count(int W);
+cudaError_t build_row_twiddles(int W, float2* twW, cudaStream_t st);
 
 // Warp-per-row kernels (ils_rows_warp.cu).
 int warp_row_variants(int M, int* idx, int max);

@@ -215,7 +215,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
 // natural order (complex m holds pixels 2m, 2m+1).  All threads call it (syncs inside).
 template <class PL, int EPI = 0>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
-                                                      const float2* __restrict__ twW, float2* out, size_t rowoff,
+                                                      const float2* __restrict__ twr, float2* out, size_t rowoff,
                                                       const Epilogue* epi);
 
 // Inverse real row FFT of strip rows 0..nrows-1 (global spectrum rows X(i)) into smem rows
@@ -224,7 +224,7 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
 // the c2r un-packing of pairs (k, M-k) in place, then the FFT stages.  All threads call it.
 template <class PL, class RowPtr>
 __device__ __forceinline__ void rows_inverse_to_smem(float2* sm, int nrows, int i, int j, RowPtr X,
-                                                     const float2* __restrict__ twW) {
+                                                     const float2* __restrict__ twW, const float2* __restrict__ twr) {
   constexpr int M = PL::N;
   const int t = threadIdx.x, T = blockDim.x;
   __syncthreads();  // the previous user of the buffer is done
@@ -236,16 +236,18 @@ __device__ __forceinline__ void rows_inverse_to_smem(float2* sm, int nrows, int 
   __syncthreads();
   unpack_c2r_rows<M>(sm, nrows, twW);
   __syncthreads();
-  fft_rows_smem_inverse<PL>(sm, i, j, i < nrows, twW, nullptr, 0, nullptr);
+  fft_rows_smem_inverse<PL>(sm, i, j, i < nrows, twr, nullptr, 0, nullptr);
 }
 
 // The inverse FFT stages on smem row i (input natural order, output natural order, to
 // smem row i, or, when out is not null, to pixel pairs rowoff + m of the global output
-// image through the epilogue).
+// image through the epilogue).  twr: the plan's StageTw table (forward-stage parts: the
+// inverse runs the stages in the forward order and conjugates).
 template <class PL, int EPI>
 __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, bool live,
-                                                      const float2* __restrict__ twW, float2* out, size_t rowoff,
+                                                      const float2* __restrict__ twr, float2* out, size_t rowoff,
                                                       const Epilogue* epi) {
+  using TW = StageTw<PL>;
   constexpr int M = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = M / R0, NS1 = M / R1, NSL = M / RL;
   auto U = [&](int m) -> float2& { return sm[smem_idx(i * M + m)]; };
@@ -268,7 +270,7 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
     if (live && j < NS1) {
 #pragma unroll
       for (int r = 0; r < R1; ++r) v[r] = U(j + r * NS1);
-      bfly<M, R1, R0, true>(v, j, twW, 2);
+      bfly_tab<R1, R0, true>(v, j, twr + TW::FWD_MID);
     }
     __syncthreads();
     if (live && j < NS1) {
@@ -282,7 +284,7 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
     if (live && j < NSL) {
 #pragma unroll
       for (int r = 0; r < RL; ++r) v[r] = U(j + r * NSL);
-      bfly<M, RL, NSL, true>(v, j, twW, 2);
+      bfly_tab<RL, NSL, true>(v, j, twr + TW::FWD_LAST);
     }
     if (out != nullptr) {
       if (live && j < NSL) {
@@ -306,11 +308,12 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
 // threads row by row; the forward FFT of output row o runs on threads (o, j).
 template <class PL, int ROWS, bool FIRST, int PEN>
 __global__ void __launch_bounds__((ROWS + 2) * PL::TPS, 1)
-row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
-                     const float* __restrict__ u0, const float2* __restrict__ spec_in,
+row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ twr, MuParams mp,
+                     const float* __restrict__ f, const float* __restrict__ u0, const float2* __restrict__ spec_in,
                      float2* __restrict__ spec_out, float* __restrict__ u_ckpt) {
   griddep_launch();
   griddep_wait();
+  using TW = StageTw<PL>;  // twr: this plan's stage twiddle tables
   constexpr int M = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL, TPS = PL::TPS;
   constexpr int NS0 = M / R0, NS1 = M / R1, NSL = M / RL;
   constexpr int P = M / 2 + 1;
@@ -338,7 +341,7 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
     } else {
       const float2* base = spec_in + ch * plane;
       auto X = [&](int r) { return base + (size_t)wrap_row(y0 - 1 + r, H) * M; };
-      rows_inverse_to_smem<PL>(sm, nout + 2, i, j, X, twW);
+      rows_inverse_to_smem<PL>(sm, nout + 2, i, j, X, twW, twr);
     }
     // (b) r = f + lambda/2 (grad_x^T mu_x + grad_y^T mu_y), one output row at a time.  Row o
     // (strip row o+1) reads u rows o, o+1, o+2 and is then written into slot o, whose u row no
@@ -405,7 +408,7 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
       if (outlive && j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = U(i, j + r * NS1);
-        bfly<M, R1, R0, false>(v, j, twW, 2);
+        bfly_tab<R1, R0, false>(v, j, twr + TW::FWD_MID);
       }
       __syncthreads();
       if (outlive && j < NS1) {
@@ -419,7 +422,7 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
       if (outlive && j < NSL) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[r] = U(i, j + r * NSL);
-        bfly<M, RL, NSL, false>(v, j, twW, 2);
+        bfly_tab<RL, NSL, false>(v, j, twr + TW::FWD_LAST);
       }
       __syncthreads();
       if (outlive && j < NSL) {
@@ -448,8 +451,8 @@ row_fwd_fixed_kernel(int H, int C, const float2* __restrict__ twW, MuParams mp, 
 // Final inverse row pass: strips of ROWS rows, last stage written straight to u.
 template <class PL, int ROWS, int EPI>
 __global__ void __launch_bounds__(ROWS * PL::TPS, 1)
-row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ spec,
-                     float* __restrict__ u, Epilogue epi) {
+row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2* __restrict__ twr,
+                     const float2* __restrict__ spec, float* __restrict__ u, Epilogue epi) {
   griddep_launch();
   griddep_wait();
   constexpr int M = PL::N, TPS = PL::TPS;
@@ -471,21 +474,22 @@ row_inv_fixed_kernel(int H, int C, const float2* __restrict__ twW, const float2*
     unpack_c2r_rows<M>(sm, n, twW);
     __syncthreads();
     const size_t rowoff = ch * plane + (size_t)(y0 + (i < n ? i : 0)) * M;
-    fft_rows_smem_inverse<PL, EPI>(sm, i, j, i < n, twW, reinterpret_cast<float2*>(u), rowoff, &epi);
+    fft_rows_smem_inverse<PL, EPI>(sm, i, j, i < n, twr, reinterpret_cast<float2*>(u), rowoff, &epi);
   }
 }
 
 // ---------------------------------------------------------------- registry
 
-using RowFwdFn = void (*)(int, int, const float2*, MuParams, const float*, const float*, const float2*, float2*,
-                          float*);
-using RowInvFn = void (*)(int, int, const float2*, const float2*, float*, Epilogue);
+using RowFwdFn = void (*)(int, int, const float2*, const float2*, MuParams, const float*, const float*, const float2*,
+                          float2*, float*);
+using RowInvFn = void (*)(int, int, const float2*, const float2*, const float2*, float*, Epilogue);
 using ColFn = void (*)(int, int, const float2*, const float*, const float*, float, float2*);
 
 struct RowEntry {
   int M, tps, rows_fwd, rows_inv;
   RowFwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
   RowInvFn inv[kEpilogues];     // per epilogue mode
+  int R0, R1, R2, tw;           // radices (R2 = 1: two stages) and StageTw size
 };
 struct ColEntry {
   int H, tps, G;
@@ -505,7 +509,8 @@ constexpr RowEntry row_entry() {
                   {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>,
                    row_fwd_fixed_kernel<PL, RF, false, 2>},
                   {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>,
-                   row_inv_fixed_kernel<PL, RI, 3>, row_inv_fixed_kernel<PL, RI, 4>}};
+                   row_inv_fixed_kernel<PL, RI, 3>, row_inv_fixed_kernel<PL, RI, 4>},
+                  PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE};
 }
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
@@ -583,7 +588,24 @@ size_t col_twiddle_count(int H) {
   return n;
 }
 
+// Entries of a row table (Tables::twW) for row length W: the W roots, the M = W/2 four-step
+// entries of the warp-per-row kernels, then the StageTw tables of every compile-time row plan
+// of M in kRows order.
+size_t row_twiddle_count(int W) {
+  size_t n = (size_t)W + W / 2;
+  for (const RowEntry& r : kRows)
+    if (r.M == W / 2) n += r.tw;
+  return n;
+}
+
 namespace {
+size_t row_tw_offset(int idx) {
+  size_t off = (size_t)3 * kRows[idx].M;
+  for (int i = 0; i < idx; ++i)
+    if (kRows[i].M == kRows[idx].M) off += kRows[i].tw;
+  return off;
+}
+
 size_t col_tw_offset(int idx) {
   size_t off = kCols[idx].H;
   for (int i = 0; i < idx; ++i)
@@ -591,9 +613,10 @@ size_t col_tw_offset(int idx) {
   return off;
 }
 
-// One StageTw table gathered from the roots tw[0..N): stage (R, NS) entries
-// tab[(r - 1) NS + k] = tw[k (N / (NS R)) r].
-__global__ void stage_tw_kernel(int N, int R0, int R1, int R2, const float2* __restrict__ tw, float2* __restrict__ tab) {
+// One StageTw table gathered from the roots: stage (R, NS) entries
+// tab[(r - 1) NS + k] = tw[step k (N / (NS R)) r] (tw holds the (step N)-th roots of unity).
+__global__ void stage_tw_kernel(int N, int R0, int R1, int R2, int step, const float2* __restrict__ tw,
+                                float2* __restrict__ tab) {
   const bool mid = R2 > 1;
   const int RL = mid ? R2 : R1;
   // (NS, R) of the four stage tables in StageTw order; zero-size where absent
@@ -604,7 +627,7 @@ __global__ void stage_tw_kernel(int N, int R0, int R1, int R2, const float2* __r
     const int n = (rr[s] - 1) * ns[s];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       const int r = 1 + i / ns[s], k = i % ns[s];
-      tab[base + i] = tw[k * (N / (ns[s] * rr[s])) * r];
+      tab[base + i] = tw[step * k * (N / (ns[s] * rr[s])) * r];
     }
     base += n;
   }
@@ -615,7 +638,18 @@ cudaError_t build_col_twiddles(int H, float2* twH, cudaStream_t st) {
   for (int i = 0; i < (int)(sizeof(kCols) / sizeof(kCols[0])); ++i) {
     const ColEntry& c = kCols[i];
     if (c.H != H) continue;
-    stage_tw_kernel<<<(c.tw + 255) / 256, 256, 0, st>>>(c.H, c.R0, c.R1, c.R2, twH, twH + col_tw_offset(i));
+    stage_tw_kernel<<<(c.tw + 255) / 256, 256, 0, st>>>(c.H, c.R0, c.R1, c.R2, 1, twH, twH + col_tw_offset(i));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t build_row_twiddles(int W, float2* twW, cudaStream_t st) {
+  for (int i = 0; i < (int)(sizeof(kRows) / sizeof(kRows[0])); ++i) {
+    const RowEntry& r = kRows[i];
+    if (r.M != W / 2) continue;
+    stage_tw_kernel<<<(r.tw + 255) / 256, 256, 0, st>>>(r.M, r.R0, r.R1, r.R2, 2, twW, twW + row_tw_offset(i));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -651,7 +685,8 @@ cudaError_t fixed_row_forward(int idx, const ImageDesc& d, const Tables& t, cons
   const int tiles = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
   const int pen = mp.pen;
   RowFwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
-  return launch_k(d.pdl, fn, tiles, threads, smem, stream, d.H, d.C, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
+  return launch_k(d.pdl, fn, tiles, threads, smem, stream, d.H, d.C, t.twW, t.twW + row_tw_offset(idx), mp, f, u0,
+                  spec_in, spec_out, u_ckpt);
 }
 
 cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
@@ -660,7 +695,8 @@ cudaError_t fixed_row_inverse(int idx, const ImageDesc& d, const Tables& t, cons
   const int threads = r.rows_inv * r.tps;
   const size_t smem = row_smem(r.rows_inv, r.M);
   const int tiles = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
-  return launch_k(d.pdl, r.inv[epi.mode], tiles, threads, smem, stream, d.H, d.C, t.twW, spec, u, epi);
+  return launch_k(d.pdl, r.inv[epi.mode], tiles, threads, smem, stream, d.H, d.C, t.twW, t.twW + row_tw_offset(idx),
+                  spec, u, epi);
 }
 
 cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2* spec, cudaStream_t stream) {

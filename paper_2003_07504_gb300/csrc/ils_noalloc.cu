@@ -23,10 +23,12 @@ namespace {
 
 constexpr int kSideMax = ILS_NOALLOC_MAX_SIDE;
 constexpr size_t kElemsMax = ILS_NOALLOC_MAX_ELEMS;  // floats per image (C*H*W)
-// table floats: twW (3*side: W + W/2 complex) + twH (2*(side + kColTw): H roots and the column
-// plans' stage tables) + ax (side/2+1, padded) + by (side)
-constexpr size_t kColTw = 16384;  // complex; at least col_twiddle_count(H) - H for every H
-constexpr size_t kTableFloats = 3 * kSideMax + 2 * (kSideMax + kColTw) + (kSideMax / 2 + 64) + kSideMax;
+// table floats: twW (3*side + 2*kStageTw: W + W/2 complex and the row plans' stage tables) +
+// twH (2*(side + kStageTw): H roots and the column plans' stage tables) + ax (side/2+1,
+// padded) + by (side)
+constexpr size_t kStageTw = 16384;  // complex; at least the stage-table part of every length
+constexpr size_t kTwW = 3 * kSideMax + 2 * kStageTw;
+constexpr size_t kTableFloats = kTwW + 2 * (kSideMax + kStageTw) + (kSideMax / 2 + 64) + kSideMax;
 constexpr size_t kScratchFloats = 2 * kElemsMax + kTableFloats;
 
 // Shared by every call on a device and kept until the process exits.
@@ -127,10 +129,11 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
   float* tab = base + 2 * kElemsMax;
   Tables t;
   t.twW = reinterpret_cast<float2*>(tab);
-  t.twH = reinterpret_cast<float2*>(tab + 3 * kSideMax);
-  t.ax = tab + 5 * kSideMax + 2 * kColTw;
+  t.twH = reinterpret_cast<float2*>(tab + kTwW);
+  t.ax = tab + kTwW + 2 * (kSideMax + kStageTw);
   t.by = t.ax + (kSideMax / 2 + 64);
-  if (col_twiddle_count(H) > (size_t)kSideMax + kColTw) return ILS_ERR_UNSUPPORTED_SIZE;
+  if (col_twiddle_count(H) > (size_t)kSideMax + kStageTw || 2 * row_twiddle_count(W) > kTwW)
+    return ILS_ERR_UNSUPPORTED_SIZE;
 
   const double c = (double)p * std::pow((double)eps, (double)p / 2.0 - 1.0);
   MuParams mp;
@@ -142,7 +145,7 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
 
   noalloc_tables_kernel<<<(kSideMax + 255) / 256, 256, 0, st>>>(H, W, (double)lambda * c, t.twW, t.twH, t.ax, t.by);
   if ((e = cudaGetLastError())) return ILS_ERR_CUDA;
-  if ((e = build_col_twiddles(H, t.twH, st))) return ILS_ERR_CUDA;
+  if ((e = build_col_twiddles(H, t.twH, st)) || (e = build_row_twiddles(W, t.twW, st))) return ILS_ERR_CUDA;
   for (int it = 0; it < N; ++it) {
     float2* out = spec[it & 1];
     const float2* in = it == 0 ? nullptr : spec[(it - 1) & 1];
