@@ -541,6 +541,7 @@ const ColEntry kCols[] = {
     col_entry<FixedPlan<1080, 36, 30>, 8, 2>(),
     col_entry<FixedPlan<1536, 32, 48>, 4, 2>(),
     col_entry<FixedPlan<2160, 45, 48>, 4, 2>(),
+    col_entry<FixedPlan<512, 16, 32>, 4, 3>(),
     // alternatives for the autotuner
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
     col_entry<FixedPlan<1080, 36, 30>, 4, 3>(),
@@ -549,6 +550,7 @@ const ColEntry kCols[] = {
     col_entry<FixedPlan<480, 20, 24>, 4, 4>(),
     col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),
     col_entry<FixedPlan<2160, 12, 12, 15>, 4>(),
+    col_entry<FixedPlan<512, 8, 8, 8>, 4, 2>(),
 };
 
 }  // namespace

@@ -399,6 +399,7 @@ constexpr WarpRowEntry warp_entry() {
 // The first entry of a length is its default; the others are autotune alternatives.
 const WarpRowEntry kWarpRows[] = {
     warp_entry<4, 14, 16, true, true>(),     // W = 256
+    warp_entry<8, 14, 16, true, true>(),     // W = 512
     warp_entry<10, 14, 16, true, true>(),    // W = 640
     warp_entry<20, 6, 8, true, true>(),      // W = 1280
     warp_entry<30, 6, 8, true, true, 2, true>(),  // W = 1920 (spectrum rows staged: 2 % faster at 1080p)

@@ -59,7 +59,7 @@ def test_parity_256_gray_default_parameters(ils):
     (2, 2), (2, 4), (3, 2), (4, 6), (8, 8), (6, 10), (5, 12), (9, 16), (15, 20),
     (45, 64), (75, 30), (135, 96), (27, 250), (64, 640), (480, 64), (32, 1280),
     (720, 48), (1080, 40), (40, 1920), (36, 2048), (1536, 24), (2160, 16), (16, 3840),
-    (100, 96), (250, 180),
+    (100, 96), (250, 180), (512, 40), (24, 512), (256, 512),
 ])
 def test_parity_sizes(ils, H, W):
     f = image(H, W, 1, seed=H * 7919 + W, preset="small")
@@ -232,7 +232,7 @@ def test_row_implementations_agree(ils, monkeypatch, H, W, C):
         assert_parity(warp, O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4))
 
 
-@pytest.mark.parametrize("H,W", [(1080, 64), (720, 64), (480, 64), (1536, 32), (2160, 16)])
+@pytest.mark.parametrize("H,W", [(1080, 64), (720, 64), (480, 64), (1536, 32), (2160, 16), (512, 32)])
 def test_column_plan_variants_agree(ils, monkeypatch, H, W):
     # every compile-time column plan for H (each with its own stage-twiddle table; the batch
     # autotuner's candidates), one and three channels, against the oracle
@@ -252,7 +252,7 @@ def test_column_plan_variants_agree(ils, monkeypatch, H, W):
             assert_parity(frames[0][1].cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840)])
+@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512)])
 def test_row_plan_variants_agree(ils, monkeypatch, H, W):
     # every warp-per-row and fixed-plan row variant of the length against the oracle
     f = image(H, W, 2, seed=W + H, preset="hd")
