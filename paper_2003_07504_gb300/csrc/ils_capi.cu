@@ -15,6 +15,26 @@
 
 using namespace ils;
 
+// What a launch sequence of a plan depends on besides the plan itself.
+struct LaunchKey {
+  const float* f;
+  const float* u0;
+  float* u;
+  float* ckpt;
+  ils::Epilogue epi;
+  bool operator==(const LaunchKey& o) const {
+    return f == o.f && u0 == o.u0 && u == o.u && ckpt == o.ckpt && epi.mode == o.epi.mode && epi.s == o.epi.s &&
+           epi.a == o.epi.a && epi.o == o.epi.o && epi.f == o.epi.f && epi.rgb == o.epi.rgb && epi.dst == o.epi.dst &&
+           epi.C == o.epi.C && epi.c0 == o.epi.c0 && epi.plane2 == o.epi.plane2;
+  }
+};
+struct GraphEntry {
+  LaunchKey key;
+  cudaGraphExec_t exec;
+  unsigned long long last_use;
+};
+constexpr size_t kMaxGraphs = 4, kMaxSeen = 8;
+
 struct ils_plan {
   int H, W, C, N;
   float lambda, p, eps, c;
@@ -36,6 +56,12 @@ struct ils_plan {
   int nsplit;
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of side stream s
+  // CUDA graphs of this plan's launch sequence, keyed by the call's pointers and output
+  // stage (run_ils): a key seen twice is captured once and then replayed
+  std::vector<GraphEntry> graphs;
+  std::vector<LaunchKey> seen;
+  cudaStream_t cap_stream;
+  unsigned long long calls;
   // optional per-kernel event timing (ils_set_profiling)
   bool profiling;
   std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
@@ -101,6 +127,10 @@ void destroy_events(ils_plan* pl) {
 
 void free_plan_memory(ils_plan* pl) {
   destroy_events(pl);
+  for (GraphEntry& g : pl->graphs) cudaGraphExecDestroy(g.exec);
+  pl->graphs.clear();
+  if (pl->cap_stream != nullptr) cudaStreamDestroy(pl->cap_stream);
+  pl->cap_stream = nullptr;
   for (cudaStream_t x : pl->side) cudaStreamDestroy(x);
   for (cudaEvent_t x : pl->fork_join) cudaEventDestroy(x);
   pl->side.clear();
@@ -215,8 +245,80 @@ ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float
   return ILS_OK;
 }
 
+ils_status launch_all(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
+                      const Epilogue& epi);
+
+// Whether calls replay CUDA graphs of their launch sequence (ILS_GRAPHS=0 turns it off).
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("ILS_GRAPHS");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return on;
+}
+
+// Captures the launch sequence for `key` on the plan's capture stream; null on any failure
+// (the caller then launches directly).
+cudaGraphExec_t capture(ils_plan* pl, const LaunchKey& key) {
+  if (pl->cap_stream == nullptr && cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    pl->cap_stream = nullptr;
+    return nullptr;
+  }
+  if (cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  const ils_status s = launch_all(pl, key.f, key.u0, key.u, key.ckpt, pl->cap_stream, key.epi);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (s == ILS_OK && e == cudaSuccess && g != nullptr && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess)
+    exec = nullptr;
+  if (g != nullptr) cudaGraphDestroy(g);
+  cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+  return exec;
+}
+
+// Algorithm 1 for one call: replays the CUDA graph of this call's launch sequence when the
+// same pointers and output stage were seen before (a video pipeline's steady state: about
+// 1 us less per kernel boundary than stream launches), otherwise launches directly.  Not
+// while profiling, for N = 0, or when the caller's stream is itself being captured.
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
                    const Epilogue& epi = Epilogue()) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (pl->N == 0 || pl->profiling || !graphs_enabled() || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
+    return launch_all(pl, f, u0, u, ckpt, st, epi);
+  const LaunchKey key{f, u0, u, ckpt, epi};
+  ++pl->calls;
+  for (GraphEntry& g : pl->graphs) {
+    if (g.key == key) {
+      g.last_use = pl->calls;
+      const cudaError_t e = cudaGraphLaunch(g.exec, st);
+      return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaGraphLaunch");
+    }
+  }
+  bool seen = false;
+  for (const LaunchKey& k : pl->seen) seen = seen || k == key;
+  if (!seen) {
+    if (pl->seen.size() == kMaxSeen) pl->seen.erase(pl->seen.begin());
+    pl->seen.push_back(key);
+    return launch_all(pl, f, u0, u, ckpt, st, epi);
+  }
+  cudaGraphExec_t exec = capture(pl, key);
+  if (exec == nullptr) return launch_all(pl, f, u0, u, ckpt, st, epi);
+  if (pl->graphs.size() == kMaxGraphs) {  // evict the least recently used
+    size_t lru = 0;
+    for (size_t i = 1; i < pl->graphs.size(); ++i)
+      if (pl->graphs[i].last_use < pl->graphs[lru].last_use) lru = i;
+    cudaGraphExecDestroy(pl->graphs[lru].exec);
+    pl->graphs.erase(pl->graphs.begin() + lru);
+  }
+  pl->graphs.push_back(GraphEntry{key, exec, pl->calls});
+  const cudaError_t e = cudaGraphLaunch(exec, st);
+  return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+// The launches of one call (2N + 1 kernels, or a copy for N = 0) on `st`.
+ils_status launch_all(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
+                      const Epilogue& epi) {
   const size_t n = (size_t)pl->C * pl->H * pl->W;
   const size_t bytes = n * sizeof(float);
   cudaError_t e;

@@ -334,6 +334,36 @@ def test_luma_with_the_welsch_penalty(ils):
     assert_parity(out, want)
 
 
+# -------------------------------------------------------------- replayed launch graphs
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_graph_replay_matches_direct_launches(ils, C):
+    # the first call with a set of pointers launches directly, the second captures a graph,
+    # later ones replay it: same bits every time, the data read at replay time, other pointer
+    # sets and output stages kept apart
+    import torch
+    H, W = 96, 1920
+    f = torch.from_numpy(np.ascontiguousarray(image(H, W, C, seed=31 + C))).cuda()
+    g = torch.from_numpy(np.ascontiguousarray(image(H, W, C, seed=37 + C))).cuda()
+    with ils.Plan(H, W, C, 1.0, 0.8, 1e-4, 4) as plan:
+        u1, u2 = torch.empty_like(f), torch.empty_like(f)
+        first = plan.smooth(f, out=u1).clone()
+        for _ in range(4):
+            assert torch.equal(plan.smooth(f, out=u1), first)
+        other = plan.smooth(g, out=u2).clone()
+        for _ in range(3):
+            assert torch.equal(plan.smooth(g, out=u2), other)
+            assert torch.equal(plan.smooth(f, out=u1), first)
+        f2 = f.clone()
+        f.copy_(g)                     # same pointer, new data
+        assert torch.equal(plan.smooth(f, out=u1), other)
+        f.copy_(f2)
+        for k in (0.0, 3.0):           # output stages with the same pointers are different launches
+            e = [plan.enhance(f, k, out=u2).clone() for _ in range(3)]
+            assert torch.equal(e[0], e[1]) and torch.equal(e[1], e[2])
+    assert_parity(first.cpu().numpy(), O.ils_smooth(f.cpu().numpy().astype(np.float64), 1.0, 0.8, 1e-4, 4))
+
+
 # -------------------------------------------------------------- pixel-interleaved images (H x W x C)
 
 @pytest.mark.parametrize("H,W,C", [(256, 256, 3), (40, 1920, 3), (16, 3840, 2), (27, 250, 1), (60, 80, 4)])
