@@ -108,6 +108,15 @@ float ils_plan_c(const ils_plan* plan);
  * ils_smooth - Algorithm 1 with u^0 = f.
  *   f : device pointer, C x H x W float32 input (read only).
  *   u : device pointer, C x H x W float32 output; must not overlap f.
+ *
+ * Launch graphs (every smoothing call of a plan): the first call with a given set of
+ * pointers (and output-stage parameters) launches its kernels on the stream; the second
+ * captures that launch sequence into a CUDA graph on a plan-owned stream, and later calls
+ * with the same set replay the graph on the caller's stream - the same kernels, the same
+ * bits, the data read at replay time, less launch overhead.  A plan keeps the graphs of its
+ * 4 most recently used pointer sets.  Not while profiling (ils_set_profiling), for N = 0,
+ * or when `stream` is itself being captured (the kernels then join the caller's capture).
+ * The environment variable ILS_GRAPHS=0, read once per process, turns it off.
  */
 ils_status ils_smooth(ils_plan* plan, const float* f, float* u, void* stream);
 
