@@ -22,15 +22,18 @@ struct LaunchKey {
   float* u;
   float* ckpt;
   ils::Epilogue epi;
+  const float* f_host;  // host input copied to f, and u copied to u_host, per channel group
+  float* u_host;
   bool operator==(const LaunchKey& o) const {
-    return f == o.f && u0 == o.u0 && u == o.u && ckpt == o.ckpt && epi.mode == o.epi.mode && epi.s == o.epi.s &&
+    return f == o.f && u0 == o.u0 && u == o.u && ckpt == o.ckpt && f_host == o.f_host && u_host == o.u_host &&
+           epi.mode == o.epi.mode && epi.s == o.epi.s &&
            epi.a == o.epi.a && epi.o == o.epi.o && epi.f == o.epi.f && epi.rgb == o.epi.rgb && epi.dst == o.epi.dst &&
            epi.C == o.epi.C && epi.c0 == o.epi.c0 && epi.plane2 == o.epi.plane2;
   }
 };
 struct GraphEntry {
   LaunchKey key;
-  cudaGraphExec_t exec;
+  cudaGraphExec_t exec;  // null: the capture failed (e.g. pageable host memory); launch directly
   unsigned long long last_use;
 };
 constexpr size_t kMaxGraphs = 4, kMaxSeen = 8;
@@ -55,7 +58,8 @@ struct ils_plan {
   // stream, so that the small per-pass grids of a frame overlap each other's fill and drain
   int nsplit;
   std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of side stream s
+  // [0] fork, [1 + s] join of side stream s, [1 + nsplit + s] its host input copied
+  std::vector<cudaEvent_t> fork_join;
   // CUDA graphs of this plan's launch sequence, keyed by the call's pointers and output
   // stage (run_ils): a key seen twice is captured once and then replayed
   std::vector<GraphEntry> graphs;
@@ -245,8 +249,7 @@ ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float
   return ILS_OK;
 }
 
-ils_status launch_all(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
-                      const Epilogue& epi);
+ils_status launch_all(ils_plan* pl, const LaunchKey& k, cudaStream_t st);
 
 // Whether calls replay CUDA graphs of their launch sequence (ILS_GRAPHS=0 turns it off).
 bool graphs_enabled() {
@@ -265,7 +268,7 @@ cudaGraphExec_t capture(ils_plan* pl, const LaunchKey& key) {
     return nullptr;
   }
   if (cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
-  const ils_status s = launch_all(pl, key.f, key.u0, key.u, key.ckpt, pl->cap_stream, key.epi);
+  const ils_status s = launch_all(pl, key, pl->cap_stream);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
   cudaGraphExec_t exec = nullptr;
@@ -281,16 +284,17 @@ cudaGraphExec_t capture(ils_plan* pl, const LaunchKey& key) {
 // 1 us less per kernel boundary than stream launches), otherwise launches directly.  Not
 // while profiling, for N = 0, or when the caller's stream is itself being captured.
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
-                   const Epilogue& epi = Epilogue()) {
+                   const Epilogue& epi = Epilogue(), const float* f_host = nullptr, float* u_host = nullptr) {
+  const LaunchKey key{f, u0, u, ckpt, epi, f_host, u_host};
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (pl->N == 0 || pl->profiling || !graphs_enabled() || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
       cs != cudaStreamCaptureStatusNone)
-    return launch_all(pl, f, u0, u, ckpt, st, epi);
-  const LaunchKey key{f, u0, u, ckpt, epi};
+    return launch_all(pl, key, st);
   ++pl->calls;
   for (GraphEntry& g : pl->graphs) {
     if (g.key == key) {
       g.last_use = pl->calls;
+      if (g.exec == nullptr) return launch_all(pl, key, st);
       const cudaError_t e = cudaGraphLaunch(g.exec, st);
       return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaGraphLaunch");
     }
@@ -300,29 +304,49 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
   if (!seen) {
     if (pl->seen.size() == kMaxSeen) pl->seen.erase(pl->seen.begin());
     pl->seen.push_back(key);
-    return launch_all(pl, f, u0, u, ckpt, st, epi);
+    return launch_all(pl, key, st);
   }
   cudaGraphExec_t exec = capture(pl, key);
-  if (exec == nullptr) return launch_all(pl, f, u0, u, ckpt, st, epi);
   if (pl->graphs.size() == kMaxGraphs) {  // evict the least recently used
     size_t lru = 0;
     for (size_t i = 1; i < pl->graphs.size(); ++i)
       if (pl->graphs[i].last_use < pl->graphs[lru].last_use) lru = i;
-    cudaGraphExecDestroy(pl->graphs[lru].exec);
+    if (pl->graphs[lru].exec != nullptr) cudaGraphExecDestroy(pl->graphs[lru].exec);
     pl->graphs.erase(pl->graphs.begin() + lru);
   }
   pl->graphs.push_back(GraphEntry{key, exec, pl->calls});
+  if (exec == nullptr) return launch_all(pl, key, st);
   const cudaError_t e = cudaGraphLaunch(exec, st);
   return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
-// The launches of one call (2N + 1 kernels, or a copy for N = 0) on `st`.
-ils_status launch_all(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
-                      const Epilogue& epi) {
+// Host copies of channels [c0, c0 + cn) for a host-buffer call (k.f_host / k.u_host).
+cudaError_t host_in(ils_plan* pl, const LaunchKey& k, int c0, int cn, cudaStream_t st) {
+  if (k.f_host == nullptr) return cudaSuccess;
+  const size_t hw = (size_t)pl->H * pl->W;
+  return cudaMemcpyAsync(const_cast<float*>(k.f) + c0 * hw, k.f_host + c0 * hw, cn * hw * sizeof(float),
+                         cudaMemcpyHostToDevice, st);
+}
+cudaError_t host_out(ils_plan* pl, const LaunchKey& k, int c0, int cn, cudaStream_t st) {
+  if (k.u_host == nullptr) return cudaSuccess;
+  const size_t hw = (size_t)pl->H * pl->W;
+  return cudaMemcpyAsync(k.u_host + c0 * hw, k.u + c0 * hw, cn * hw * sizeof(float), cudaMemcpyDeviceToHost, st);
+}
+
+// The launches of one call on `st` (2N + 1 kernels, or a copy for N = 0).  For host buffers
+// each channel group's input copy, kernels and output copy run in order on its stream, so the
+// copies of one group overlap the kernels of the others.
+ils_status launch_all(ils_plan* pl, const LaunchKey& k, cudaStream_t st) {
+  const float* f = k.f;
+  const float* u0 = k.u0;
+  float* u = k.u;
+  float* ckpt = k.ckpt;
+  const Epilogue& epi = k.epi;
   const size_t n = (size_t)pl->C * pl->H * pl->W;
   const size_t bytes = n * sizeof(float);
   cudaError_t e;
   if (pl->N == 0) {
+    if ((e = host_in(pl, k, 0, pl->C, st))) return cuda_fail(e, "H2D copy");
     if (epi.mode == 3 || epi.mode == 4) {  // u = f through the output stage
       const size_t pairs = n / 2;
       if (epi.mode == 3) epilogue_only_kernel<3><<<grid_for(pairs), 256, 0, st>>>(epi, f, u, pairs);
@@ -330,25 +354,36 @@ ils_status launch_all(ils_plan* pl, const float* f, const float* u0, float* u, f
       e = cudaGetLastError();
       return e == cudaSuccess ? ILS_OK : cuda_fail(e, "output stage launch");
     }
-    e = cudaMemcpyAsync(u, u0 ? u0 : f, bytes, cudaMemcpyDeviceToDevice, st);
-    return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaMemcpyAsync");
+    if ((e = cudaMemcpyAsync(u, u0 ? u0 : f, bytes, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy");
+    e = host_out(pl, k, 0, pl->C, st);
+    return e == cudaSuccess ? ILS_OK : cuda_fail(e, "D2H copy");
   }
   ils_status s;
   if (!pl->profiling && pl->nsplit > 1) {
     if ((e = cudaEventRecord(pl->fork_join[0], st))) return cuda_fail(e, "event");
-    for (int k = 0; k < pl->nsplit; ++k) {
-      const int c0 = k * pl->C / pl->nsplit, c1 = (k + 1) * pl->C / pl->nsplit;
-      if ((e = cudaStreamWaitEvent(pl->side[k], pl->fork_join[0], 0))) return cuda_fail(e, "stream wait");
-      if ((s = enqueue_ils(pl, c0, c1 - c0, f, u0, u, ckpt, pl->side[k], epi, nullptr))) return s;
-      if ((e = cudaEventRecord(pl->fork_join[1 + k], pl->side[k])) ||
-          (e = cudaStreamWaitEvent(st, pl->fork_join[1 + k], 0)))
+    for (int g = 0; g < pl->nsplit; ++g) {
+      const int c0 = g * pl->C / pl->nsplit, c1 = (g + 1) * pl->C / pl->nsplit;
+      cudaStream_t sg = pl->side[g];
+      if ((e = cudaStreamWaitEvent(sg, pl->fork_join[0], 0))) return cuda_fail(e, "stream wait");
+      if (k.f_host != nullptr) {
+        // one input copy at a time, group by group, so that group 0 starts computing first
+        cudaEvent_t* h2d = &pl->fork_join[1 + pl->nsplit];
+        if ((g > 0 && (e = cudaStreamWaitEvent(sg, h2d[g - 1], 0))) || (e = host_in(pl, k, c0, c1 - c0, sg)) ||
+            (e = cudaEventRecord(h2d[g], sg)))
+          return cuda_fail(e, "H2D copy");
+      }
+      if ((s = enqueue_ils(pl, c0, c1 - c0, f, u0, u, ckpt, sg, epi, nullptr))) return s;
+      if ((e = host_out(pl, k, c0, c1 - c0, sg))) return cuda_fail(e, "D2H copy");
+      if ((e = cudaEventRecord(pl->fork_join[1 + g], sg)) || (e = cudaStreamWaitEvent(st, pl->fork_join[1 + g], 0)))
         return cuda_fail(e, "join");
     }
     return ILS_OK;
   }
   int slot = 0;
+  if ((e = host_in(pl, k, 0, pl->C, st))) return cuda_fail(e, "H2D copy");
   if ((s = enqueue_ils(pl, 0, pl->C, f, u0, u, ckpt, st, epi, pl->profiling ? &slot : nullptr))) return s;
   if ((e = mark(pl, slot, -1, st))) return cuda_fail(e, "event");
+  if ((e = host_out(pl, k, 0, pl->C, st))) return cuda_fail(e, "D2H copy");
   if (pl->profiling) {
     // accumulate this call's launch durations (waits for the call to finish)
     if ((e = cudaEventSynchronize(pl->ev[slot]))) return cuda_fail(e, "cudaEventSynchronize");
@@ -483,7 +518,7 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
     }
     pl->side.push_back(x);
   }
-  for (int k = 0; k < (pl->nsplit > 1 ? pl->nsplit + 1 : 0); ++k) {
+  for (int k = 0; k < (pl->nsplit > 1 ? 2 * pl->nsplit + 1 : 0); ++k) {
     cudaEvent_t x;
     if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming))) {
       free_plan_memory(pl);
@@ -798,9 +833,8 @@ ils_status ils_smooth_host(ils_plan* pl, const float* f_host, float* u_host, voi
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(pl->stage_f, f_host, bytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D copy");
-  if ((s = run_ils(pl, pl->stage_f, nullptr, pl->stage_u, nullptr, st))) return s;
-  if ((e = cudaMemcpyAsync(u_host, pl->stage_u, bytes, cudaMemcpyDeviceToHost, st))) return cuda_fail(e, "D2H copy");
+  // the copies run inside the launch sequence, per channel group (launch_all)
+  if ((s = run_ils(pl, pl->stage_f, nullptr, pl->stage_u, nullptr, st, Epilogue(), f_host, u_host))) return s;
   if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "cudaStreamSynchronize");
   return ILS_OK;
 }

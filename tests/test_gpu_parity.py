@@ -135,19 +135,31 @@ def test_mean_preserved_and_energy_decreases(ils):
 
 # -------------------------------------------------------------- host-buffer entry point
 
-def test_smooth_host_matches_device_call(ils):
+@pytest.mark.parametrize("C", [1, 3, 4])
+def test_smooth_host_matches_device_call(ils, C):
+    # the copies run per channel group inside the launch sequence (and inside its replayed
+    # graph from the second call with the same buffers on)
     import torch
-    f = image(96, 128, 3, seed=23)
-    dev = run_gpu(ils, f)
-    with ils.Plan(96, 128, 3) as plan:
-        fh = torch.from_numpy(f).pin_memory()
+    f = image(96, 128, C, seed=23 + C)
+    g = image(96, 128, C, seed=29 + C)
+    dev, dev_g = run_gpu(ils, f), run_gpu(ils, g)
+    with ils.Plan(96, 128, C) as plan:
+        fh = torch.from_numpy(f.copy()).pin_memory()
         uh = torch.empty_like(fh).pin_memory()
+        for _ in range(4):
+            uh.zero_()
+            plan.smooth_host(fh, uh)
+            np.testing.assert_array_equal(uh.numpy(), dev)
+        fh.copy_(torch.from_numpy(g))   # same buffers, new data
         plan.smooth_host(fh, uh)
-        np.testing.assert_array_equal(uh.numpy(), dev)
-        # pageable memory works as well
+        np.testing.assert_array_equal(uh.numpy(), dev_g)
+        # pageable memory works as well (its copies are not captured)
         uh2 = torch.empty(f.shape)
-        plan.smooth_host(torch.from_numpy(f), uh2)
-        np.testing.assert_array_equal(uh2.numpy(), dev)
+        fp = torch.from_numpy(f.copy())
+        for _ in range(3):
+            uh2.zero_()
+            plan.smooth_host(fp, uh2)
+            np.testing.assert_array_equal(uh2.numpy(), dev)
 
 
 # -------------------------------------------------------------- the headline workload at full size
