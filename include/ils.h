@@ -190,7 +190,11 @@ ils_status ils_smooth_from(ils_plan* plan, const float* f, const float* u0, floa
  * Algorithm 1, copies u back and synchronizes `stream` before returning.
  *   f_host, u_host : host pointers to C x H x W float32 (page-locked memory
  *                    gives full copy bandwidth; pageable memory also works).
- * Uses device staging buffers owned by the plan (allocated on first use).
+ * Uses device staging buffers owned by the plan (allocated on first use).  With 2-8
+ * channels the copies are pipelined per channel group: the groups' input copies run one
+ * after another, and each group's kernels and output copy follow its own input copy on its
+ * internal stream, so copies overlap the other groups' kernels.  With page-locked buffers
+ * the copies are part of the replayed launch graph (see ils_smooth).
  */
 ils_status ils_smooth_host(ils_plan* plan, const float* f_host, float* u_host, void* stream);
 
