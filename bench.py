@@ -142,6 +142,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, ws: int, device) -> float:
+    """The largest `value` over the ranks (the slowest replica sets a weak-scaling run's time);
+    `device` is the tensor device of the process group's backend (cuda for nccl, cpu for gloo)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_fps(total_ms_max: float, steps: int, ws: int, channels: int) -> float:
+    """Whole-job frames per second of `ws` replicas that each ran `steps` steps of a
+    `channels`-channel image (frames counted in C-channel frames), timed by the slowest rank."""
+    frames = steps * ws * (channels / C)
+    return frames / (total_ms_max / 1000.0)
+
+
 def make_frame(c=None, h=None, w=None):
     from paper_2003_07504_gb300 import synth
     return synth.preset_image(h or H, w or W, c or C, "hd", SEED)
@@ -572,12 +591,9 @@ def run_ours(args):
     total_ms = sum(step_ms)
     pct = np.percentile(step_ms, [10, 50, 90]) if step_ms else [0.0, 0.0, 0.0]
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     frames = args.steps * ws * (ch / C)   # frames of C channels
-    fps = frames / (total_ms / 1000.0)
+    fps = replica_fps(total_ms, args.steps, ws, ch)
 
     # end to end through the host-buffer entry point: pinned input, H2D + kernels + D2H per step
     e2e_fps = None
@@ -593,10 +609,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             plan.smooth_host(fh, uh)
             e2e_times.append(time.perf_counter() - t0)
-        e2e_total = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(e2e_total, op=dist.ReduceOp.MAX)
-        e2e_fps = frames / float(e2e_total.item())
+        e2e_fps = frames / max_over_ranks(sum(e2e_times), ws, dev)
 
     if rank == 0:
         per_kind, frame_bytes = bytes_model(hh, ww, ch, N_ITERS)
