@@ -114,7 +114,9 @@ float ils_plan_c(const ils_plan* plan);
  * captures that launch sequence into a CUDA graph on a plan-owned stream, and later calls
  * with the same set replay the graph on the caller's stream - the same kernels, the same
  * bits, the data read at replay time, less launch overhead.  A plan keeps the graphs of its
- * 4 most recently used pointer sets.  Not while profiling (ils_set_profiling), for N = 0,
+ * 8 most recently used pointer sets; once it has captured 4 graphs it captures more only
+ * while they are replayed at least 4 times per capture (callers that rarely repeat a
+ * pointer set keep direct launches).  Not while profiling (ils_set_profiling), for N = 0,
  * or when `stream` is itself being captured (the kernels then join the caller's capture).
  * The environment variable ILS_GRAPHS=0, read once per process, turns it off.
  */

@@ -36,7 +36,7 @@ struct GraphEntry {
   cudaGraphExec_t exec;  // null: the capture failed (e.g. pageable host memory); launch directly
   unsigned long long last_use;
 };
-constexpr size_t kMaxGraphs = 4, kMaxSeen = 8;
+constexpr size_t kMaxGraphs = 8, kMaxSeen = 16;
 
 struct ils_plan {
   int H, W, C, N;
@@ -65,7 +65,7 @@ struct ils_plan {
   std::vector<GraphEntry> graphs;
   std::vector<LaunchKey> seen;
   cudaStream_t cap_stream;
-  unsigned long long calls;
+  unsigned long long calls, captures, replays;
   // optional per-kernel event timing (ils_set_profiling)
   bool profiling;
   std::vector<cudaEvent_t> ev;  // one event before each launch plus one after the last
@@ -295,10 +295,15 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
     if (g.key == key) {
       g.last_use = pl->calls;
       if (g.exec == nullptr) return launch_all(pl, key, st);
+      ++pl->replays;
       const cudaError_t e = cudaGraphLaunch(g.exec, st);
       return e == cudaSuccess ? ILS_OK : cuda_fail(e, "cudaGraphLaunch");
     }
   }
+  // a caller whose pointer sets rarely repeat (more sets in rotation than graphs kept) would
+  // pay a capture per call: after 4 captures, capture again only if graphs are replayed
+  // at least 4 times per capture
+  if (pl->captures >= 4 && pl->replays < 4 * pl->captures) return launch_all(pl, key, st);
   bool seen = false;
   for (const LaunchKey& k : pl->seen) seen = seen || k == key;
   if (!seen) {
@@ -307,6 +312,7 @@ ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, floa
     return launch_all(pl, key, st);
   }
   cudaGraphExec_t exec = capture(pl, key);
+  ++pl->captures;
   if (pl->graphs.size() == kMaxGraphs) {  // evict the least recently used
     size_t lru = 0;
     for (size_t i = 1; i < pl->graphs.size(); ++i)

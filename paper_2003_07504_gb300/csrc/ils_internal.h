@@ -244,6 +244,9 @@ cudaError_t warp_set_attributes();
 cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
                              const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
                              cudaStream_t stream);
+cudaError_t warp_row_adjoint(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp,
+                             const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
+                             bool last, float2* spec_out, cudaStream_t stream);
 cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,
                              cudaStream_t stream, const Epilogue& epi);
 

@@ -540,8 +540,10 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
 cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tables& t, const MuParams& mp,
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream) {
-  dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   if (mp.pen == 2) return cudaErrorInvalidValue;  // no adjoint for half-quadratic splitting
+  if (g.warp_row >= 0)
+    return warp_row_adjoint(g.warp_row, d, t, mp, spec_in, u_n, fbar, fbar_first, gu0, last, spec_out, stream);
+  dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   auto fn = mp.pen == 1 ? (g.ept_row == 16 ? row_adjoint_kernel<16, 1> : row_adjoint_kernel<32, 1>)
                       : (g.ept_row == 16 ? row_adjoint_kernel<16, 0> : row_adjoint_kernel<32, 0>);
   return launch_k(d.pdl, fn, grid, g.threads_row, g.smem_fwd, stream, d.H, d.W, g.rows_fwd, d.planM, t.twW, mp, spec_in,

@@ -365,13 +365,102 @@ row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restr
                                           twW);
 }
 
+// Reverse-mode row pass of step n (the adjoint of Algorithm 1's iteration; see the generic
+// row_adjoint_kernel for the derivation): warp w inverse-transforms strip row w of r = A^-1
+// gbar (rows y0-1 .. y0+ROWS), then output warp o = w-1 forms, per pixel pair,
+//   fbar += r,  gbar' = lambda/2 sum_* grad_*^T [ g''(grad_* u^n) * grad_* r ]
+// (g'' of Appendix B; u^n read from global memory), and forward-transforms gbar' for the
+// next step's column pass unless this is the last step (then gbar' goes to gu0 or fbar).
+template <int PEN>
+__device__ __forceinline__ float g2_pen(float x, const MuParams& mp) {
+  const float x2 = x * x;
+  if constexpr (PEN == 1) {
+    return fmaf(-2.0f * sfu_exp2(-mp.wbeta * x2), fmaf(-2.0f * mp.winv2g2, x2, 1.0f), mp.c);
+  } else {
+    const float w = sfu_exp2((mp.a - 1.0f) * sfu_log2(x2 + mp.eps));
+    return fmaf(-mp.p * w, fmaf(mp.p - 1.0f, x2, mp.eps), mp.c);
+  }
+}
+
+template <int L, int ROWS, int PEN, int MINB>
+__global__ void __launch_bounds__((ROWS + 2) * 32, MINB)
+row_warp_adj_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float2* __restrict__ spec_in,
+                    const float* __restrict__ u_n, float* __restrict__ fbar, int fbar_first, float* __restrict__ gu0,
+                    int last, float2* __restrict__ spec_out) {
+  griddep_launch();
+  griddep_wait();
+  using WR = WarpRow<L>;
+  constexpr int M = WR::M;
+  extern __shared__ float2 sm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int strips = (H + ROWS - 1) / ROWS;
+  const int ch = blockIdx.x / strips;
+  const int y0 = (blockIdx.x - ch * strips) * ROWS;
+  const int nout = min(ROWS, H - y0);
+  const size_t plane = (size_t)H * M;
+  float2* buf = sm + w * WR::BUF;
+  if (w < nout + 2)
+    WR::template inverse_row_to_buf<false>(spec_in + ch * plane + (size_t)wrap_row(y0 - 1 + w, H) * M, buf, lane,
+                                           twW);
+  __syncthreads();
+  const int o = w - 1;
+  const bool out_live = o >= 0 && o < nout;
+  float2 v[L];
+  if (out_live) {
+    const int y = y0 + o;
+    const float2* uc = reinterpret_cast<const float2*>(u_n) + ch * plane;
+    const float2* urow = uc + (size_t)y * M;
+    const float2* uup = uc + (size_t)wrap_row(y - 1, H) * M;
+    const float2* udn = uc + (size_t)wrap_row(y + 1, H) * M;
+    const float2* rup = sm + (w - 1) * WR::BUF;
+    const float2* rdn = sm + (w + 1) * WR::BUF;
+    float2* fb = reinterpret_cast<float2*>(fbar) + ch * plane + (size_t)y * M;
+    float2* g0 = gu0 != nullptr ? reinterpret_cast<float2*>(gu0) + ch * plane + (size_t)y * M : nullptr;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = lane + 32 * n2;
+      const int ml = m == 0 ? M - 1 : m - 1, mr = m == M - 1 ? 0 : m + 1;
+      const float2 rc = buf[m];
+      const float rl = buf[ml].y, rrt = buf[mr].x;
+      const float2 ru = rup[m], rd = rdn[m];
+      const float2 u0c = urow[m];
+      const float ul = urow[ml].y, ur = urow[mr].x;
+      const float2 uu = uup[m], ud = udn[m];
+      const float qx_l = g2_pen<PEN>(u0c.x - ul, mp) * (rc.x - rl);
+      const float qx_c = g2_pen<PEN>(u0c.y - u0c.x, mp) * (rc.y - rc.x);
+      const float qx_r = g2_pen<PEN>(ur - u0c.y, mp) * (rrt - rc.y);
+      const float qy0u = g2_pen<PEN>(u0c.x - uu.x, mp) * (rc.x - ru.x);
+      const float qy0d = g2_pen<PEN>(ud.x - u0c.x, mp) * (rd.x - rc.x);
+      const float qy1u = g2_pen<PEN>(u0c.y - uu.y, mp) * (rc.y - ru.y);
+      const float qy1d = g2_pen<PEN>(ud.y - u0c.y, mp) * (rd.y - rc.y);
+      const float2 gb = c2(mp.half_lambda * ((qx_l - qx_c) + (qy0u - qy0d)),
+                           mp.half_lambda * ((qx_c - qx_r) + (qy1u - qy1d)));
+      float2 acc = fbar_first ? c2(0.0f, 0.0f) : fb[m];
+      acc.x += rc.x;
+      acc.y += rc.y;
+      if (last && g0 == nullptr) {
+        acc.x += gb.x;
+        acc.y += gb.y;
+      }
+      fb[m] = acc;
+      if (last && g0 != nullptr) g0[m] = gb;
+      v[n2] = gb;
+    }
+  }
+  if (last) return;  // kernel-uniform
+  __syncthreads();   // every warp has read the r rows; buffer w becomes warp w's scratch
+  if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+}
+
 using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
+using AdjFn = void (*)(int, const float2*, MuParams, const float2*, const float*, float*, int, float*, int, float2*);
 using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
   FwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
   InvFn inv[kEpilogues];     // per epilogue mode
+  AdjFn adj[2];              // per penalty with an adjoint (Eq. 7, Welsch)
 };
 
 // STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
@@ -393,7 +482,8 @@ constexpr WarpRowEntry warp_entry() {
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB, SPEC>},
                       {row_warp_inv_kernel<L, RI, 0, SPEC>, row_warp_inv_kernel<L, RI, 1, SPEC>,
                        row_warp_inv_kernel<L, RI, 2, SPEC>, row_warp_inv_kernel<L, RI, 3, SPEC>,
-                       row_warp_inv_kernel<L, RI, 4, SPEC>}};
+                       row_warp_inv_kernel<L, RI, 4, SPEC>},
+                      {row_warp_adj_kernel<L, RF, 0, MINB>, row_warp_adj_kernel<L, RF, 1, MINB>}};
 }
 
 // The first entry of a length is its default; the others are autotune alternatives.
@@ -432,6 +522,9 @@ cudaError_t warp_set_attributes() {
     }
     for (int m = 0; m < kEpilogues; ++m)
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
+    const int sa = (r.rows_fwd + 2) * r.buf * (int)sizeof(float2);
+    for (int pen = 0; pen < 2; ++pen)
+      if ((e = cudaFuncSetAttribute(r.adj[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sa))) return e;
   }
   return cudaSuccess;
 }
@@ -445,6 +538,17 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
   const int pen = mp.pen;
   FwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
+}
+
+cudaError_t warp_row_adjoint(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp,
+                             const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
+                             bool last, float2* spec_out, cudaStream_t stream) {
+  const WarpRowEntry& r = kWarpRows[idx];
+  if (mp.pen != 0 && mp.pen != 1) return cudaErrorInvalidValue;
+  const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
+  const size_t smem = (size_t)(r.rows_fwd + 2) * r.buf * sizeof(float2);
+  return launch_k(d.pdl, r.adj[mp.pen], blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, spec_in, u_n,
+                  fbar, (int)fbar_first, gu0, (int)last, spec_out);
 }
 
 cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const float2* spec, float* u,

@@ -50,6 +50,9 @@ def gpu_grad(ils, f, w, lam=1.0, p=0.8, N=4, u0=None, separate=False):
 @pytest.mark.parametrize("H,W,C,lam,p,N", [
     (32, 40, 1, 1.0, 0.8, 4), (45, 64, 2, 2.0, 1.0, 3), (64, 64, 1, 0.5, 0.5, 2), (30, 48, 3, 1.0, 0.8, 1),
     (256, 256, 1, 1.0, 0.8, 4), (75, 30, 1, 3.5, 0.8, 4),
+    # warp-per-row adjoint kernels: L = 8, 10, 20, 30, 32 (ragged last strip: H not a multiple of 6)
+    (20, 512, 1, 1.0, 0.8, 3), (15, 640, 2, 1.0, 0.8, 2), (16, 1280, 1, 2.0, 0.8, 2), (25, 1920, 1, 1.0, 0.8, 2),
+    (9, 2048, 1, 1.0, 1.0, 2),
 ])
 def test_adjoint_matches_fp64_reverse_mode(ils, H, W, C, lam, p, N):
     f = synth.preset_image(H, W, C, "small", H + W + C)
@@ -133,7 +136,8 @@ def test_adjoint_batch_of_512_images_against_fp64_samples(ils):
     np.testing.assert_array_equal(gpu_grad(ils, f[5:6].copy(), w[5:6].copy()), g[5:6])
 
 
-@pytest.mark.parametrize("H,W,lam,gamma,N", [(32, 40, 20.0, 10 / 255, 3), (48, 64, 5.0, 0.1, 4)])
+@pytest.mark.parametrize("H,W,lam,gamma,N", [(32, 40, 20.0, 10 / 255, 3), (48, 64, 5.0, 0.1, 4),
+                                             (20, 512, 20.0, 10 / 255, 3), (12, 1920, 5.0, 0.1, 2)])
 def test_welsch_adjoint_matches_fp64_reverse_mode(ils, H, W, lam, gamma, N):
     # Welsch g'' (Appendix B) in the adjoint row kernel; c = 2, so FP32 cancellation is mild
     import torch
