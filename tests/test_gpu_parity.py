@@ -376,6 +376,28 @@ def test_graph_replay_matches_direct_launches(ils, C):
     assert_parity(first.cpu().numpy(), O.ils_smooth(f.cpu().numpy().astype(np.float64), 1.0, 0.8, 1e-4, 4))
 
 
+def test_calls_inside_a_caller_stream_capture(ils):
+    # a caller capturing its own CUDA graph gets the plan's kernels in that graph (the plan's
+    # graph cache stays out of the way), channel streams included
+    import torch
+    H, W, C = 64, 1920, 3
+    f = torch.from_numpy(np.ascontiguousarray(image(H, W, C, seed=41))).cuda()
+    with ils.Plan(H, W, C, 1.0, 0.8, 1e-4, 4) as plan:
+        want = plan.smooth(f).clone()
+        u = torch.zeros_like(f)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            plan.smooth(f, out=u)      # warm up on the capture stream
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.smooth(f, out=u)
+        u.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(u, want)
+
+
 # -------------------------------------------------------------- pixel-interleaved images (H x W x C)
 
 @pytest.mark.parametrize("H,W,C", [(256, 256, 3), (40, 1920, 3), (16, 3840, 2), (27, 250, 1), (60, 80, 4)])
