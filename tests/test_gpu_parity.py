@@ -135,15 +135,15 @@ def test_mean_preserved_and_energy_decreases(ils):
 
 # -------------------------------------------------------------- host-buffer entry point
 
-@pytest.mark.parametrize("C", [1, 3, 4])
-def test_smooth_host_matches_device_call(ils, C):
+@pytest.mark.parametrize("C,H,W", [(1, 96, 128), (3, 96, 128), (4, 96, 128), (3, 30, 1920), (1, 24, 3840)])
+def test_smooth_host_matches_device_call(ils, C, H, W):
     # the copies run per channel group inside the launch sequence (and inside its replayed
-    # graph from the second call with the same buffers on)
+    # graph from the second call with the same page-locked buffers on)
     import torch
-    f = image(96, 128, C, seed=23 + C)
-    g = image(96, 128, C, seed=29 + C)
+    f = image(H, W, C, seed=23 + C)
+    g = image(H, W, C, seed=29 + C)
     dev, dev_g = run_gpu(ils, f), run_gpu(ils, g)
-    with ils.Plan(96, 128, C) as plan:
+    with ils.Plan(H, W, C) as plan:
         fh = torch.from_numpy(f.copy()).pin_memory()
         uh = torch.empty_like(fh).pin_memory()
         for _ in range(4):
