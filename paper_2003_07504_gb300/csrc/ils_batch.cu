@@ -24,6 +24,10 @@
 
 using namespace ils;
 
+namespace ils {
+std::vector<float2> unit_roots(int L);  // exp(-2 pi i t / L), t < L (ils_capi.cu)
+}
+
 namespace {
 
 struct BatchClass {
@@ -50,15 +54,6 @@ bool smooth_235(int n) {
   for (int r : {2, 3, 5})
     while (n % r == 0) n /= r;
   return n == 1;
-}
-
-std::vector<float2> roots(int L) {
-  std::vector<float2> v(L);
-  for (int t = 0; t < L; ++t) {
-    const double a = -2.0 * M_PI * (double)t / (double)L;
-    v[t] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  return v;
 }
 
 template <typename T>
@@ -350,7 +345,7 @@ ils_status ils_batch_create(const ils_frame* frames, int count, int flags, ils_b
       }
       B->cls.push_back(c);
       ci = (int)B->cls.size() - 1;
-      std::vector<float2> th = roots(f.H);
+      std::vector<float2> th = unit_roots(f.H);
       th.resize(col_twiddle_count(f.H));  // stage tables, gathered on the device below
       if ((e = upload(&B->cls[ci].twW, row_twiddles(f.W))) || (e = upload(&B->cls[ci].twH, th)) ||
           (e = build_col_twiddles(f.H, B->cls[ci].twH, 0)) || (e = build_row_twiddles(f.W, B->cls[ci].twW, 0)) ||

@@ -151,16 +151,6 @@ void free_plan_memory(ils_plan* pl) {
   cudaFree(pl->tab.by);
 }
 
-// exp(-2 pi i t / L) for t = 0..L-1, double precision, reduced argument.
-std::vector<float2> roots(int L) {
-  std::vector<float2> v(L);
-  for (int t = 0; t < L; ++t) {
-    const double a = -2.0 * M_PI * (double)t / (double)L;
-    v[t] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  return v;
-}
-
 // With profiling on, records an event before launch number `slot` of this call.
 cudaError_t mark(ils_plan* pl, int slot, int kind, cudaStream_t st) {
   if (!pl->profiling) return cudaSuccess;
@@ -406,9 +396,19 @@ ils_status launch_all(ils_plan* pl, const LaunchKey& k, cudaStream_t st) {
 }  // namespace
 
 namespace ils {
+// exp(-2 pi i t / L) for t = 0..L-1 (double precision, rounded once).
+std::vector<float2> unit_roots(int L) {
+  std::vector<float2> v(L);
+  for (int t = 0; t < L; ++t) {
+    const double a = -2.0 * M_PI * (double)t / (double)L;
+    v[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return v;
+}
+
 std::vector<float2> row_twiddles(int W) {
   const int M = W / 2;
-  std::vector<float2> v = roots(W);
+  std::vector<float2> v = unit_roots(W);
   v.resize(row_twiddle_count(W), make_float2(0.0f, 0.0f));
   for (int t = 0; t < M; ++t) {
     const int k2 = t / 32, n1 = t % 32;
@@ -501,7 +501,7 @@ ils_status create_plan(int H, int W, int C, float lambda, int N, MuParams mp, do
     const double s1 = std::sin(M_PI * (double)l / (double)H);
     by[l] = (float)(2.0 * (double)lambda * c * s1 * s1);
   }
-  std::vector<float2> tw = row_twiddles(W), th = roots(H);
+  std::vector<float2> tw = row_twiddles(W), th = unit_roots(H);
   if ((e = cudaMemcpy(pl->tab.twW, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.twH, th.data(), th.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(pl->tab.ax, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
