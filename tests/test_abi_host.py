@@ -61,3 +61,38 @@ def test_null_arguments(L):
     assert L.ils_smooth_host(None, None, None, None) == 1
     assert L.ils_plan_destroy(None) == 0
     assert L.ils_plan_c(None) == -1.0
+
+
+def test_header_is_plain_c_and_links(L, tmp_path):
+    # a C99 program includes the header, links libils.so and calls entry points that must
+    # answer without a GPU: status strings and argument validation
+    import os
+    import shutil
+    import subprocess
+    from paper_2003_07504_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib_dir = os.path.dirname(_lib.LIB_PATH)
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "ils.h"
+int main(void) {
+  ils_plan* plan = NULL;
+  if (strcmp(ils_status_string(ILS_OK), "ILS_OK") != 0) return 1;
+  if (ils_plan_create(16, 16, 1, -1.0f, 0.8f, 1e-4f, 4, &plan) != ILS_ERR_INVALID_ARG || plan != NULL) return 2;
+  if (ils_plan_create(14, 16, 1, 1.0f, 0.8f, 1e-4f, 4, &plan) != ILS_ERR_UNSUPPORTED_SIZE) return 3;
+  if (ils_smooth(NULL, NULL, NULL, NULL) != ILS_ERR_INVALID_ARG) return 4;
+  if (ils_plan_destroy(NULL) != ILS_OK) return 5;
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"), str(src),
+                    "-o", str(exe), "-L", lib_dir, "-lils", f"-Wl,-rpath,{lib_dir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
