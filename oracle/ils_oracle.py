@@ -53,6 +53,7 @@ __all__ = [
     "ils_channel_welsch", "ils_smooth_welsch", "energy_welsch", "ils_backward_welsch",
     "LUMA_BT601", "luma", "detail_enhance", "ils_smooth_luma",
     "LUMA_FLOOR", "log_luma", "tonemap_log", "hwc_to_planar", "planar_to_hwc", "ils_smooth_hwc",
+    "gaussian_weights", "gaussian_blur_periodic", "texture_smooth",
     "hqs_shrink_l1", "hqs_channel", "hqs_smooth",
 ]
 
@@ -468,6 +469,43 @@ def ils_smooth_hwc(f_hwc, lam=1.0, p=0.8, eps=1e-4, N=4):
     """ILS of a pixel-interleaved image: the channels are independent (Sec. 3.4, option II),
     so it is ILS of each channel plane, stored back interleaved."""
     return planar_to_hwc(ils_smooth(hwc_to_planar(f_hwc), lam, p, eps, N))
+
+
+def gaussian_weights(sigma):
+    """Taps w_k, k = -r..r, of the truncated, normalized Gaussian: r = ceil(3 sigma),
+    w_k = exp(-k^2 / (2 sigma^2)) / sum_j exp(-j^2 / (2 sigma^2)); sigma = 0 gives [1].
+    Reading: the paper pre-smooths with 'a Gaussian filter of a small variation' (Sec. 5)
+    and states neither the truncation nor the boundary."""
+    if sigma <= 0:
+        return np.ones(1)
+    r = int(np.ceil(3.0 * sigma))
+    k = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def gaussian_blur_periodic(f, sigma):
+    """Separable Gaussian blur of each H x W channel with periodic wrap (the boundary model of
+    Eq. 9's solve): rows, then columns, each a sum of shifted copies."""
+    f = np.asarray(f, dtype=np.float64)
+    w = gaussian_weights(sigma)
+    r = (len(w) - 1) // 2
+    tmp = np.zeros_like(f)
+    for i, k in enumerate(range(-r, r + 1)):
+        tmp += w[i] * np.roll(f, -k, axis=-1)      # out[x] += w_k f[x + k]
+    out = np.zeros_like(f)
+    for i, k in enumerate(range(-r, r + 1)):
+        out += w[i] * np.roll(tmp, -k, axis=-2)
+    return out
+
+
+def texture_smooth(f, sigma=1.0, lam=30.0, gamma=10.0 / 255.0, N=15):
+    """Texture smoothing of Sec. 5: the input is pre-smoothed by a small Gaussian (so that
+    the Welsch penalty, which barely penalizes large gradients, also flattens high-contrast
+    texture), then smoothed by Welsch-penalty ILS with the paper's lambda = 30, gamma = 10/255,
+    N = 15.  Reading: sigma = 1 pixel by default (the paper gives no value)."""
+    g = gaussian_blur_periodic(f, sigma)
+    return ils_smooth_welsch(g, lam, gamma, N)
 
 
 # ----------------------------------------------------------------------------

@@ -577,6 +577,56 @@ def test_tonemap_exposure_equivariance():
     np.testing.assert_allclose(bb, g ** s_ * a, rtol=1e-9)
 
 
+# ---------------------------------------------------------------- Gaussian pre-smoothing (Sec. 5, texture smoothing)
+
+def test_gaussian_weights_shape():
+    w = O.gaussian_weights(1.0)
+    assert len(w) == 7 and abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(w, w[::-1], atol=0)
+    assert w[3] == w.max() and w[2] / w[3] == pytest.approx(np.exp(-0.5), rel=1e-14)
+    np.testing.assert_array_equal(O.gaussian_weights(0.0), [1.0])
+
+
+def test_gaussian_blur_impulse_response_and_mean():
+    # the response to a unit impulse is the outer product of the taps (brute force), wrapped
+    H, W, s = 9, 11, 1.3
+    f = np.zeros((H, W))
+    f[2, 9] = 1.0
+    g = O.gaussian_blur_periodic(f, s)
+    w = O.gaussian_weights(s)
+    r = (len(w) - 1) // 2
+    want = np.zeros((H, W))
+    for a in range(-r, r + 1):
+        for b in range(-r, r + 1):
+            want[(2 + a) % H, (9 + b) % W] += w[a + r] * w[b + r]
+    np.testing.assert_allclose(g, want, atol=1e-15)
+    x = small_image(12, 10, seed=61)
+    assert abs(O.gaussian_blur_periodic(x, 0.8).mean() - x.mean()) < 1e-14
+    np.testing.assert_allclose(O.gaussian_blur_periodic(np.full((5, 6), 0.3), 2.0), 0.3, atol=1e-15)
+    np.testing.assert_allclose(O.gaussian_blur_periodic(x, 0.0), x, atol=0)
+
+
+def test_gaussian_blur_is_a_periodic_convolution():
+    # equal to the product of DFTs with the wrapped kernel (numpy.fft as a library comparator)
+    H, W, s = 16, 20, 1.7
+    x = small_image(H, W, seed=67)
+    w = O.gaussian_weights(s)
+    r = (len(w) - 1) // 2
+    k = np.zeros((H, W))
+    for a in range(-r, r + 1):
+        for b in range(-r, r + 1):
+            k[(-a) % H, (-b) % W] += w[a + r] * w[b + r]   # correlation taps as a kernel
+    want = np.real(np.fft.ifft2(np.fft.fft2(x) * np.fft.fft2(k)))
+    np.testing.assert_allclose(O.gaussian_blur_periodic(x, s), want, atol=1e-12)
+
+
+def test_texture_smooth_is_welsch_ils_of_the_blurred_input():
+    x = small_image(12, 14, seed=71)
+    g = O.gaussian_blur_periodic(x, 1.0)
+    np.testing.assert_allclose(O.texture_smooth(x, 1.0, 30.0, 10 / 255, 3),
+                               O.ils_channel_welsch(g, 30.0, 10 / 255, 3), atol=1e-14)
+
+
 # ---------------------------------------------------------------- interleaved (H x W x C) images
 
 def test_hwc_layout_by_explicit_indexing():
