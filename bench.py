@@ -291,6 +291,11 @@ def welsch_leg(ils, torch, dev, steps, flush):
         _, frame_bytes = bytes_model(H, W, C, n)
         out[name] = {"lambda": lam, "gamma": gamma, "N": n, "ms": ms, "fps": 1000.0 / ms,
                      "frac_of_hbm_peak": frame_bytes / (ms / 1000.0) / 1e9 / peak}
+    # texture smoothing as the paper runs it: Gaussian pre-smoothing (sigma = 1 px) + Welsch ILS
+    with ils.Plan(H, W, C, 30.0, N=15, penalty="welsch", gamma=10 / 255) as plan:
+        ms = _timed(lambda: plan.smooth_presmoothed(f, 1.0, out=u), torch, steps, flush)
+    out["texture_presmoothed"] = {"lambda": 30.0, "gamma": 10 / 255, "N": 15, "sigma": 1.0, "ms": ms,
+                                  "fps": 1000.0 / ms}
     out["workload"] = "Welsch-penalty ILS, 1920x1080 RGB FP32"
     return out
 

@@ -181,6 +181,25 @@ ils_status ils_log_luma(const float* rgb, float* l, int H, int W, void* stream);
 ils_status ils_tonemap_log(ils_plan* plan, const float* rgb, float* out, float s, float k, float o, void* stream);
 
 /*
+ * ils_gaussian_blur - separable Gaussian blur with periodic wrap: taps w_k, k = -r..r,
+ * r = ceil(3 sigma), w_k proportional to exp(-k^2 / (2 sigma^2)) and summing to 1
+ * (sigma = 0: a copy).  The pre-smoothing of Sec. 5's texture smoothing.
+ *   f, out : device pointers, C x H x W float32, non-overlapping.  0 <= sigma <= 5,
+ *            C <= 65535; otherwise ILS_ERR_INVALID_ARG.
+ */
+ils_status ils_gaussian_blur(const float* f, float* out, int H, int W, int C, float sigma, void* stream);
+
+/*
+ * ils_smooth_presmoothed - texture smoothing of Sec. 5: Algorithm 1 on the Gaussian
+ * pre-smoothed input (ils_gaussian_blur of f with `sigma`, into a plan-owned buffer; the
+ * paper uses a Welsch plan with lambda = 30, gamma = 10/255, N = 15 and a small sigma).
+ *   f, u : device pointers, C x H x W float32, non-overlapping.  0 <= sigma <= 5.
+ * The first call allocates a C x H x W float32 buffer that the plan keeps (shared with
+ * ils_smooth_host's input staging; make it before any stream capture).
+ */
+ils_status ils_smooth_presmoothed(ils_plan* plan, const float* f, float* u, float sigma, void* stream);
+
+/*
  * ils_smooth_from - Algorithm 1 started from a given u^0 instead of f (warm start).
  *   u0 : device pointer, C x H x W float32 (read only); may equal f.
  *   u  : device pointer output; must overlap neither f nor u0.

@@ -53,6 +53,8 @@ SIGNATURES = {
     "ils_smooth_enhance": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
     "ils_smooth_luma": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
     "ils_smooth_hwc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_gaussian_blur": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, c_void_p]),
+    "ils_smooth_presmoothed": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
     "ils_log_luma": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "ils_tonemap_log": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, c_float, c_void_p]),
     "ils_smooth_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -15,6 +15,10 @@
 
 using namespace ils;
 
+namespace ils {
+cudaError_t launch_gaussian_blur(const float* f, float* out, int H, int W, int C, float sigma, cudaStream_t st);
+}
+
 // What a launch sequence of a plan depends on besides the plan itself.
 struct LaunchKey {
   const float* f;
@@ -825,6 +829,28 @@ ils_status ils_tonemap_log(ils_plan* pl, const float* rgb, float* out, float s, 
   epi.rgb = rgb;
   epi.plane2 = n / 2;
   return run_ils(pl, pl->luma, nullptr, out, nullptr, st, epi);
+}
+
+ils_status ils_gaussian_blur(const float* f, float* out, int H, int W, int C, float sigma, void* stream) {
+  if (f == nullptr || out == nullptr || H < 1 || W < 1 || C < 1 || C > 65535 || !(sigma >= 0.0f) || sigma > 5.0f)
+    return ILS_ERR_INVALID_ARG;
+  if (overlaps(f, out, (size_t)C * H * W * sizeof(float))) return ILS_ERR_INVALID_ARG;
+  const cudaError_t e = launch_gaussian_blur(f, out, H, W, C, sigma, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ILS_OK : cuda_fail(e, "Gaussian blur launch");
+}
+
+ils_status ils_smooth_presmoothed(ils_plan* pl, const float* f, float* u, float sigma, void* stream) {
+  if (pl == nullptr || f == nullptr || u == nullptr || !(sigma >= 0.0f) || sigma > 5.0f) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  if (overlaps(f, u, bytes)) return ILS_ERR_INVALID_ARG;
+  if (pl->stage_f == nullptr) {
+    const ils_status s = dev_alloc((void**)&pl->stage_f, bytes);
+    if (s != ILS_OK) return s;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = launch_gaussian_blur(f, pl->stage_f, pl->H, pl->W, pl->C, sigma, st);
+  if (e != cudaSuccess) return cuda_fail(e, "Gaussian blur launch");
+  return run_ils(pl, pl->stage_f, nullptr, u, nullptr, st);
 }
 
 ils_status ils_smooth_host(ils_plan* pl, const float* f_host, float* u_host, void* stream) {

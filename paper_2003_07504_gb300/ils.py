@@ -138,6 +138,18 @@ class Plan:
                    "ils_smooth_hwc")
         return out
 
+    def smooth_presmoothed(self, f: torch.Tensor, sigma: float = 1.0, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+        """Texture smoothing (Sec. 5): ILS of the input pre-smoothed by a periodic Gaussian of
+        standard deviation sigma (<= 5 pixels); the paper pairs it with a Welsch plan, N = 15."""
+        _check_image(self._as3d(f), self.shape, "f")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_image(self._as3d(out), self.shape, "out")
+        _lib.check(_lib.lib().ils_smooth_presmoothed(self._h, f.data_ptr(), out.data_ptr(), float(sigma),
+                                                     _stream_ptr(stream)), "ils_smooth_presmoothed")
+        return out
+
     def tonemap(self, rgb: torch.Tensor, s: float, k: float = 1.0, o: float = 0.0,
                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Single-scale HDR tone mapping of a 3 x H x W linear-radiance image (plan made with C = 1):
@@ -325,4 +337,18 @@ def log_luma(rgb: torch.Tensor, out: torch.Tensor | None = None, stream=None) ->
         out = torch.empty((H, W), dtype=torch.float32, device=rgb.device)
     _check_image(out, (H, W), "out")
     _lib.check(_lib.lib().ils_log_luma(rgb.data_ptr(), out.data_ptr(), H, W, _stream_ptr(stream)), "ils_log_luma")
+    return out
+
+
+def gaussian_blur(f: torch.Tensor, sigma: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Separable periodic Gaussian blur (taps r = ceil(3 sigma), normalized) of a (C, H, W) or
+    (H, W) float32 CUDA tensor; 0 <= sigma <= 5."""
+    shape = tuple(f.shape)
+    C, H, W = (1, *shape) if len(shape) == 2 else shape
+    _check_image(f, shape, "f")
+    if out is None:
+        out = torch.empty_like(f)
+    _check_image(out, shape, "out")
+    _lib.check(_lib.lib().ils_gaussian_blur(f.data_ptr(), out.data_ptr(), H, W, C, float(sigma), _stream_ptr(stream)),
+               "ils_gaussian_blur")
     return out

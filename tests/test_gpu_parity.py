@@ -398,6 +398,32 @@ def test_calls_inside_a_caller_stream_capture(ils):
         assert torch.equal(u, want)
 
 
+# -------------------------------------------------------------- Gaussian pre-smoothing, texture smoothing (Sec. 5)
+
+@pytest.mark.parametrize("C,H,W,sigma", [(3, 64, 96, 1.0), (1, 7, 5, 2.5), (2, 33, 70, 0.5), (1, 40, 1920, 5.0),
+                                         (1, 16, 16, 0.0), (3, 1080, 48, 1.3)])
+def test_gaussian_blur_matches_oracle(ils, C, H, W, sigma):
+    import torch
+    f = image(H, W, C, seed=H + W + C)
+    got = ils.gaussian_blur(torch.from_numpy(np.ascontiguousarray(f)).cuda(), sigma).cpu().numpy()
+    want = O.gaussian_blur_periodic(f.astype(np.float64), sigma)
+    assert np.abs(got - want).max() <= 2e-6   # FP32 sums of at most 31 x 31 normalized taps of [0,1] values
+
+
+@pytest.mark.parametrize("H,W,C,N", [(48, 64, 3, 15), (30, 1920, 1, 6)])
+def test_texture_smoothing_matches_oracle(ils, H, W, C, N):
+    import torch
+    f = image(H, W, C, seed=5 * H + W)
+    lam, gamma, sigma = 30.0, 10 / 255, 1.0
+    with ils.Plan(H, W, C, lam, N=N, penalty="welsch", gamma=gamma) as plan:
+        ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+        u = plan.smooth_presmoothed(ft, sigma).cpu().numpy()
+        # the same as blurring, then smoothing
+        u2 = plan.smooth(ils.gaussian_blur(ft, sigma)).cpu().numpy()
+        np.testing.assert_array_equal(u, u2)
+    assert_parity(u, O.texture_smooth(f.astype(np.float64), sigma, lam, gamma, N))
+
+
 # -------------------------------------------------------------- pixel-interleaved images (H x W x C)
 
 @pytest.mark.parametrize("H,W,C", [(256, 256, 3), (40, 1920, 3), (16, 3840, 2), (27, 250, 1), (60, 80, 4)])
