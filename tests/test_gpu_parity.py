@@ -188,6 +188,25 @@ def test_uhd_properties(ils):
     assert np.abs(run_gpu(ils, c) - c).max() < 2e-6
 
 
+def test_maximum_side_properties(ils):
+    # 8192 x 8192 (the largest side a plan accepts; generic kernels): beyond the naive-DFT
+    # oracle, so properties that hold at any size: transpose equivariance (periodic, isotropic
+    # operator), the mean kept, lambda = 0 returning f
+    import torch
+    n = 8192
+    f = torch.from_numpy(image(1024, 1024, 1, seed=8192, preset="hd")).cuda().repeat(1, 8, 8).contiguous()
+    f += 1e-3 * torch.rand_like(f)   # break the 8 x 8 periodicity
+    with ils.Plan(n, n, 1, 1.0, 0.8, 1e-4, 4) as plan:
+        u = plan.smooth(f)
+        ut = plan.smooth(f[0].t().contiguous().unsqueeze(0))
+        torch.cuda.synchronize()
+        assert float((u[0].t() - ut[0]).abs().max()) < 2e-5
+        assert abs(float(u.double().mean()) - float(f.double().mean())) < 1e-6
+        assert float((u - f).abs().max()) > 1e-3
+    with ils.Plan(n, n, 1, 0.0, 0.8, 1e-4, 2) as plan0:
+        assert float((plan0.smooth(f) - f).abs().max()) < 2e-6
+
+
 # -------------------------------------------------------------- errors
 
 def test_invalid_calls_raise(ils):
