@@ -52,9 +52,9 @@ def bytes_model(H, W, C, N):
     return per, total
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when there is
-    none or the kernel's sources changed since the counters were taken."""
+def load_capture(kernel: str):
+    """The committed ncu counters of `kernel` (profiles/row_pass_traffic.json), or None when there
+    are none or the kernel's sources changed since they were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "row_pass_traffic.json")
     try:
@@ -66,9 +66,31 @@ def load_traffic(kernel: str):
             with open(os.path.join(ROOT, src), "rb") as fh:
                 if hashlib.sha256(fh.read()).hexdigest() != digest:
                     return None
-        return d["traffic_bytes_per_launch"] / 1e9
+        return d
     except (OSError, ValueError, KeyError):
         return None
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes (GB) per launch of `kernel` from the committed ncu capture, or None."""
+    d = load_capture(kernel)
+    return None if d is None else d["traffic_bytes_per_launch"] / 1e9
+
+
+SMSP_PER_GPU = 152 * 4   # SM sub-partitions: one warp-instruction issue per cycle each
+
+
+def issue_roof(kernel: str, launch_ms: float, sm_mhz):
+    """The launch's warp-instructions (committed ncu count) against the GPU's issue rate at the
+    sampled SM clock: the fraction of issue slots the kernel used, the roof its latency-bound
+    instruction stream sits under."""
+    d = load_capture(kernel)
+    if d is None or "warp_instructions_per_launch" not in d or not sm_mhz or launch_ms <= 0:
+        return None
+    n = float(d["warp_instructions_per_launch"])
+    peak = SMSP_PER_GPU * float(sm_mhz) * 1e6   # warp-instructions per second
+    return {"warp_instructions_per_launch": n, "peak_warp_instr_per_s": peak,
+            "min_launch_us": n / peak * 1e6, "frac": n / (launch_ms / 1000.0) / peak}
 
 
 def load_peaks():
@@ -644,6 +666,7 @@ def run_ours(args):
                        "mpix_per_s": fps * hh * ww / 1e6},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind, "traffic": load_traffic(dom),
+                         "issue": issue_roof(dom, dom_ms / dom_n, clocks.get("sm_mhz")),
                          "traffic_unit": "GB per launch (ncu dram read + write)",
                          "launch_timing": "events around every launch, second loop of the same K steps",
                          "algorithmic_bytes_per_launch": per_kind[dom],
