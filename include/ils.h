@@ -311,6 +311,12 @@ ils_status ils_cnn_destroy(ils_cnn* net);                        /* NULL accepte
 ils_status ils_cnn_set_weights(ils_cnn* net, const float* params, long long count);  /* also resets Adam */
 ils_status ils_cnn_get_weights(const ils_cnn* net, float* params, long long count);
 ils_status ils_cnn_get_grads(const ils_cnn* net, float* grads, long long count);
+/* Adam state for training checkpoints: first and second moments in parameter order (host
+ * arrays of ils_cnn_param_count() values) and the step count of the bias correction.
+ * Restore with ils_cnn_set_adam after ils_cnn_set_weights (which resets the state);
+ * step in [0, 2e9]. */
+ils_status ils_cnn_get_adam(const ils_cnn* net, float* m, float* v, long long count, long long* step);
+ils_status ils_cnn_set_adam(ils_cnn* net, const float* m, const float* v, long long count, long long step);
 
 /* u0 = f + net(f) (f, u0 device, non-overlapping).  Keeps the activations for backward. */
 ils_status ils_cnn_forward(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);

@@ -73,6 +73,8 @@ SIGNATURES = {
     "ils_cnn_destroy": (c_int, [c_void_p]),
     "ils_cnn_set_weights": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
     "ils_cnn_get_weights": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "ils_cnn_get_adam": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, P(ctypes.c_longlong)]),
+    "ils_cnn_set_adam": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, ctypes.c_longlong]),
     "ils_cnn_get_grads": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
     "ils_cnn_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "ils_cnn_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),

@@ -609,6 +609,59 @@ ils_status ils_cnn_get_weights(const ils_cnn* n, float* params, long long count)
   return ILS_OK;
 }
 
+// Adam state (first and second moments, in parameter order, and the step count): the
+// checkpoint of a training run, restored after ils_cnn_set_weights (which resets it).
+ils_status ils_cnn_get_adam(const ils_cnn* n, float* m, float* v, long long count, long long* step) {
+  if (n == nullptr || m == nullptr || v == nullptr || step == nullptr || count != (long long)param_count())
+    return ILS_ERR_INVALID_ARG;
+  cudaError_t e;
+  if ((e = cudaDeviceSynchronize())) return cnn_fail(e, "get_adam");
+  for (int which = 0; which < 2; ++which) {
+    float* dst = which == 0 ? m : v;
+    size_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      const int co_n = kCout[l], ci_n = kCin[l], K = kpad(l);
+      std::vector<float> w((size_t)co_n * K);
+      if ((e = cudaMemcpy(w.data(), which == 0 ? n->mw[l] : n->vw[l], w.size() * 4, cudaMemcpyDeviceToHost)))
+        return cnn_fail(e, "get_adam");
+      for (int co = 0; co < co_n; ++co)
+        for (int ci = 0; ci < ci_n; ++ci)
+          for (int tap = 0; tap < 9; ++tap) dst[off + ((size_t)co * ci_n + ci) * 9 + tap] = w[(size_t)co * K + tap * ci_n + ci];
+      off += (size_t)co_n * ci_n * 9;
+      if ((e = cudaMemcpy(dst + off, which == 0 ? n->mb[l] : n->vb[l], (size_t)co_n * 4, cudaMemcpyDeviceToHost)))
+        return cnn_fail(e, "get_adam");
+      off += co_n;
+    }
+  }
+  *step = n->step;
+  return ILS_OK;
+}
+
+ils_status ils_cnn_set_adam(ils_cnn* n, const float* m, const float* v, long long count, long long step) {
+  if (n == nullptr || m == nullptr || v == nullptr || count != (long long)param_count() || step < 0 ||
+      step > 2000000000LL)
+    return ILS_ERR_INVALID_ARG;
+  cudaError_t e;
+  for (int which = 0; which < 2; ++which) {
+    const float* src = which == 0 ? m : v;
+    size_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      const int co_n = kCout[l], ci_n = kCin[l], K = kpad(l);
+      std::vector<float> w((size_t)co_n * K, 0.0f);   // padding columns stay zero
+      for (int co = 0; co < co_n; ++co)
+        for (int ci = 0; ci < ci_n; ++ci)
+          for (int tap = 0; tap < 9; ++tap) w[(size_t)co * K + tap * ci_n + ci] = src[off + ((size_t)co * ci_n + ci) * 9 + tap];
+      off += (size_t)co_n * ci_n * 9;
+      if ((e = cudaMemcpy(which == 0 ? n->mw[l] : n->vw[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice)) ||
+          (e = cudaMemcpy(which == 0 ? n->mb[l] : n->vb[l], src + off, (size_t)co_n * 4, cudaMemcpyHostToDevice)))
+        return cnn_fail(e, "set_adam");
+      off += co_n;
+    }
+  }
+  n->step = (int)step;
+  return ILS_OK;
+}
+
 // gradients in the same order as the parameters
 ils_status ils_cnn_get_grads(const ils_cnn* n, float* grads, long long count) {
   if (n == nullptr || grads == nullptr || count != (long long)param_count()) return ILS_ERR_INVALID_ARG;

@@ -88,6 +88,22 @@ class WarmStartNet:
         _lib.check(_lib.lib().ils_cnn_get_grads(self._h, g.ctypes.data, g.size), "ils_cnn_get_grads")
         return g
 
+    def get_adam(self):
+        """(m, v, step): Adam moments in parameter order and the bias-correction step count."""
+        m = np.empty(param_count(), np.float32)
+        v = np.empty(param_count(), np.float32)
+        step = ctypes.c_longlong(0)
+        _lib.check(_lib.lib().ils_cnn_get_adam(self._h, m.ctypes.data, v.ctypes.data, m.size, ctypes.byref(step)),
+                   "ils_cnn_get_adam")
+        return m, v, int(step.value)
+
+    def set_adam(self, m: np.ndarray, v: np.ndarray, step: int) -> None:
+        """Restore Adam state (after set_params, which resets it)."""
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        _lib.check(_lib.lib().ils_cnn_set_adam(self._h, m.ctypes.data, v.ctypes.data, m.size, int(step)),
+                   "ils_cnn_set_adam")
+
     @staticmethod
     def _shape(f):
         if f.dim() != 4 or f.shape[1] != 3 or f.dtype != torch.float32 or not f.is_cuda or not f.is_contiguous():
@@ -178,10 +194,23 @@ def crop_pool(n_images: int, size: int, seed: int) -> np.ndarray:
                                            seed=seed + i) for i in range(n_images)])
 
 
+def save_checkpoint(path: str, net: "WarmStartNet", step: int, losses, best) -> None:
+    """Training state after `step` steps: weights, Adam moments and step count, the loss log
+    and the best snapshot (npz; the data order and learning-rate schedule follow from step)."""
+    m, v, t = net.get_adam()
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, params=net.get_params(), adam_m=m, adam_v=v, adam_t=t, step=step,
+             losses=np.asarray(losses, dtype=np.float64).reshape(-1, 2),
+             best_loss=np.inf if best is None else best[0],
+             best_params=net.get_params() if best is None else best[1])
+    os.replace(tmp, path)
+
+
 def train(steps: int = 600, batch: int = 16, crop: int = 256, lr: float = 1e-3, lam: float = 1.0, p: float = 0.8,
           eps: float = 1e-4, N: int = 4, n_crops: int = 20000, seed: int = 0, log_every: int = 50,
           params: np.ndarray | None = None, pool_images: int = 24, pool_size: int = 1024, verbose: bool = True,
-          warmup: int = 200):
+          warmup: int = 200, checkpoint: str | None = None, checkpoint_every: int = 500, resume: str | None = None,
+          stop_after: int | None = None):
     """Train the network on (f, ILS_N(f)) pairs of random crops; returns (params, losses).
 
     The crops are the first n_crops of a seeded sequence of (image, offset) draws from a pool
@@ -189,6 +218,10 @@ def train(steps: int = 600, batch: int = 16, crop: int = 256, lr: float = 1e-3, 
     Learning rate: linear warm-up over `warmup` steps, then cosine decay.  The returned
     parameters are those at the lowest logged loss (a ReLU network can collapse to a
     constant output after one large step; the snapshot keeps the last good state).
+    checkpoint: file written every `checkpoint_every` steps and at the end (save_checkpoint);
+    resume: such a file to continue from (same seed, batch and schedule arguments);
+    stop_after: end after that many steps of the `steps`-long schedule (an interrupted run;
+    the checkpoint, if any, is written there).
     """
     dev = torch.device("cuda")
     pool = torch.from_numpy(crop_pool(pool_images, pool_size, seed=7000 + seed)).to(dev)
@@ -203,8 +236,18 @@ def train(steps: int = 600, batch: int = 16, crop: int = 256, lr: float = 1e-3, 
     loss = torch.zeros(1, device=dev)
     losses = []
     best = None
-    cursor = 0
-    for step in range(steps):
+    start = 0
+    if resume is not None:
+        ck = np.load(resume)
+        net.set_params(ck["params"])
+        net.set_adam(ck["adam_m"], ck["adam_v"], int(ck["adam_t"]))
+        start = int(ck["step"])
+        losses = [(int(a), float(b)) for a, b in ck["losses"]]
+        if np.isfinite(float(ck["best_loss"])):
+            best = (float(ck["best_loss"]), ck["best_params"].astype(np.float32))
+    cursor = start * batch
+    end = steps if stop_after is None else min(steps, stop_after)
+    for step in range(start, end):
         for i in range(batch):
             k, y, x = draws[cursor % n_crops]
             cursor += 1
@@ -223,6 +266,10 @@ def train(steps: int = 600, batch: int = 16, crop: int = 256, lr: float = 1e-3, 
                 best = (losses[-1][1], net.get_params())
             if verbose:
                 print(f"step {step:5d}  mse {losses[-1][1]:.3e}", flush=True)
+        if checkpoint is not None and ((step + 1) % checkpoint_every == 0 or step == end - 1):
+            save_checkpoint(checkpoint, net, step + 1, losses, best)
+    if best is None:   # resumed at the end: nothing left to run
+        best = (float("inf"), net.get_params())
     params = best[1]
     plan.close()
     net.close()
@@ -263,6 +310,9 @@ def main(argv=None):
     ap.add_argument("--n-crops", type=int, default=20000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--checkpoint", default=None, help="training-state file, written every --checkpoint-every steps")
+    ap.add_argument("--checkpoint-every", type=int, default=500)
+    ap.add_argument("--resume", default=None, help="continue training from a --checkpoint file")
     ap.add_argument("--smooth", metavar="HxW", default=None,
                     help="instead of training: warm-started smoothing (1 ILS iteration) of a synthetic RGB "
                          "frame of this size with the weights in --out, repeated --repeat times")
@@ -287,7 +337,8 @@ def main(argv=None):
         net.close()
         return
     t0 = time.time()
-    params, losses = train(steps=a.steps, batch=a.batch, crop=a.crop, lr=a.lr, n_crops=a.n_crops, seed=a.seed)
+    params, losses = train(steps=a.steps, batch=a.batch, crop=a.crop, lr=a.lr, n_crops=a.n_crops, seed=a.seed,
+                           checkpoint=a.checkpoint, checkpoint_every=a.checkpoint_every, resume=a.resume)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.save(a.out, params)
     print(json.dumps({"out": a.out, "seconds": time.time() - t0, "losses": losses}))

@@ -92,6 +92,58 @@ def test_adam_step_matches_oracle(ws):
     net.close()
 
 
+def test_adam_state_round_trip_and_restored_step(ws):
+    # checkpointed Adam state restores the next update: two steps on one network against one
+    # step, a checkpoint (weights, moments, step count) into a second network, and its step
+    import torch
+    p = random_params(ws, 5)
+    H, W = 16, 16
+    ft = torch.from_numpy(synth.preset_image(H, W, 3, "small", 11).reshape(1, 3, H, W)).cuda()
+    gu = torch.from_numpy(synth.random_field((1, 3, H, W), seed=3)).cuda()
+
+    def grad_step(net):
+        net.forward(ft)
+        net.zero_grad()
+        net.backward(ft, gu)
+        g = net.get_grads().astype(np.float64)
+        net.adam_step(1e-3)
+        return g
+
+    a = ws.WarmStartNet(H * W, p)
+    grad_step(a)
+    m, v, t = a.get_adam()
+    assert t == 1 and np.abs(m).max() > 0 and np.abs(v).max() > 0
+    b = ws.WarmStartNet(H * W, a.get_params())
+    b.set_adam(m, v, t)
+    m2, v2, t2 = b.get_adam()
+    np.testing.assert_array_equal(m2, m)
+    np.testing.assert_array_equal(v2, v)
+    assert t2 == t
+    w1 = a.get_params().astype(np.float64)
+    g = grad_step(b)
+    # the second Adam step from the restored state, in FP64
+    want, _, _ = O.adam_step(w1, g, m.astype(np.float64), v.astype(np.float64), 2, lr=1e-3)
+    np.testing.assert_allclose(b.get_params(), want, rtol=1e-5, atol=1e-7)
+    a.close()
+    b.close()
+
+
+def test_training_resumes_from_a_checkpoint(ws, tmp_path):
+    # a 6-step run against the same run stopped after 3 steps (checkpoint written) and resumed:
+    # the same data order, schedule and optimizer state, so the same loss trajectory and
+    # weights up to the FP32 atomic order of the weight gradients
+    kw = dict(steps=6, batch=2, crop=64, lr=3e-3, n_crops=16, pool_images=2, pool_size=128, log_every=1,
+              verbose=False, warmup=2)
+    full, full_losses = ws.train(**kw)
+    ck = str(tmp_path / "ck.npz")
+    ws.train(stop_after=3, checkpoint=ck, checkpoint_every=1000, **kw)
+    assert int(np.load(ck)["step"]) == 3
+    resumed, resumed_losses = ws.train(resume=ck, **kw)
+    assert [st for st, _ in resumed_losses] == [st for st, _ in full_losses] == list(range(6))
+    np.testing.assert_allclose([v for _, v in resumed_losses], [v for _, v in full_losses], rtol=1e-3)
+    np.testing.assert_allclose(resumed, full, rtol=1e-3, atol=1e-5)
+
+
 def test_mse_kernel(ws):
     import torch
     a = torch.from_numpy(synth.random_field((2, 3, 10, 12), seed=1)).cuda()
