@@ -1,6 +1,7 @@
 // C ABI of libils.so (declared in include/ils.h): plans, validation, tables and
 // the iteration driver of Algorithm 1.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -79,6 +80,13 @@ struct ils_plan {
 };
 
 namespace {
+
+// NVTX range over a scope (host side): a profiler attached to the process shows each
+// call and each pass launch of Algorithm 1; without one the calls cost a pointer test.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 thread_local std::string g_last_error;
 
@@ -230,14 +238,19 @@ ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float
     if ((e = mark_if(it == 0 ? ILS_KERNEL_ROW_FIRST : ILS_KERNEL_ROW))) return cuda_fail(e, "event");
     d.pdl = chain && it > 0;
     const Tables tn = iter_tab(pl, it);
-    if ((e = launch_row_forward(d, pl->geo, tn, iter_mp(pl, it), f, it == 0 ? u0 : nullptr, in, out, ck, st)))
-      return cuda_fail(e, "row pass launch");
+    {
+      NvtxRange r(it == 0 ? "ils row pass n=0" : "ils row pass");
+      if ((e = launch_row_forward(d, pl->geo, tn, iter_mp(pl, it), f, it == 0 ? u0 : nullptr, in, out, ck, st)))
+        return cuda_fail(e, "row pass launch");
+    }
     if ((e = mark_if(ILS_KERNEL_COLUMN))) return cuda_fail(e, "event");
     d.pdl = chain;
+    NvtxRange rc("ils column pass");
     if ((e = launch_col_solve(d, pl->geo, tn, out, st))) return cuda_fail(e, "column pass launch");
   }
   if ((e = mark_if(ILS_KERNEL_ROW_INVERSE))) return cuda_fail(e, "event");
   d.pdl = chain;
+  NvtxRange ri("ils final inverse row pass");
   if ((e = launch_row_inverse(d, pl->geo, pl->tab, spec[(pl->N - 1) & 1], u, st, epi)))
     return cuda_fail(e, "inverse row pass launch");
   return ILS_OK;
@@ -280,6 +293,7 @@ cudaGraphExec_t capture(ils_plan* pl, const LaunchKey& key) {
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
                    const Epilogue& epi = Epilogue(), const float* f_host = nullptr, float* u_host = nullptr) {
   const LaunchKey key{f, u0, u, ckpt, epi, f_host, u_host};
+  NvtxRange call("ils call");
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (pl->N == 0 || pl->profiling || !graphs_enabled() || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
       cs != cudaStreamCaptureStatusNone)
