@@ -164,6 +164,46 @@ def dist_env():
     return ws, rank, local
 
 
+def headline_line(ws, steps, warmup, ch, hh, ww, fps, total_ms, pct, prof, e2e_fps, frame_nbytes, clocks) -> dict:
+    """The JSON line of the headline measurement: fps of `steps` timed steps over `ws` replicas,
+    the dominant kernel's HBM roofline (per-launch event times in `prof`: kind -> (ms, launches))
+    and its issue roof, the end-to-end fps, the sampled clocks."""
+    per_kind, frame_bytes = bytes_model(hh, ww, ch, N_ITERS)
+    peak, peak_kind = load_peaks()
+    # dominant kernel = the kind with the largest share of device time
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    achieved = per_kind[dom] / (dom_ms / dom_n / 1000.0) / 1e9
+    whole = frame_bytes / (total_ms / steps / 1000.0) / 1e9
+    workload = f"ILS {ww}x{hh} {'RGB' if ch == 3 else f'{ch}-channel'} FP32, N=4, lambda=1, p=0.8, eps=1e-4"
+    return {
+        "metric": METRIC, "value": fps, "unit": "fps", "n_gpus": ws, "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload,
+                   "global_batch": ws, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed (512 MiB write) between timed steps",
+                   "mpix_per_s": fps * hh * ww / 1e6},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": load_traffic(dom),
+                     "issue": issue_roof(dom, dom_ms / dom_n, clocks.get("sm_mhz")),
+                     "traffic_unit": "GB per launch (ncu dram read + write)",
+                     "launch_timing": "events around every launch, second loop of the same K steps",
+                     "algorithmic_bytes_per_launch": per_kind[dom],
+                     "whole_step_gbs": whole, "whole_step_frac": whole / peak,
+                     "model": "fused: (20N+4) B per pixel and channel; an unfused stencil / FFT / "
+                              "solve / IFFT sequence would move ~28 B per pixel, channel and iteration"},
+        "step_ms_p10_p50_p90": [float(v) for v in pct],
+        "kernels": {k: {"launches": v[1], "ms_total": v[0], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+                    for k, v in prof.items()},
+        "e2e": None if e2e_fps is None else {"value": e2e_fps, "unit": "fps",
+                                              "h2d_bytes_per_step": frame_nbytes,
+                                              "d2h_bytes_per_step": frame_nbytes},
+        "gpu_launches": sum(v[1] for v in prof.values()),
+        "clocks": clocks,
+    }
+
+
 def max_over_ranks(value: float, ws: int, device) -> float:
     """The largest `value` over the ranks (the slowest replica sets a weak-scaling run's time);
     `device` is the tensor device of the process group's backend (cuda for nccl, cpu for gloo)."""
@@ -647,41 +687,9 @@ def run_ours(args):
         e2e_fps = frames / max_over_ranks(sum(e2e_times), ws, dev)
 
     if rank == 0:
-        per_kind, frame_bytes = bytes_model(hh, ww, ch, N_ITERS)
-        peak, peak_kind = load_peaks()
-        # dominant kernel = the kind with the largest share of device time
-        dom = max(prof, key=lambda k: prof[k][0])
-        dom_ms, dom_n = prof[dom]
-        achieved = per_kind[dom] / (dom_ms / dom_n / 1000.0) / 1e9
-        whole = frame_bytes / (total_ms / args.steps / 1000.0) / 1e9
-        workload = f"ILS {ww}x{hh} {'RGB' if ch == 3 else f'{ch}-channel'} FP32, N=4, lambda=1, p=0.8, eps=1e-4"
-        clocks = clk.summary()
-        line = {
-            "metric": METRIC, "value": fps, "unit": "fps", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload,
-                       "global_batch": ws, "parallelism": f"replicas x{ws}",
-                       "l2": "flushed (512 MiB write) between timed steps",
-                       "mpix_per_s": fps * hh * ww / 1e6},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": load_traffic(dom),
-                         "issue": issue_roof(dom, dom_ms / dom_n, clocks.get("sm_mhz")),
-                         "traffic_unit": "GB per launch (ncu dram read + write)",
-                         "launch_timing": "events around every launch, second loop of the same K steps",
-                         "algorithmic_bytes_per_launch": per_kind[dom],
-                         "whole_step_gbs": whole, "whole_step_frac": whole / peak,
-                         "model": "fused: (20N+4) B per pixel and channel; an unfused stencil / FFT / "
-                                  "solve / IFFT sequence would move ~28 B per pixel, channel and iteration"},
-            "step_ms_p10_p50_p90": [float(v) for v in pct],
-            "kernels": {k: {"launches": v[1], "ms_total": v[0], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
-                        for k, v in prof.items()},
-            "e2e": None if e2e_fps is None else {"value": e2e_fps, "unit": "fps",
-                                                  "h2d_bytes_per_step": int(frame.nbytes),
-                                                  "d2h_bytes_per_step": int(frame.nbytes)},
-            "gpu_launches": sum(v[1] for v in prof.values()),
-            "clocks": clocks,
-        }
+        line = headline_line(ws=ws, steps=args.steps, warmup=args.warmup, ch=ch, hh=hh, ww=ww, fps=fps,
+                             total_ms=total_ms, pct=pct, prof=prof, e2e_fps=e2e_fps, frame_nbytes=int(frame.nbytes),
+                             clocks=clk.summary())
         if not args.no_extras:
             ksteps = max(3, min(args.steps, 10))
             line["gray"] = gray_leg(ils, torch, dev, ksteps, flush)

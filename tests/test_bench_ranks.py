@@ -66,3 +66,30 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_headline_line_has_the_contract_keys():
+    # the JSON line's keys and their meaning, from synthetic measurements (no GPU)
+    import json
+    prof = {"row_first": (0.9, 20), "row": (2.6, 60), "column": (2.4, 80), "row_inverse": (0.45, 20)}
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    line = bench.headline_line(ws=1, steps=20, warmup=5, ch=3, hh=1080, ww=1920, fps=3900.0, total_ms=20 / 3.9,
+                               pct=[0.25, 0.256, 0.26], prof=prof, e2e_fps=2290.0, frame_nbytes=24883200,
+                               clocks=clocks)
+    json.dumps(line)   # serializable
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
+        assert k in line, k
+    assert line["unit"] == "fps" and line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["config"]["workload"].startswith("ILS 1920x1080 RGB")
+    r = line["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in r, k
+    assert r["kernel"] == "row" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    # the row pass moves 12 B per pixel and channel: 74.6 MB per 1080p RGB launch
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(12 * 1920 * 1080 * 3, rel=1e-3)
+    assert r["achieved"] == pytest.approx(r["algorithmic_bytes_per_launch"] / (2.6 / 60 / 1e3) / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    e = line["e2e"]
+    assert e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 24883200 and e["unit"] == "fps"
+    assert line["gpu_launches"] == 180
