@@ -50,6 +50,8 @@ typedef enum {
   ILS_ERR_OOM = 3,              /* a device or host allocation failed */
   ILS_ERR_CUDA = 4,             /* a CUDA runtime call failed; see ils_last_error() */
   ILS_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up (status word set by a kernel) */
+  ILS_ERR_FALLBACK_TAKEN = 6,   /* information, never a call's return value: the warm-started
+                                   smoother ran plain ILS instead (ils_warm_smooth's flag) */
 } ils_status;
 
 /* Human-readable name of a status code (static storage). */
@@ -220,8 +222,40 @@ ils_status ils_smooth_from(ils_plan* plan, const float* f, const float* u0, floa
 ils_status ils_smooth_host(ils_plan* plan, const float* f_host, float* u_host, void* stream);
 
 /*
+ * ils_set_checkpointing - plan-owned checkpoints for the adjoint (reverse mode through
+ * Algorithm 1; the paper has no adjoint, this is the chain rule through Eq. 9 and Eq. 7).
+ *   on != 0 : the plan allocates N x C x H x W float32 (on the current device, once) and every
+ *             later ils_smooth / ils_smooth_from call stores its iterates u^0 .. u^{N-1} there
+ *             for ils_backward (the same launches, each row pass also writing its u^n).
+ *   on == 0 : frees that buffer (synchronizes the device); calls stop storing iterates.
+ * Returns ILS_ERR_INVALID_ARG for a half-quadratic-splitting plan (no adjoint), ILS_ERR_OOM
+ * if the buffer cannot be allocated.  Allocate before any stream capture.
+ */
+ils_status ils_set_checkpointing(ils_plan* plan, int on);
+
+/*
+ * ils_backward - gradient of a scalar loss L through the plan's last checkpointed smoothing.
+ * With A the Eq. 9 operator (symmetric) and g = dL/du^{n+1}, each step n = N-1 .. 0 computes
+ * r = A^-1 g with the same FFT solve, adds r to dL/df (the direct dependence through Eq. 9's
+ * F(f)), and forms dL/du^n = lambda/2 sum_* grad_*^T [g''(grad_* u^n) * grad_* r], g'' from
+ * Appendix B.
+ *   f      : the device pointer f of the last ils_smooth / ils_smooth_from call made with
+ *            checkpointing on (its checkpoints are used; another pointer, or no such call,
+ *            returns ILS_ERR_INVALID_ARG).
+ *   grad_u : device pointer, dL/du^N, C x H x W (read only).
+ *   grad_f : device pointer, receives dL/df, C x H x W; for ils_smooth (u^0 = f) this
+ *            includes the path through u^0, for ils_smooth_from with a separate u^0 only the
+ *            direct part (ils_backward_ckpt returns dL/du^0 separately).  Must not overlap
+ *            f or grad_u.
+ * The first call after a warm-started forward allocates a C x H x W buffer that the plan
+ * keeps.  Stream-ordered after the forward on the same stream.
+ */
+ils_status ils_backward(ils_plan* plan, const float* f, const float* grad_u, float* grad_f, void* stream);
+
+/*
  * ils_smooth_checkpointed - Algorithm 1 (from u0, or from f when u0 is NULL) that
- * also stores the iterates u^0 .. u^{N-1} for ils_backward.
+ * also stores the iterates u^0 .. u^{N-1} in a caller-owned buffer for ils_backward_ckpt
+ * (for callers that keep several forward results alive at once, e.g. autograd graphs).
  *   ckpt : device pointer, caller-owned, N x C x H x W float32 (iterate n at offset
  *          n*C*H*W); must not overlap f, u0 or u.  May be NULL only when N = 0.
  */
@@ -229,11 +263,8 @@ ils_status ils_smooth_checkpointed(ils_plan* plan, const float* f, const float* 
                                    void* stream);
 
 /*
- * ils_backward - gradient of a scalar loss L through Algorithm 1 (reverse mode; the
- * paper has no adjoint, this is the chain rule through Eq. 9 and Eq. 7).  With A the
- * Eq. 9 operator (symmetric) and g = dL/du^{n+1}, each step computes r = A^-1 g with
- * the same FFT solve, adds r to dL/df, and forms dL/du^n =
- * lambda/2 sum_* grad_*^T [g''(grad_* u^n) * grad_* r], g'' from Appendix B.
+ * ils_backward_ckpt - ils_backward on caller-owned checkpoints, with the gradient of the
+ * starting point available separately.
  *   ckpt    : the iterates written by ils_smooth_checkpointed for this input (read only).
  *   grad_u  : device pointer, dL/du^N, C x H x W (read only).
  *   grad_f  : device pointer, receives dL/df (the direct dependence through Eq. 9's F(f)),
@@ -241,8 +272,8 @@ ils_status ils_smooth_checkpointed(ils_plan* plan, const float* f, const float* 
  *   grad_u0 : NULL, or a device pointer receiving dL/du^0 separately (warm starts).
  * Outputs must not overlap each other or grad_u.
  */
-ils_status ils_backward(ils_plan* plan, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
-                        void* stream);
+ils_status ils_backward_ckpt(ils_plan* plan, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
+                             void* stream);
 
 /*
  * Batches of frames of uneven size (not in the paper: a serving-side extension).
@@ -355,17 +386,28 @@ ils_status ils_mse(const float* u0, const float* target, float* grad, long long 
 /*
  * Warm-started smoothing: u = ILS_iters(f; u^0 = f + net(f)) (Algorithm 1 from u^0),
  * and plain ILS (n_plain iterations from f) instead when the last iterate change
- * max |u^iters - u^{iters-1}| exceeds tau.  C must be a multiple of 3 (RGB frames).
- * The network is borrowed and must outlive the object.
+ * delta = max |u^iters - u^{iters-1}| exceeds tau (a NaN change counts as +inf).
+ * C must be a multiple of 3 (RGB frames).  The network is borrowed and must outlive the
+ * object.  delta is reduced inside the final inverse row pass and the decision is taken on
+ * the device: each call runs as one CUDA graph (network, warm iterations, decision, and a
+ * conditional node whose body is the plain ILS), captured at the first call for a given
+ * (f, u) pair and replayed for later calls with the same pair.
  */
 typedef struct ils_warm ils_warm;
 ils_status ils_warm_create(int H, int W, int C, float lambda, float p, float eps, int iters, int n_plain, float tau,
                            ils_cnn* net, ils_warm** out);
 ils_status ils_warm_destroy(ils_warm* warm);
-/* f, u: device C x H x W.  Waits on `stream` for the iterate change (a 4-byte read).
- * *fallback_taken and *delta (either may be NULL) report the decision and the change. */
+/* f, u: device C x H x W, non-overlapping.  With fallback_taken and delta both NULL the call
+ * is asynchronous (nothing waits on the host); otherwise it synchronizes `stream` and sets
+ * *fallback_taken to ILS_ERR_FALLBACK_TAKEN when the plain path ran (ILS_OK otherwise) and
+ * *delta to the warm path's last change.  Returns ILS_ERR_INVALID_ARG when `stream` is being
+ * captured (the call launches a graph of its own).  ILS_GRAPHS=0 in the environment keeps
+ * direct launches with the decision taken on the host. */
 ils_status ils_warm_smooth(ils_warm* warm, const float* f, float* u, int* fallback_taken, float* delta,
                            void* stream);
+/* The decision and delta of the last ils_warm_smooth call, once its stream has been
+ * synchronized (host arrays written by the call's final device-to-host copy). */
+ils_status ils_warm_result(const ils_warm* warm, int* fallback_taken, float* delta);
 
 /*
  * Per-kernel timing, for measurement tools.  Kernel kinds of one ils_smooth call:
@@ -404,19 +446,26 @@ ils_status ils_get_profile(const ils_plan* plan, double* ms, long long* launches
  *
  * Limits: C*H*W <= ILS_NOALLOC_MAX_ELEMS (2^21 floats, e.g. one 1920 x 1080
  * channel) and H, W <= ILS_NOALLOC_MAX_SIDE; larger images return
- * ILS_ERR_UNSUPPORTED_SIZE.  The array (about 16.3 MiB) is part of the library:
- * every GPU that loads libils.so holds it until the process exits.
+ * ILS_ERR_UNSUPPORTED_SIZE.  The array (ILS_NOALLOC_SCRATCH_BYTES = 17,252,608
+ * bytes, 16.45 MiB: two image-sized spectra and the largest twiddle and
+ * denominator tables) is part of the library: every GPU that loads libils.so
+ * holds it until the process exits.
  *
- * The first call on a device looks up the array's device address with that
- * device current (and sets the kernels' shared-memory limits); make that first
- * call before any stream capture.  All calls on a device share the one array,
- * which keeps the previous call's contents (nothing in it needs to start at
- * zero: every word is written before it is read).  Calls that overlap on the
- * GPU - on two streams, or from two threads - race on it and must be
- * serialized by the caller.  Returns ILS_ERR_CUDA if a launch fails.
+ * A __device__ array has one instance per CUDA context.  The first call in a
+ * context (the device's primary context, or a context the host application
+ * made current) looks up the array's address in that context and sets the
+ * kernels' shared-memory limits there; the result is cached per context (keyed
+ * by the context's process-unique identifier, so a context re-created after
+ * cudaDeviceReset is set up again).  Make that first call before any stream
+ * capture.  All calls in a context share the one array, which keeps the
+ * previous call's contents (nothing in it needs to start at zero: every word is
+ * written before it is read).  Calls that overlap on the GPU - on two streams,
+ * or from two threads - race on it and must be serialized by the caller.
+ * Returns ILS_ERR_CUDA if a launch fails.
  */
 #define ILS_NOALLOC_MAX_ELEMS (1 << 21)
 #define ILS_NOALLOC_MAX_SIDE 8192
+#define ILS_NOALLOC_SCRATCH_BYTES 17252608
 ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, float p, float eps, int N,
                               const float* f, float* u, void* stream);
 

@@ -18,7 +18,10 @@ STATUS = {
     3: "ILS_ERR_OOM",
     4: "ILS_ERR_CUDA",
     5: "ILS_ERR_TIMEOUT",
+    6: "ILS_ERR_FALLBACK_TAKEN",
 }
+
+ILS_ERR_FALLBACK_TAKEN = 6
 
 _lib = None
 
@@ -60,7 +63,9 @@ SIGNATURES = {
     "ils_smooth_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ils_smooth_checkpointed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    "ils_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_backward_ckpt": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ils_set_checkpointing": (c_int, [c_void_p, c_int]),
     "ils_set_profiling": (c_int, [c_void_p, c_int]),
     "ils_get_profile": (c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_longlong)]),
     "ils_batch_create": (c_int, [ctypes.c_void_p, c_int, c_int, P(c_void_p)]),
@@ -88,6 +93,7 @@ SIGNATURES = {
                                 P(c_void_p)]),
     "ils_warm_destroy": (c_int, [c_void_p]),
     "ils_warm_smooth": (c_int, [c_void_p, c_void_p, c_void_p, P(c_int), P(c_float), c_void_p]),
+    "ils_warm_result": (c_int, [c_void_p, P(c_int), P(c_float)]),
     "ils_smooth_noalloc": (c_int, [c_int, c_int, c_int, c_float, c_float, c_float, c_int,
                                    c_void_p, c_void_p, c_void_p]),
 }

@@ -33,7 +33,8 @@ struct LaunchKey {
     return f == o.f && u0 == o.u0 && u == o.u && ckpt == o.ckpt && f_host == o.f_host && u_host == o.u_host &&
            epi.mode == o.epi.mode && epi.s == o.epi.s &&
            epi.a == o.epi.a && epi.o == o.epi.o && epi.f == o.epi.f && epi.rgb == o.epi.rgb && epi.dst == o.epi.dst &&
-           epi.C == o.epi.C && epi.c0 == o.epi.c0 && epi.plane2 == o.epi.plane2;
+           epi.C == o.epi.C && epi.c0 == o.epi.c0 && epi.plane2 == o.epi.plane2 && epi.prev == o.epi.prev &&
+           epi.dmax == o.epi.dmax;
   }
 };
 struct GraphEntry {
@@ -55,6 +56,12 @@ struct ils_plan {
   float* stage_f;      // device staging for ils_smooth_host
   float* stage_u;
   float* luma;         // luminance of ils_smooth_luma (H x W), allocated at its first call
+  // plan-owned checkpoints (ils_set_checkpointing): while on, ils_smooth / ils_smooth_from store
+  // u^0 .. u^{N-1} here, and ils_backward differentiates the last such call (its f, u0 kept)
+  float* ckpt_own;
+  const float* ckpt_f;
+  const float* ckpt_u0;
+  bool ckpt_valid;
   // half-quadratic splitting: per-iteration Eq. 14 parameters and denominator tables
   // (iteration n: ax at iter_tab + n (M + 1 + H), by right after it)
   std::vector<MuParams> mp_iter;
@@ -156,6 +163,7 @@ void free_plan_memory(ils_plan* pl) {
   cudaFree(pl->stage_f);
   cudaFree(pl->stage_u);
   cudaFree(pl->luma);
+  cudaFree(pl->ckpt_own);
   cudaFree(pl->iter_tab);
   cudaFree(pl->tab.twW);
   cudaFree(pl->tab.twH);
@@ -222,6 +230,7 @@ ils_status enqueue_ils(ils_plan* pl, int c0, int cn, const float* f, const float
   Epilogue epi = epi_in;
   if (epi.mode == 1) epi.f += off;
   if (epi.mode == 3) epi.c0 += c0;
+  if (epi.mode == 5) epi.prev += off;
   f += off;
   u += off;
   if (u0 != nullptr) u0 += off;
@@ -447,6 +456,13 @@ bool pdl_enabled() {
 void record_cuda_error(const char* where, cudaError_t e) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
 }
+
+// Algorithm 1 from u0 (f when null) through the plan with an output stage and optional
+// caller-owned checkpoints (the warm-started smoother's call; no argument checks here).
+int run_plan_epilogue(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt, const Epilogue& epi,
+                      cudaStream_t st) {
+  return (int)run_ils(pl, f, u0, u, ckpt, st, epi);
+}
 }  // namespace ils
 
 extern "C" {
@@ -459,6 +475,7 @@ const char* ils_status_string(ils_status s) {
     case ILS_ERR_OOM: return "ILS_ERR_OOM";
     case ILS_ERR_CUDA: return "ILS_ERR_CUDA";
     case ILS_ERR_TIMEOUT: return "ILS_ERR_TIMEOUT";
+    case ILS_ERR_FALLBACK_TAKEN: return "ILS_ERR_FALLBACK_TAKEN";
   }
   return "ILS_ERR_UNKNOWN";
 }
@@ -683,7 +700,34 @@ ils_status ils_smooth_from(ils_plan* pl, const float* f, const float* u0, float*
   if (pl == nullptr || f == nullptr || u == nullptr) return ILS_ERR_INVALID_ARG;
   const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
   if (overlaps(f, u, bytes) || (u0 != nullptr && overlaps(u0, u, bytes))) return ILS_ERR_INVALID_ARG;
-  return run_ils(pl, f, u0, u, nullptr, static_cast<cudaStream_t>(stream));
+  float* ck = nullptr;
+  if (pl->ckpt_own != nullptr) {
+    ck = pl->ckpt_own;
+    pl->ckpt_valid = false;  // until the call is enqueued
+  }
+  const ils_status s = run_ils(pl, f, u0, u, ck, static_cast<cudaStream_t>(stream));
+  if (ck != nullptr && s == ILS_OK) {
+    pl->ckpt_f = f;
+    pl->ckpt_u0 = u0 == f ? nullptr : u0;
+    pl->ckpt_valid = true;
+  }
+  return s;
+}
+
+ils_status ils_set_checkpointing(ils_plan* pl, int on) {
+  if (pl == nullptr || !pl->mp_iter.empty()) return ILS_ERR_INVALID_ARG;  // no adjoint of the splitting
+  pl->ckpt_valid = false;
+  if (!on) {
+    if (pl->ckpt_own != nullptr) {
+      const cudaError_t e = cudaDeviceSynchronize();  // the buffer may still be written
+      cudaFree(pl->ckpt_own);
+      pl->ckpt_own = nullptr;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    }
+    return ILS_OK;
+  }
+  if (pl->ckpt_own != nullptr || pl->N == 0) return ILS_OK;
+  return dev_alloc((void**)&pl->ckpt_own, (size_t)pl->N * pl->C * pl->H * pl->W * sizeof(float));
 }
 
 ils_status ils_smooth_checkpointed(ils_plan* pl, const float* f, const float* u0, float* u, float* ckpt,
@@ -698,8 +742,8 @@ ils_status ils_smooth_checkpointed(ils_plan* pl, const float* f, const float* u0
   return run_ils(pl, f, u0, u, pl->N > 0 ? ckpt : nullptr, static_cast<cudaStream_t>(stream));
 }
 
-ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
-                        void* stream) {
+ils_status ils_backward_ckpt(ils_plan* pl, const float* ckpt, const float* grad_u, float* grad_f, float* grad_u0,
+                             void* stream) {
   if (pl == nullptr || grad_u == nullptr || grad_f == nullptr || (ckpt == nullptr && pl->N > 0) ||
       !pl->mp_iter.empty())  // no adjoint for half-quadratic splitting
     return ILS_ERR_INVALID_ARG;
@@ -741,6 +785,24 @@ ils_status ils_backward(ils_plan* pl, const float* ckpt, const float* grad_u, fl
     }
   }
   return ILS_OK;
+}
+
+ils_status ils_backward(ils_plan* pl, const float* f, const float* grad_u, float* grad_f, void* stream) {
+  if (pl == nullptr || f == nullptr || grad_u == nullptr || grad_f == nullptr) return ILS_ERR_INVALID_ARG;
+  // the checkpoints must be those of a forward call on this f
+  if (pl->N > 0 && (pl->ckpt_own == nullptr || !pl->ckpt_valid || pl->ckpt_f != f)) return ILS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)pl->C * pl->H * pl->W * sizeof(float);
+  if (overlaps(grad_f, f, bytes)) return ILS_ERR_INVALID_ARG;
+  // u^0 = f: dL/du^0 joins dL/df; a separate warm start u^0 keeps only the direct part
+  float* gu0 = nullptr;
+  if (pl->N > 0 && pl->ckpt_u0 != nullptr) {
+    if (pl->stage_u == nullptr) {
+      const ils_status s = dev_alloc((void**)&pl->stage_u, bytes);
+      if (s != ILS_OK) return s;
+    }
+    gu0 = pl->stage_u;
+  }
+  return ils_backward_ckpt(pl, pl->ckpt_own, grad_u, grad_f, gu0, stream);
 }
 
 ils_status ils_smooth(ils_plan* pl, const float* f, float* u, void* stream) {

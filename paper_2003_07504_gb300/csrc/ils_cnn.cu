@@ -400,15 +400,6 @@ __global__ void mse_kernel(const float* u0, const float* target, float* grad, si
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * scale);
 }
 
-// max |a - b| over n values, as the bit pattern of a non-negative float (monotone in the value)
-__global__ void maxabsdiff_kernel(const float* a, const float* b, size_t n, unsigned int* out) {
-  float m = 0.0f;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(a[i] - b[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
-}
-
 }  // namespace cnn
 }  // namespace ils
 
@@ -833,10 +824,3 @@ ils_status ils_mse(const float* u0, const float* target, float* grad, long long 
 }
 
 }  // extern "C"
-
-namespace ils {
-cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st) {
-  maxabsdiff_kernel<<<512, 256, 0, st>>>(a, b, n, out);
-  return cudaGetLastError();
-}
-}  // namespace ils

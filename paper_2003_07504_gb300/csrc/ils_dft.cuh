@@ -2,11 +2,17 @@
 //
 // dft_reg<R, INV>(v) replaces v[0..R-1] by its R-point DFT (forward: exp(-2 pi i jk/R),
 // INV: exp(+2 pi i jk/R), unnormalized).  R in {2,3,4,5,8} are written out; every other
-// supported R = A*B is one Cooley-Tukey step on registers: B DFTs of size A on the
-// stride-B subsequences, multiplication by w_R^{n2 k1}, then A DFTs of size B, with
-// output index k1 + A k2.  The w_R constants come from a compile-time table built with
-// a Taylor-series sine/cosine written here (no math-library call), so after unrolling
-// every twiddle is an immediate.
+// supported R = A*B is split once on registers:
+//  * gcd(A, B) = 1: the prime-factor (Good-Thomas) mapping.  Input n = (B n1 + A n2) mod R
+//    and output k with k = k1 (mod A), k = k2 (mod B) turn the R-point DFT into B DFTs of
+//    size A followed by A DFTs of size B with no twiddle multiplications at all (the
+//    kernel exp(-2 pi i n k / R) factors exactly into the two smaller kernels);
+//  * otherwise one Cooley-Tukey step: B DFTs of size A on the stride-B subsequences,
+//    multiplication by w_R^{n2 k1}, then A DFTs of size B, with output index k1 + A k2.
+//    Twiddles on the eighth turns (w = +-1, +-i, (+-1 +- i)/sqrt 2) are applied as sign
+//    changes and swaps (and one sqrt(1/2) scaling); the others come from a compile-time table
+//    built with a Taylor-series sine/cosine written here (no math-library call), so after
+//    unrolling every twiddle is an immediate.
 //
 // All functions are __host__ __device__ so the same code can be exercised on the CPU.
 #pragma once
@@ -164,36 +170,82 @@ template <> struct Split<64> { static constexpr int A = 8, B = 8; };
 template <int R, bool INV>
 ILS_HD void dft_reg(float2* v);
 
+constexpr int ct_gcd(int a, int b) { return b == 0 ? a : ct_gcd(b, a % b); }
+// x with x * a = 1 (mod m), for gcd(a, m) = 1
+constexpr int ct_modinv(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((x * a) % m == 1) return x;
+  return m == 1 ? 0 : -1;
+}
+
+// t * w_R^m (forward: exp(-2 pi i m / R); INV: the conjugate), m a compile-time constant after
+// unrolling.  Eighth turns are exact sign changes and swaps.
+template <int R, bool INV>
+ILS_HD float2 twiddle_const(float2 t, int m, const Roots<R>& w) {
+  constexpr float h = 0.70710678118654752440f;  // sqrt(2)/2
+  m %= R;
+  if (m == 0) return t;
+  if ((8 * m) % R == 0) {
+    const int q = 8 * m / R;  // forward angle -q pi / 4
+    switch (q) {
+      case 2: return rot90<INV>(t);
+      case 4: return c2(-t.x, -t.y);
+      case 6: return rot90<!INV>(t);
+      case 1: return INV ? c2(h * (t.x - t.y), h * (t.x + t.y)) : c2(h * (t.x + t.y), h * (t.y - t.x));
+      case 3: return INV ? c2(-h * (t.x + t.y), h * (t.x - t.y)) : c2(h * (t.y - t.x), -h * (t.x + t.y));
+      case 5: return INV ? c2(h * (t.y - t.x), -h * (t.x + t.y)) : c2(-h * (t.x + t.y), h * (t.x - t.y));
+      default: return INV ? c2(h * (t.x + t.y), h * (t.y - t.x)) : c2(h * (t.x - t.y), h * (t.x + t.y));
+    }
+  }
+  return cmul(t, c2(w.re[m], INV ? -w.im[m] : w.im[m]));
+}
+
 template <int A, int B, bool INV>
 ILS_HD void dft_composite(float2* v) {
   constexpr int R = A * B;
-  constexpr Roots<R> w{};
   float2 y[R];
+  if constexpr (ct_gcd(A, B) == 1) {
+    // Good-Thomas: x[(B n1 + A n2) mod R] -> DFT_A over n1 -> DFT_B over n2 -> X[k], k = k1 (A),
+    // k = k2 (B), i.e. k = (k1 B (B^-1 mod A) + k2 A (A^-1 mod B)) mod R
+    constexpr int eA = B * ct_modinv(B % A, A), eB = A * ct_modinv(A % B, B);
 #pragma unroll
-  for (int n2 = 0; n2 < B; ++n2) {
-    float2 t[A];
+    for (int n2 = 0; n2 < B; ++n2) {
+      float2 t[A];
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) t[n1] = v[B * n1 + n2];
-    dft_reg<A, INV>(t);
+      for (int n1 = 0; n1 < A; ++n1) t[n1] = v[(B * n1 + A * n2) % R];
+      dft_reg<A, INV>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) y[n2 * A + k1] = t[k1];
+    }
 #pragma unroll
     for (int k1 = 0; k1 < A; ++k1) {
-      const int m = (n2 * k1) % R;
-      if (m == 0) {
-        y[n2 * A + k1] = t[k1];
-      } else {
-        const float2 tw = c2(w.re[m], INV ? -w.im[m] : w.im[m]);
-        y[n2 * A + k1] = cmul(t[k1], tw);
-      }
+      float2 t[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+      dft_reg<B, INV>(t);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) v[(k1 * eA + k2 * eB) % R] = t[k2];
     }
-  }
+  } else {
+    constexpr Roots<R> w{};
 #pragma unroll
-  for (int k1 = 0; k1 < A; ++k1) {
-    float2 t[B];
+    for (int n2 = 0; n2 < B; ++n2) {
+      float2 t[A];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
-    dft_reg<B, INV>(t);
+      for (int n1 = 0; n1 < A; ++n1) t[n1] = v[B * n1 + n2];
+      dft_reg<A, INV>(t);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+      for (int k1 = 0; k1 < A; ++k1) y[n2 * A + k1] = twiddle_const<R, INV>(t[k1], n2 * k1, w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      float2 t[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+      dft_reg<B, INV>(t);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+    }
   }
 }
 

@@ -67,13 +67,14 @@ struct StageTw {
 };
 
 // bfly with the twiddles of a StageTw table (the same values as root(), read coalesced).
+// tab is a global table or a CTA's shared-memory copy (plain loads: either address space).
 template <int R, int NS, bool INV>
 __device__ __forceinline__ void bfly_tab(float2 (&v)[R], int j, const float2* __restrict__ tab) {
   if constexpr (NS > 1) {
     const int k = j % NS;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      float2 w = __ldg(&tab[(r - 1) * NS + k]);
+      float2 w = tab[(r - 1) * NS + k];
       if (INV) w.y = -w.y;
       v[r] = cmul(v[r], w);
     }

@@ -70,7 +70,12 @@ constexpr int kPenalties = 3;
 //           pixels hold C channels each (out is not written);
 //   mode 4: log-luminance tone mapping (Sec. 4.2: smoothing on the logarithm of the
 //           luminance): f is l = ln Y of the 3-plane image rgb, u the base layer b, and
-//           out_c = rgb_c exp(a l + s b + o) for the three planes.
+//           out_c = rgb_c exp(a l + s b + o) for the three planes;
+//   mode 5: out = u, and the largest iterate change max |u - prev| (prev = u^{N-1}) of the
+//           pass is max-reduced into *dmax (the bits of a non-negative float; a NaN change
+//           counts as +inf): the fallback test of the warm-started smoother.
+// store<MODE> returns the pair's contribution to that maximum (0 for the other modes); a
+// kernel keeps the running maximum per thread and calls finish<MODE> once at its end.
 struct Epilogue {
   int mode = 0;
   float s = 1.0f;
@@ -80,11 +85,19 @@ struct Epilogue {
   float* dst = nullptr;      // mode 3
   int C = 1, c0 = 0;         // mode 3: channels per pixel of dst, channel of the first plane
   size_t plane2 = 0;         // modes 2-4: pixel pairs per plane (H W / 2)
+  const float* prev = nullptr;  // mode 5
+  unsigned int* dmax = nullptr;  // mode 5
   // MODE is the kernel's compile-time copy of `mode` (one instantiation per mode)
   template <int MODE>
-  __device__ __forceinline__ void store(float2* out, size_t i, float2 u) const {
+  __device__ __forceinline__ float store(float2* out, size_t i, float2 u) const {
     if constexpr (MODE == 0) {
       out[i] = u;
+    } else if constexpr (MODE == 5) {
+      out[i] = u;
+      const float2 q = reinterpret_cast<const float2*>(prev)[i];
+      const float d = fmaxf(fabsf(u.x - q.x), fabsf(u.y - q.y));
+      // fmaxf drops a NaN operand: a NaN in either pair member must still read as a change
+      return (u.x - q.x == u.x - q.x && u.y - q.y == u.y - q.y) ? d : __int_as_float(0x7f800000);
     } else if constexpr (MODE == 3) {
       // 32-bit split of the pair index (the host limits interleaved images to < 2^32 pairs)
       const unsigned ii = (unsigned)i, p2 = (unsigned)plane2;
@@ -116,9 +129,20 @@ struct Epilogue {
         }
       }
     }
+    return 0.0f;
+  }
+  // mode 5: max-reduce this thread's running maximum into *dmax, one atomic per warp (over
+  // the lanes that reach the call; non-negative floats order like their bit patterns)
+  template <int MODE>
+  __device__ __forceinline__ void finish(float dm) const {
+    if constexpr (MODE == 5) {
+      const unsigned m = __activemask();
+      const unsigned v = __reduce_max_sync(m, __float_as_uint(dm));
+      if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMax(dmax, v);
+    }
   }
 };
-constexpr int kEpilogues = 5;
+constexpr int kEpilogues = 6;
 
 // Launch geometry picked by the host planner (validated before any launch).
 struct Geometry {
@@ -213,8 +237,6 @@ cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt
 cudaError_t warm_fused_set_attributes();
 cudaError_t launch_warm_fused(int B, int H, int W, const float* f, void* act, float* u0, const void* const* w,
                               const float* const* bias, int* error, cudaStream_t st);
-// max |a - b| over n floats as the bit pattern of a non-negative float, atomically max'ed into *out
-cudaError_t launch_maxabsdiff(const float* a, const float* b, size_t n, unsigned int* out, cudaStream_t st);
 
 // Compile-time specialised kernels (ils_kernels_fixed.cu).
 int fixed_row_index(int M);

@@ -325,8 +325,10 @@ row_inverse_kernel(int H, int W, int rows, FftPlan planM, const float2* __restri
   __syncthreads();
   fft_smem<EPT, true>(sm, planM, n, 1, M, twW, 2);
   const size_t rowoff = ch * plane + (size_t)y0 * M;
+  float dm = 0.0f;
   for (int w = threadIdx.x; w < n * M; w += T)
-    epi.template store<EPI>(reinterpret_cast<float2*>(u), rowoff + w, sm[smem_idx(w)]);
+    dm = fmaxf(dm, epi.template store<EPI>(reinterpret_cast<float2*>(u), rowoff + w, sm[smem_idx(w)]));
+  epi.template finish<EPI>(dm);
 }
 
 // ---------------------------------------------------------------- host side
@@ -480,6 +482,8 @@ cudaError_t set_kernel_attributes() {
   if ((e = allow_smem(row_inverse_kernel<32, 3>))) return e;
   if ((e = allow_smem(row_inverse_kernel<16, 4>))) return e;
   if ((e = allow_smem(row_inverse_kernel<32, 4>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<16, 5>))) return e;
+  if ((e = allow_smem(row_inverse_kernel<32, 5>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<32, 0>))) return e;
   if ((e = allow_smem(row_adjoint_kernel<16, 1>))) return e;
@@ -529,9 +533,9 @@ cudaError_t launch_row_inverse(const ImageDesc& d, const Geometry& g, const Tabl
   using InvFn = void (*)(int, int, int, FftPlan, const float2*, const float2*, float*, Epilogue);
   static const InvFn fns[2][kEpilogues] = {
       {row_inverse_kernel<16, 0>, row_inverse_kernel<16, 1>, row_inverse_kernel<16, 2>, row_inverse_kernel<16, 3>,
-       row_inverse_kernel<16, 4>},
+       row_inverse_kernel<16, 4>, row_inverse_kernel<16, 5>},
       {row_inverse_kernel<32, 0>, row_inverse_kernel<32, 1>, row_inverse_kernel<32, 2>, row_inverse_kernel<32, 3>,
-       row_inverse_kernel<32, 4>}};
+       row_inverse_kernel<32, 4>, row_inverse_kernel<32, 5>}};
   const InvFn fn = fns[g.ept_inv == 16 ? 0 : 1][epi.mode];
   return launch_k(d.pdl, fn, grid, g.threads_inv, g.smem_inv, stream, d.H, d.W, g.rows_inv, d.planM, t.twW, spec, u,
                   epi);

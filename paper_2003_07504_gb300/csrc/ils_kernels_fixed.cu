@@ -21,6 +21,39 @@ namespace {
 
 __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (y >= H ? y - H : y); }
 
+// Asynchronous global -> shared copies of 8 and 4 bytes (cp.async.ca); the caller waits.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared memory of a column-pass CTA: the tile of G columns (padded by smem_idx), then the
+// plan's stage twiddle table and the H-entry y part of the Eq. 9 denominator, copied once
+// per CTA so that every twiddle and denominator read of the transforms is a shared-memory
+// load instead of a dependent global load.
+// Staged only where MINB CTAs per SM still fit (the 2160-point plans read the tables from
+// global memory instead).
+template <class PL, int G>
+constexpr size_t col_tile_bytes() {  // smem_elems(N G) complex (one padding slot per 16)
+  return (size_t)(PL::N * G + (PL::N * G - 1) / 16) * sizeof(float2);
+}
+template <class PL, int G, int MINB>
+constexpr bool col_stages_tables() {
+  return MINB * (col_tile_bytes<PL, G>() + (size_t)StageTw<PL>::SIZE * sizeof(float2) +
+                 (size_t)PL::N * sizeof(float) + 1024) <= (size_t)227 * 1024;
+}
+template <class PL, int G, int MINB>
+constexpr size_t col_smem_bytes() {
+  return col_tile_bytes<PL, G>() + (col_stages_tables<PL, G, MINB>()
+                                        ? (size_t)StageTw<PL>::SIZE * sizeof(float2) + (size_t)PL::N * sizeof(float)
+                                        : 0);
+}
+
 
 
 
@@ -73,8 +106,17 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
   griddep_wait();
   constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = N / R0, NS1 = N / R1, NSL = N / RL;
-  using TW = StageTw<PL>;  // twc: this plan's stage twiddle tables
+  using TW = StageTw<PL>;  // twc: this plan's stage twiddle tables (copied to tws)
   extern __shared__ float2 sm[];
+  constexpr bool STAGE_TW = col_stages_tables<PL, G, MINB>();
+  float2* tws_s = sm + smem_elems(N * G);
+  float* bys_s = reinterpret_cast<float*>(tws_s + TW::SIZE);
+  if constexpr (STAGE_TW) {
+    for (int i = threadIdx.x; i < TW::SIZE; i += blockDim.x) cp_async8(tws_s + i, twc + i);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async4(bys_s + i, by + i);
+  }
+  const float2* tws = STAGE_TW ? tws_s : twc;
+  const float* bys = STAGE_TW ? bys_s : by;
   const int tiles_per_ch = (M + G - 1) / G;
   const int ntiles = tiles_per_ch * C;
   {
@@ -105,6 +147,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
         for (int q = 0; q < BATCH; ++q)
           if (q0 + q < PER && t + (q0 + q) * T < N * G) sm[smem_idx(t + (q0 + q) * T)] = ld[q];
       }
+      cp_async_wait_all_();  // this thread's table copies
       __syncthreads();
       float2 v[R0];
       if (j < NS0) {
@@ -124,7 +167,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly_tab<R1, R0, false>(v, j, twc + TW::FWD_MID);
+        bfly_tab<R1, R0, false>(v, j, tws + TW::FWD_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -139,7 +182,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NSL) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[r] = S(j + r * NSL);
-        bfly_tab<RL, NSL, false>(v, j, twc + TW::FWD_LAST);
+        bfly_tab<RL, NSL, false>(v, j, tws + TW::FWD_LAST);
       }
       if (k0 == 0) {
         // Column 0 packs two real columns: Z = A + iB with A = F(X[:,0]), B = F(X[:,M]).
@@ -156,7 +199,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
           for (int r = 0; r < RL; ++r) {
             const int l = j + r * NSL;
             const float2 zm = S(l == 0 ? 0 : N - l);
-            const float byl = __ldg(&by[l]);
+            const float byl = (bys[l]);
             const float ia = __fdividef(1.0f, 1.0f + byl);
             const float ib = __fdividef(1.0f, 1.0f + axM + byl);
             const float sp = 0.5f * scale * (ia + ib), sn = 0.5f * scale * (ia - ib);
@@ -168,7 +211,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
         const float axk = __ldg(&ax[live ? k : 0]);
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
-          const float s = __fdividef(scale, 1.0f + axk + __ldg(&by[j + r * NSL]));
+          const float s = __fdividef(scale, 1.0f + axk + (bys[j + r * NSL]));
           v[r] = cscale(v[r], s);
         }
       }
@@ -185,7 +228,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly_tab<R1, RL, true>(v, j, twc + TW::INV_MID);
+        bfly_tab<R1, RL, true>(v, j, tws + TW::INV_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -200,7 +243,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS0) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) v[r] = S(j + r * NS0);
-        bfly_tab<R0, NS0, true>(v, j, twc + TW::INV_LAST);
+        bfly_tab<R0, NS0, true>(v, j, tws + TW::INV_LAST);
         if (live) {
 #pragma unroll
           for (int r = 0; r < R0; ++r) col[(size_t)(j + r * NS0) * M] = v[r];
@@ -287,10 +330,12 @@ __device__ __forceinline__ void fft_rows_smem_inverse(float2* sm, int i, int j, 
       bfly_tab<RL, NSL, true>(v, j, twr + TW::FWD_LAST);
     }
     if (out != nullptr) {
+      float dm = 0.0f;
       if (live && j < NSL) {
 #pragma unroll
-        for (int r = 0; r < RL; ++r) epi->template store<EPI>(out, rowoff + j + r * NSL, v[r]);
+        for (int r = 0; r < RL; ++r) dm = fmaxf(dm, epi->template store<EPI>(out, rowoff + j + r * NSL, v[r]));
       }
+      epi->template finish<EPI>(dm);
       return;
     }
     __syncthreads();
@@ -495,6 +540,7 @@ struct ColEntry {
   int H, tps, G;
   ColFn fn;
   int R0, R1, R2, tw;  // radices (R2 = 1: two stages) and StageTw size
+  size_t smem;         // dynamic shared memory per CTA (col_smem_bytes)
 };
 
 template <class PL, int RF, int RI>
@@ -509,12 +555,13 @@ constexpr RowEntry row_entry() {
                   {row_fwd_fixed_kernel<PL, RF, false, 0>, row_fwd_fixed_kernel<PL, RF, false, 1>,
                    row_fwd_fixed_kernel<PL, RF, false, 2>},
                   {row_inv_fixed_kernel<PL, RI, 0>, row_inv_fixed_kernel<PL, RI, 1>, row_inv_fixed_kernel<PL, RI, 2>,
-                   row_inv_fixed_kernel<PL, RI, 3>, row_inv_fixed_kernel<PL, RI, 4>},
+                   row_inv_fixed_kernel<PL, RI, 3>, row_inv_fixed_kernel<PL, RI, 4>, row_inv_fixed_kernel<PL, RI, 5>},
                   PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE};
 }
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
-  return ColEntry{PL::N, PL::TPS, G, col_fixed_kernel<PL, G, MINB>, PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE};
+  return ColEntry{PL::N,  PL::TPS, G, col_fixed_kernel<PL, G, MINB>, PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE,
+                  col_smem_bytes<PL, G, MINB>()};
 }
 
 // Several entries may share a length: the first is the default, the others are
@@ -672,7 +719,7 @@ cudaError_t fixed_set_attributes() {
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
   }
   for (const ColEntry& c : kCols) {
-    const int s = (int)((size_t)smem_elems(c.H * c.G) * sizeof(float2));
+    const int s = (int)c.smem;
     if ((e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, s))) return e;
   }
   return cudaSuccess;
@@ -705,7 +752,7 @@ cudaError_t fixed_col_solve(int idx, const ImageDesc& d, const Tables& t, float2
   const ColEntry& c = kCols[idx];
   const int M = d.W / 2;
   const int threads = c.G * c.tps;
-  const size_t smem = (size_t)smem_elems(c.H * c.G) * sizeof(float2);
+  const size_t smem = c.smem;
   const int tiles = (M + c.G - 1) / c.G * d.C;
   const float scale = 1.0f / ((float)d.H * (float)d.W);
   return launch_k(d.pdl, c.fn, tiles, threads, smem, stream, M, d.C, t.twH + col_tw_offset(idx), t.ax, t.by, scale,

@@ -8,6 +8,7 @@
 // all.  This entry point gives them the same smoothing with no allocation of
 // any kind (no cudaMalloc/cudaFree, no host heap, no library allocator); the
 // caller still provides the input and output buffers.
+#include <cuda.h>  // CUcontext, CUresult: two driver calls resolved at run time
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,27 +35,73 @@ constexpr size_t kScratchFloats = 2 * kElemsMax + kTableFloats;
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+static_assert(kScratchFloats * sizeof(float) == ILS_NOALLOC_SCRATCH_BYTES, "the header states the array's size");
 
-// Device address of the scratch array on the current device; the first call on a
-// device resolves it (and sets the kernels' shared-memory limits) with that device current.
-ils_status scratch_for_current_device(float** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return ILS_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return ILS_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_addr[dev] == nullptr) {
+// A __device__ array has one instance per CUDA context, and its address is only valid in
+// that context.  The address (and whether the kernels' shared-memory limits have been set,
+// which is also per context) is therefore cached per context, keyed by the context's
+// process-unique identifier: a context made current by a host application, or a primary
+// context re-created after cudaDeviceReset, gets its own set-up.
+struct CtxEntry {
+  unsigned long long id;
+  void* scratch;
+};
+constexpr int kMaxContexts = 64;
+std::mutex g_mu;
+CtxEntry g_ctx[kMaxContexts] = {};
+int g_nctx = 0, g_next = 0;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// The calling thread's current context identifier (driver calls resolved at run time; the
+// library links only the CUDA runtime).
+ils_status current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static const bool resolved = [] {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return ILS_ERR_CUDA;
-    e = set_kernel_attributes();
-    if (e != cudaSuccess) return ILS_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+    return get_current != nullptr && get_id != nullptr;
+  }();
+  if (!resolved) return ILS_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return ILS_ERR_CUDA;
+  if (ctx == nullptr) {
+    // no context bound to this thread yet: a runtime call binds the device's primary context
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return ILS_ERR_CUDA;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return ILS_ERR_CUDA;
   }
-  *out = static_cast<float*>(g_scratch_addr[dev]);
+  return get_id(ctx, id) == CUDA_SUCCESS ? ILS_OK : ILS_ERR_CUDA;
+}
+
+// Device address of the scratch array in the current context; the first call in a context
+// resolves it (and sets the kernels' shared-memory limits) with that context current.
+ils_status scratch_for_current_context(float** out) {
+  unsigned long long id = 0;
+  ils_status s = current_context_id(&id);
+  if (s != ILS_OK) return s;
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (int i = 0; i < g_nctx; ++i) {
+    if (g_ctx[i].id == id) {
+      *out = static_cast<float*>(g_ctx[i].scratch);
+      return ILS_OK;
+    }
+  }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return ILS_ERR_CUDA;
+  if (set_kernel_attributes() != cudaSuccess) return ILS_ERR_CUDA;
+  // the oldest entry makes room when every slot is taken (its context may be gone)
+  const int slot = g_nctx < kMaxContexts ? g_nctx++ : (g_next++ % kMaxContexts);
+  g_ctx[slot] = CtxEntry{id, p};
+  *out = static_cast<float*>(p);
   return ILS_OK;
 }
 
@@ -116,7 +163,7 @@ extern "C" ils_status ils_smooth_noalloc(int H, int W, int C, float lambda, floa
     return ILS_ERR_UNSUPPORTED_SIZE;
 
   float* base = nullptr;
-  ils_status s = scratch_for_current_device(&base);
+  ils_status s = scratch_for_current_context(&base);
   if (s != ILS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;

@@ -29,7 +29,34 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's committed copy groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
+
+// Twiddle tables of a row transform: rt[k] = exp(-2 pi i k / (2M)) for k < M (the real-FFT
+// packing and unpacking) and ft[32 k2 + n1] = exp(-2 pi i n1 k2 / M) (the four-step twiddles,
+// k2-major so a warp reads 32 consecutive entries).  Either straight from the global table
+// (Tables::twW: rt = twW, ft = twW + 2M) or from a CTA's shared-memory copy (stage_row_twiddles:
+// rt = tws, ft = tws + M), which turns the transforms' dependent global loads into
+// shared-memory loads.
+struct TwRef {
+  const float2* rt;
+  const float2* ft;
+};
+
+// CTA-wide 16-byte asynchronous copy of the row twiddles into tws[0 .. 2M) (rt then ft); the
+// caller waits (cp.async.wait_all) and synchronizes the CTA before the first use.
+template <int M>
+__device__ __forceinline__ void stage_row_twiddles(float2* tws, const float2* __restrict__ twW) {
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const int part = i >= M / 2 ? 1 : 0, c = i - part * (M / 2);
+    cp_async16(tws + part * M + 2 * c, twW + part * 2 * M + 2 * c);
+  }
+}
 
 template <int L>
 struct WarpRow {
@@ -40,15 +67,14 @@ struct WarpRow {
   static constexpr int K2P = (L + 31) / 32;  // 32-point transforms per lane (k2 = lane + 32 j < L)
 
   // v: lane holds x[lane + 32 n2]; out[j] (where k2 = lane + 32 j < L): X[k2 + L k1].  buf: this
-  // warp's buffer.  twW[t] = exp(-2 pi i t / (2M)).  L > 32 (a 1920-point row) runs two
-  // 32-point transforms per lane.
+  // warp's buffer.  L > 32 (a 1920-point row) runs two 32-point transforms per lane.
   template <bool INV>
   __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[K2P][32], float2* buf, int lane,
-                                             const float2* __restrict__ twW) {
+                                             const TwRef& tw) {
     dft_reg<L, INV>(v);
 #pragma unroll
     for (int k2 = 1; k2 < L; ++k2) {
-      float2 w = __ldg(&twW[2 * M + 32 * k2 + lane]);  // w_M^{lane k2}, coalesced (Tables::twW)
+      float2 w = tw.ft[32 * k2 + lane];  // w_M^{lane k2}
       if (INV) w.y = -w.y;
       v[k2] = cmul(v[k2], w);
     }
@@ -67,60 +93,47 @@ struct WarpRow {
     __syncwarp();
   }
 
-  // Hermitian unpacking of the packed half spectrum X for the inverse real transform:
-  // v[n2] = Z[k], k = lane + 32 n2, with Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/(2M)}
-  // (X[k] - conj X[M-k]) and Z[0] from slot 0 = (X[0], X[M]).  SPEC: the row is first copied
-  // into buf with 16-byte asynchronous copies (one request per 16 bytes instead of two 8-byte
-  // loads per pair, off the register scoreboard) and unpacked from shared memory.
-  template <bool SPEC>
-  __device__ __forceinline__ static void load_c2r(const float2* __restrict__ X, float2 (&v)[L], float2* buf, int lane,
-                                                  const float2* __restrict__ twW) {
-    static_assert(!SPEC || L % 2 == 0, "16-byte copies of a 32 L-point row need L even");
-    if constexpr (SPEC) {
+  // 16-byte asynchronous copy of the packed spectrum row X into buf (the caller waits).
+  __device__ __forceinline__ static void stage_row(const float2* __restrict__ X, float2* buf, int lane) {
+    static_assert(L % 2 == 0, "16-byte copies of a 32 L-point row need L even");
 #pragma unroll
-      for (int q = 0; q < L / 2; ++q) cp_async16(buf + 2 * (lane + 32 * q), X + 2 * (lane + 32 * q));
-      cp_async_wait_all();
-      __syncwarp();
-#pragma unroll
-      for (int n2 = 0; n2 < L; ++n2) {
-        const int k = lane + 32 * n2;
-        if (k == 0) {
-          const float2 x = buf[0];
-          v[n2] = c2(x.x + x.y, x.x - x.y);
-        } else {
-          const float2 a = buf[k], b = cconj(buf[M - k]);
-          const float2 s = cadd(a, b), d = csub(a, b);
-          const float2 t = cmul(cconj(__ldg(&twW[k])), d);
-          v[n2] = c2(s.x - t.y, s.y + t.x);
-        }
-      }
-      __syncwarp();  // every lane has read buf before the transform writes it
-    } else {
-#pragma unroll
-      for (int n2 = 0; n2 < L; ++n2) {
-        const int k = lane + 32 * n2;
-        if (k == 0) {
-          const float2 x = X[0];
-          v[n2] = c2(x.x + x.y, x.x - x.y);
-        } else {
-          const float2 a = X[k], b = cconj(X[M - k]);
-          const float2 s = cadd(a, b), d = csub(a, b);
-          const float2 t = cmul(cconj(__ldg(&twW[k])), d);
-          v[n2] = c2(s.x - t.y, s.y + t.x);
-        }
-      }
-    }
+    for (int q = 0; q < L / 2; ++q) cp_async16(buf + 2 * (lane + 32 * q), X + 2 * (lane + 32 * q));
   }
 
-  // Inverse real transform of the packed half spectrum X (global row) into buf in natural
-  // order: buf[m] = (x[2m], x[2m+1]) * (the unnormalized factor 2M; the column pass divides).
-  template <bool SPEC>
+  // Hermitian unpacking of the packed half spectrum X for the inverse real transform:
+  // v[n2] = Z[k], k = lane + 32 n2, with Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/(2M)}
+  // (X[k] - conj X[M-k]) and Z[0] from slot 0 = (X[0], X[M]).  X is a global row, or the row
+  // staged in this warp's buffer (stage_row; then every lane has read buf on return).
+  template <bool STAGED>
+  __device__ __forceinline__ static void load_c2r(const float2* __restrict__ X, float2 (&v)[L], float2* buf, int lane,
+                                                  const TwRef& tw) {
+    const float2* src = STAGED ? buf : X;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int k = lane + 32 * n2;
+      if (k == 0) {
+        const float2 x = src[0];
+        v[n2] = c2(x.x + x.y, x.x - x.y);
+      } else {
+        const float2 a = src[k], b = cconj(src[M - k]);
+        const float2 s = cadd(a, b), d = csub(a, b);
+        const float2 t = cmul(cconj(tw.rt[k]), d);
+        v[n2] = c2(s.x - t.y, s.y + t.x);
+      }
+    }
+    if (STAGED) __syncwarp();  // every lane has read buf before the transform writes it
+  }
+
+  // Inverse real transform of the packed half spectrum X (global row, or staged in buf) into
+  // buf in natural order: buf[m] = (x[2m], x[2m+1]) * (the unnormalized factor 2M; the column
+  // pass divides).
+  template <bool STAGED>
   __device__ __forceinline__ static void inverse_row_to_buf(const float2* __restrict__ X, float2* buf, int lane,
-                                                            const float2* __restrict__ twW) {
+                                                            const TwRef& tw) {
     float2 v[L];
-    load_c2r<SPEC>(X, v, buf, lane, twW);
+    load_c2r<STAGED>(X, v, buf, lane, tw);
     float2 out[K2P][32];
-    fft<true>(v, out, buf, lane, twW);
+    fft<true>(v, out, buf, lane, tw);
 #pragma unroll
     for (int j = 0; j < K2P; ++j) {
       if (lane + 32 * j < L) {
@@ -131,31 +144,34 @@ struct WarpRow {
     __syncwarp();
   }
 
-  // Inverse real transform of X straight to global memory through the epilogue (pair
-  // index rowoff + m of the output image).
-  template <int EPI, bool SPEC>
+  // Inverse real transform of X (global row, or staged in buf) straight to global memory
+  // through the epilogue (pair index rowoff + m of the output image).
+  template <int EPI, bool STAGED>
   __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* out,
                                                                size_t rowoff, const Epilogue& epi, float2* buf,
-                                                               int lane, const float2* __restrict__ twW) {
+                                                               int lane, const TwRef& tw) {
     float2 v[L];
-    load_c2r<SPEC>(X, v, buf, lane, twW);
+    load_c2r<STAGED>(X, v, buf, lane, tw);
     float2 res[K2P][32];
-    fft<true>(v, res, buf, lane, twW);
+    fft<true>(v, res, buf, lane, tw);
+    float dm = 0.0f;
 #pragma unroll
     for (int j = 0; j < K2P; ++j) {
       if (lane + 32 * j < L) {
 #pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) epi.template store<EPI>(out, rowoff + lane + 32 * j + L * k1, res[j][k1]);
+        for (int k1 = 0; k1 < 32; ++k1)
+          dm = fmaxf(dm, epi.template store<EPI>(out, rowoff + lane + 32 * j + L * k1, res[j][k1]));
       }
     }
+    epi.template finish<EPI>(dm);
   }
 
   // Forward real transform of r (lane holds r-pairs at m = lane + 32 n2) to the packed
   // half spectrum in the global row dst (slot 0 = (X[0], X[M])).
   __device__ __forceinline__ static void forward_row_to_global(float2 (&v)[L], float2* dst, float2* buf, int lane,
-                                                               const float2* __restrict__ twW) {
+                                                               const TwRef& tw) {
     float2 out[K2P][32];
-    fft<false>(v, out, buf, lane, twW);
+    fft<false>(v, out, buf, lane, tw);
 #pragma unroll
     for (int j = 0; j < K2P; ++j) {
       if (lane + 32 * j < L) {
@@ -164,7 +180,12 @@ struct WarpRow {
       }
     }
     __syncwarp();
-    // pairs (k, M-k), k = 0..M/2
+    pack_to_global(buf, dst, lane, tw);
+  }
+
+  // buf holds Z = FFT_M(r[2m] + i r[2m+1]) in natural order: write the packed half spectrum
+  // of the real row r to dst, pairs (k, M-k) for k = 0..M/2.
+  __device__ __forceinline__ static void pack_to_global(const float2* buf, float2* dst, int lane, const TwRef& tw) {
 #pragma unroll
     for (int q = 0; q < (M / 2 + 1 + 31) / 32; ++q) {
       const int k = lane + 32 * q;
@@ -175,10 +196,10 @@ struct WarpRow {
       } else {
         const float2 a = buf[k], b = buf[M - k];
         const float2 fa = cscale(cadd(a, cconj(b)), 0.5f), fo = cscale(csub(a, cconj(b)), 0.5f);
-        dst[k] = cadd(fa, cmul(__ldg(&twW[k]), c2(fo.y, -fo.x)));
+        dst[k] = cadd(fa, cmul(tw.rt[k], c2(fo.y, -fo.x)));
         if (M - k != k) {
           const float2 fb = cscale(cadd(b, cconj(a)), 0.5f), fq = cscale(csub(b, cconj(a)), 0.5f);
-          dst[M - k] = cadd(fb, cmul(__ldg(&twW[M - k]), c2(fq.y, -fq.x)));
+          dst[M - k] = cadd(fb, cmul(tw.rt[M - k], c2(fq.y, -fq.x)));
         }
       }
     }
@@ -186,16 +207,100 @@ struct WarpRow {
   }
 };
 
+// The shared-mu stencil (Eq. 7 and the divergence of Eq. 9's numerator) of a row-pass CTA,
+// each mu evaluated once; every thread of the CTA calls it (three CTA barriers).  On entry
+// strip row b (rows y0-1 .. y0+nout) is in buffer b in natural pair order; on return output
+// warp w = o+1 (out_live) holds r of output row o in v (lane: pairs m = lane + 32 n2), and
+// buffer w-1 has no other reader left (its scratch for the forward transform).
+//   fr:  global f row of output row o (read when neither staged nor equal to u);
+//   fst: staged f row (STAGE); f_is_u: f equals u^n (the first pass from u^0 = f);
+//   ck:  checkpoint row of output row o or null (receives u^n).
+template <int L, bool STAGE, int PEN>
+__device__ __forceinline__ void stencil_shared(float2 (&v)[L], const MuParams& mp, float2* sm, int w, int lane,
+                                               int nout, bool out_live, bool f_is_u, const float2* fr,
+                                               const float2* fst, float2* ck) {
+  using WR = WarpRow<L>;
+  auto U = [&](int row, int m) -> float2 { return sm[row * WR::BUF + m]; };
+  float2* buf = sm + w * WR::BUF;
+  // S1: warp b <= nout computes mu_y at the boundary between strip rows b and b+1.
+  float2 Y[L];
+  if (w <= nout) {
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = lane + 32 * n2;
+      const float2 a = U(w, m), b = U(w + 1, m);
+      Y[n2] = c2(mu_pen<PEN>(b.x - a.x, mp), mu_pen<PEN>(b.y - a.y, mp));
+    }
+  }
+  if (STAGE) cp_async_wait_all();
+  __syncthreads();
+  // S2: an output warp forms r = f + lambda/2 (div_x mu_x - mu_y(own boundary)) from its own
+  // row, mu_x once per pixel; x neighbours move between lanes by shuffle, so each lane reads
+  // and then overwrites only its own pairs (mu_y of its boundary replaces u in place).
+  if (w <= nout) {
+    float2 cn = buf[lane];
+    const float u_first = __shfl_sync(kFull, cn.x, 0);  // pixel 0: right neighbour of pixel 2M-1
+    float carry = 0.0f;  // mu_x of the pixel left of lane 0's pair
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = lane + 32 * n2;
+      const float2 c = cn;
+      if (n2 + 1 < L) cn = buf[m + 32];
+      if (out_live) {
+        const float nx_in = __shfl_down_sync(kFull, c.x, 1);
+        const float nx_wrap = __shfl_sync(kFull, n2 + 1 < L ? cn.x : u_first, 0);
+        const float nx = lane == 31 ? nx_wrap : nx_in;  // u at pixel 2m+2
+        const float mx_c = mu_pen<PEN>(c.y - c.x, mp);     // mu_x at pixel 2m
+        const float mx_r = mu_pen<PEN>(nx - c.y, mp);      // mu_x at pixel 2m+1
+        const float up = __shfl_up_sync(kFull, mx_r, 1);
+        const float mx_l = lane == 0 ? carry : up;    // mu_x at pixel 2m-1
+        carry = __shfl_sync(kFull, mx_r, 31);
+        const float2 fv = f_is_u ? c : (STAGE ? fst[m] : fr[m]);
+        v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) - Y[n2].x, fv.x),
+                   fmaf(mp.half_lambda, (mx_c - mx_r) - Y[n2].y, fv.y));
+        if (ck != nullptr) ck[m] = c;
+      }
+      buf[m] = Y[n2];
+    }
+    // lane 0's first pair: the left neighbour of pixel 0 is pixel 2M-1, finished last
+    if (out_live && lane == 0) v[0].x = fmaf(mp.half_lambda, carry, v[0].x);
+  }
+  __syncthreads();
+  // S3: add mu_y of the boundary above (written by warp w-1); that row buffer has no other
+  // reader now, so it becomes this warp's scratch for the forward transform.
+  if (out_live) {
+    const float2* above = sm + (w - 1) * WR::BUF;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const float2 t = above[lane + 32 * n2];
+      v[n2] = c2(fmaf(mp.half_lambda, t.x, v[n2].x), fmaf(mp.half_lambda, t.y, v[n2].y));
+    }
+    __syncwarp();
+  }
+}
+
+// Copies the u^0 rows of a first row pass into the strip buffers (16-byte asynchronous copies
+// when the row is 16-byte aligned; the caller waits and synchronizes).
+template <int L>
+__device__ __forceinline__ void load_u0_row(const float2* __restrict__ src, float2* buf, int lane) {
+  if (L % 2 == 0 && (reinterpret_cast<size_t>(src) & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < L / 2; ++q) cp_async16(buf + 2 * (lane + 32 * q), src + 2 * (lane + 32 * q));
+  } else {
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) buf[lane + 32 * n2] = src[lane + 32 * n2];
+  }
+}
+
 // Fused row pass: CTA = ROWS + 2 warps over rows y0-1 .. y0+ROWS (periodic); warp w holds
 // strip row w in buffer w.  FIRST: u^0 rows are read from u0 (or f); otherwise rebuilt by the
 // inverse transform of spec_in.  Then warp o+1 computes r for output row o and transforms it.
-// SHARED: each mu is evaluated once (mu_y of a row boundary passed between warps through
-// shared memory, mu_x between lanes by shuffle; three CTA barriers); otherwise every warp
-// evaluates the mu of all four gradients of each of its pixels and of the left neighbour
-// (two barriers, no cross-warp data beyond the strip rows).
+// SHARED: each mu is evaluated once (stencil_shared); otherwise every warp evaluates the mu
+// of all four gradients of each of its pixels and of the left neighbour (two barriers, no
+// cross-warp data beyond the strip rows).
 // STAGE (with SHARED): the f rows of the output rows are copied to shared memory
 // asynchronously at the start (behind the inverse transforms) instead of being loaded in
-// the stencil.
+// the stencil; not when f is the u^0 of a first pass (the strip rows already hold it).
 template <int L, int ROWS, bool FIRST, bool STAGE, bool SHARED, int PEN, int MINB, bool SPEC>
 __global__ void __launch_bounds__((ROWS + 2) * 32, MINB)
 row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
@@ -215,9 +320,23 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   auto U = [&](int row, int m) -> float2 { return sm[row * WR::BUF + m]; };
   const int o = w - 1;  // output row of this warp
   const bool out_live = o >= 0 && o < nout;
+  const bool f_is_u = FIRST && (u0 == nullptr || u0 == f);  // r's f term is the strip row itself
+  const size_t orow = ch * plane + (size_t)(y0 + max(o, 0)) * M;  // pair offset of the output row
   float2* fst = sm + (ROWS + 2) * WR::BUF + max(o, 0) * M;  // staged f row (STAGE)
-  if (STAGE && out_live && mp.half_lambda != 0.0f) {
-    const float2* src = reinterpret_cast<const float2*>(f) + ch * plane + (size_t)(y0 + o) * M;
+  float2* tws = sm + (ROWS + 2) * WR::BUF + (STAGE ? ROWS * M : 0);  // the CTA's twiddle tables
+  const TwRef tw{tws, tws + M};
+  stage_row_twiddles<M>(tws, twW);  // constant tables: before the wait on the previous grid
+  griddep_wait();  // f is never written by this library's kernels; the spectrum is
+  float2 v[L];
+  const int yy = wrap_row(y0 - 1 + w, H);
+  if (w < nout + 2) {
+    if (FIRST) load_u0_row<L>(reinterpret_cast<const float2*>(u0 != nullptr ? u0 : f) + ch * plane + (size_t)yy * M,
+                              buf, lane);
+    else if (SPEC) WR::stage_row(spec_in + ch * plane + (size_t)yy * M, buf, lane);
+  }
+  cp_async_commit();
+  if (STAGE && out_live && mp.half_lambda != 0.0f && !f_is_u) {  // waited for in the stencil
+    const float2* src = reinterpret_cast<const float2*>(f) + orow;
     if ((reinterpret_cast<size_t>(src) & 15) == 0) {
 #pragma unroll
       for (int q = 0; q < M / 64; ++q) cp_async16(fst + 2 * (lane + 32 * q), src + 2 * (lane + 32 * q));
@@ -226,30 +345,21 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
       for (int n2 = 0; n2 < L; ++n2) fst[lane + 32 * n2] = src[lane + 32 * n2];
     }
   }
-  griddep_wait();  // f is never written by this library's kernels; the spectrum is
-  if (w < nout + 2) {
-    const int yy = wrap_row(y0 - 1 + w, H);
-    if (FIRST) {
-      const float2* src = reinterpret_cast<const float2*>(u0 != nullptr ? u0 : f) + ch * plane + (size_t)yy * M;
-#pragma unroll
-      for (int n2 = 0; n2 < L; ++n2) buf[lane + 32 * n2] = src[lane + 32 * n2];
-    } else {
-      WR::template inverse_row_to_buf<SPEC>(spec_in + ch * plane + (size_t)yy * M, buf, lane, twW);
-    }
-  }
+  cp_async_commit();
+  cp_async_wait_group<1>();  // the twiddles and this thread's strip-row copies have landed
   __syncthreads();
-  float2 v[L];
+  if (!FIRST && w < nout + 2) WR::template inverse_row_to_buf<SPEC>(spec_in + ch * plane + (size_t)yy * M, buf, lane, tw);
+  __syncthreads();
   if (mp.half_lambda == 0.0f) {  // lambda = 0 (or a plain row FFT): r = f
     if (out_live) {
-      const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
-      const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
+      const float2* fr = reinterpret_cast<const float2*>(f) + orow;
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) {
         const int m = lane + 32 * n2;
         v[n2] = fr[m];
-        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = U(w, m);
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[orow + m] = U(w, m);
       }
-      WR::forward_row_to_global(v, spec_out + rowoff, buf, lane, twW);
+      WR::forward_row_to_global(v, spec_out + orow, buf, lane, tw);
     }
     return;
   }
@@ -257,8 +367,7 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
     // Stencil (Eq. 7 and the divergence of Eq. 9's numerator) per pixel pair from the
     // strip rows alone: mu of the pair's four gradients and of the left neighbour's.
     if (out_live) {
-      const size_t rowoff = ch * plane + (size_t)(y0 + o) * M;
-      const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
+      const float2* fr = reinterpret_cast<const float2*>(f) + orow;
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) {
         const int m = lane + 32 * n2;
@@ -277,71 +386,17 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
         const float my1d = mu_pen<PEN>(dn.y - c.y, mp);
         v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x),
                    fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
-        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[orow + m] = c;
       }
     }
     __syncthreads();
-    if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+    if (out_live) WR::forward_row_to_global(v, spec_out + orow, buf, lane, tw);
     return;
-  }
-  // Stencil (Eq. 7 and the divergence of Eq. 9's numerator), each mu evaluated once:
-  // S1: warp b <= nout computes mu_y at the boundary between strip rows b and b+1.
-  float2 Y[L];
-  if (w <= nout) {
-#pragma unroll
-    for (int n2 = 0; n2 < L; ++n2) {
-      const int m = lane + 32 * n2;
-      const float2 a = U(w, m), b = U(w + 1, m);
-      Y[n2] = c2(mu_pen<PEN>(b.x - a.x, mp), mu_pen<PEN>(b.y - a.y, mp));
-    }
-  }
-  if (STAGE) cp_async_wait_all();
-  __syncthreads();
-  // S2: an output warp forms r = f + lambda/2 (div_x mu_x - mu_y(own boundary)) from its own
-  // row, mu_x once per pixel; x neighbours move between lanes by shuffle, so each lane reads
-  // and then overwrites only its own pairs (mu_y of its boundary replaces u in place).
-  if (w <= nout) {
-    const size_t rowoff = ch * plane + (size_t)(y0 + max(o, 0)) * M;
-    const float2* fr = reinterpret_cast<const float2*>(f) + rowoff;
-    float2 cn = buf[lane];
-    const float u_first = __shfl_sync(kFull, cn.x, 0);  // pixel 0: right neighbour of pixel 2M-1
-    float carry = 0.0f;  // mu_x of the pixel left of lane 0's pair
-#pragma unroll
-    for (int n2 = 0; n2 < L; ++n2) {
-      const int m = lane + 32 * n2;
-      const float2 c = cn;
-      if (n2 + 1 < L) cn = buf[m + 32];
-      if (out_live) {
-        const float nx_in = __shfl_down_sync(kFull, c.x, 1);
-        const float nx_wrap = __shfl_sync(kFull, n2 + 1 < L ? cn.x : u_first, 0);
-        const float nx = lane == 31 ? nx_wrap : nx_in;  // u at pixel 2m+2
-        const float mx_c = mu_pen<PEN>(c.y - c.x, mp);     // mu_x at pixel 2m
-        const float mx_r = mu_pen<PEN>(nx - c.y, mp);      // mu_x at pixel 2m+1
-        const float up = __shfl_up_sync(kFull, mx_r, 1);
-        const float mx_l = lane == 0 ? carry : up;    // mu_x at pixel 2m-1
-        carry = __shfl_sync(kFull, mx_r, 31);
-        const float2 fv = STAGE ? fst[m] : fr[m];
-        v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) - Y[n2].x, fv.x),
-                   fmaf(mp.half_lambda, (mx_c - mx_r) - Y[n2].y, fv.y));
-        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[rowoff + m] = c;
-      }
-      buf[m] = Y[n2];
-    }
-    // lane 0's first pair: the left neighbour of pixel 0 is pixel 2M-1, finished last
-    if (out_live && lane == 0) v[0].x = fmaf(mp.half_lambda, carry, v[0].x);
-  }
-  __syncthreads();
-  // S3: add mu_y of the boundary above (written by warp w-1); that row buffer has no other
-  // reader now, so it becomes this warp's scratch for the forward transform.
-  if (out_live) {
-    const float2* above = sm + (w - 1) * WR::BUF;
-#pragma unroll
-    for (int n2 = 0; n2 < L; ++n2) {
-      const float2 t = above[lane + 32 * n2];
-      v[n2] = c2(fmaf(mp.half_lambda, t.x, v[n2].x), fmaf(mp.half_lambda, t.y, v[n2].y));
-    }
-    __syncwarp();
-    WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, sm + (w - 1) * WR::BUF, lane, twW);
+  } else {
+    stencil_shared<L, STAGE, PEN>(v, mp, sm, w, lane, nout, out_live, f_is_u,
+                                  reinterpret_cast<const float2*>(f) + orow, fst,
+                                  u_ckpt != nullptr ? reinterpret_cast<float2*>(u_ckpt) + orow : nullptr);
+    if (out_live) WR::forward_row_to_global(v, spec_out + orow, sm + (w - 1) * WR::BUF, lane, tw);
   }
 }
 
@@ -351,7 +406,6 @@ __global__ void __launch_bounds__(ROWS * 32)
 row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u,
                     Epilogue epi) {
   griddep_launch();
-  griddep_wait();
   using WR = WarpRow<L>;
   constexpr int M = WR::M;
   extern __shared__ float2 sm[];
@@ -359,10 +413,16 @@ row_warp_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restr
   const int strips = (H + ROWS - 1) / ROWS;
   const int ch = blockIdx.x / strips;
   const int y = (blockIdx.x - ch * strips) * ROWS + w;
+  const size_t off = ch * (size_t)H * M + (size_t)min(y, H - 1) * M;
+  float2* tws = sm + ROWS * WR::BUF;
+  stage_row_twiddles<M>(tws, twW);
+  griddep_wait();
+  if (SPEC && y < H) WR::stage_row(spec + off, sm + w * WR::BUF, lane);
+  cp_async_wait_all();
+  __syncthreads();
   if (y >= H) return;  // warp-uniform; no CTA barrier below
-  const size_t off = ch * (size_t)H * M + (size_t)y * M;
-  WR::template inverse_row_to_global<EPI, SPEC>(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF, lane,
-                                          twW);
+  WR::template inverse_row_to_global<EPI, SPEC>(spec + off, reinterpret_cast<float2*>(u), off, epi, sm + w * WR::BUF,
+                                                lane, TwRef{tws, tws + M});
 }
 
 // Reverse-mode row pass of step n (the adjoint of Algorithm 1's iteration; see the generic
@@ -399,9 +459,14 @@ row_warp_adj_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   const int nout = min(ROWS, H - y0);
   const size_t plane = (size_t)H * M;
   float2* buf = sm + w * WR::BUF;
+  float2* tws = sm + (ROWS + 2) * WR::BUF;
+  const TwRef tw{tws, tws + M};
+  stage_row_twiddles<M>(tws, twW);
+  cp_async_wait_all();
+  __syncthreads();
   if (w < nout + 2)
     WR::template inverse_row_to_buf<false>(spec_in + ch * plane + (size_t)wrap_row(y0 - 1 + w, H) * M, buf, lane,
-                                           twW);
+                                           tw);
   __syncthreads();
   const int o = w - 1;
   const bool out_live = o >= 0 && o < nout;
@@ -449,7 +514,7 @@ row_warp_adj_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   }
   if (last) return;  // kernel-uniform
   __syncthreads();   // every warp has read the r rows; buffer w becomes warp w's scratch
-  if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, twW);
+  if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, tw);
 }
 
 using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
@@ -465,8 +530,10 @@ struct WarpRowEntry {
 
 // STAGE only where the staged rows still leave room for two CTAs per SM.  MINB: CTAs per SM
 // the register allocation must allow (2 at 256 threads = 128 registers per thread).
-// SPEC: the inverse transforms stage their spectrum rows in shared memory (load_c2r).
-template <int L, int RF, int RI, bool STAGE, bool SHARED, int MINB = ((RF + 2) * 32 <= 256 ? 2 : 1), bool SPEC = false>
+// SPEC / SPEC_I: the row passes / the final inverse pass stage their spectrum rows in shared
+// memory with 16-byte asynchronous copies (load_c2r from buf) instead of loading them directly.
+template <int L, int RF, int RI, bool STAGE, bool SHARED, int MINB = ((RF + 2) * 32 <= 256 ? 2 : 1), bool SPEC = false,
+          bool SPEC_I = SPEC>
 constexpr WarpRowEntry warp_entry() {
   static_assert(SHARED || !STAGE, "f staging is part of the shared-mu stencil");
   return WarpRowEntry{32 * L,
@@ -480,26 +547,28 @@ constexpr WarpRowEntry warp_entry() {
                       {row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 0, MINB, SPEC>,
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 1, MINB, SPEC>,
                        row_warp_fwd_kernel<L, RF, false, STAGE, SHARED, 2, MINB, SPEC>},
-                      {row_warp_inv_kernel<L, RI, 0, SPEC>, row_warp_inv_kernel<L, RI, 1, SPEC>,
-                       row_warp_inv_kernel<L, RI, 2, SPEC>, row_warp_inv_kernel<L, RI, 3, SPEC>,
-                       row_warp_inv_kernel<L, RI, 4, SPEC>},
+                      {row_warp_inv_kernel<L, RI, 0, SPEC_I>, row_warp_inv_kernel<L, RI, 1, SPEC_I>,
+                       row_warp_inv_kernel<L, RI, 2, SPEC_I>, row_warp_inv_kernel<L, RI, 3, SPEC_I>,
+                       row_warp_inv_kernel<L, RI, 4, SPEC_I>, row_warp_inv_kernel<L, RI, 5, SPEC_I>},
                       {row_warp_adj_kernel<L, RF, 0, MINB>, row_warp_adj_kernel<L, RF, 1, MINB>}};
 }
 
-// The first entry of a length is its default; the others are autotune alternatives.
+// The first entry of a length is its default; the others are autotune alternatives.  Every
+// CTA also holds its 2M-entry twiddle table (16 B per complex point of a row), which is what
+// limits the 1920-wide rows to the per-pair stencil without f staging at two CTAs per SM.
 const WarpRowEntry kWarpRows[] = {
     warp_entry<4, 14, 16, true, true>(),     // W = 256
     warp_entry<8, 14, 16, true, true>(),     // W = 512
     warp_entry<10, 14, 16, true, true>(),    // W = 640
     warp_entry<20, 6, 8, true, true>(),      // W = 1280
-    warp_entry<30, 6, 8, true, true, 2, true>(),  // W = 1920 (spectrum rows staged: 2 % faster at 1080p)
+    warp_entry<30, 6, 8, false, false, 2, false, true>(),  // W = 1920: per-pair stencil, inverse pass staged
     warp_entry<32, 6, 8, false, true>(),     // W = 2048
-    warp_entry<30, 14, 8, false, true>(),    // W = 1920, taller strips
-    warp_entry<30, 6, 8, false, false>(),    // W = 1920, per-pair stencil
+    warp_entry<30, 6, 8, false, false, 2, true>(),   // W = 1920, row passes staged too
+    warp_entry<30, 14, 8, false, false, 1, false, true>(),  // W = 1920, taller strips (16-warp CTAs)
+    warp_entry<30, 6, 6, false, false, 2, false, true>(),   // W = 1920, 6-row inverse CTAs (3 per SM)
+    warp_entry<30, 6, 8, false, true, 2, false, true>(),    // W = 1920, shared-mu stencil
     warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
     warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
-    warp_entry<30, 6, 8, false, false, 3>(), // W = 1920, per-pair stencil, 3 CTAs per SM (84 registers)
-    warp_entry<30, 6, 8, true, true>(),      // W = 1920, spectrum rows read straight from global memory
 };
 
 }  // namespace
@@ -514,15 +583,15 @@ int warp_row_variants(int M, int* idx, int max) {
 cudaError_t warp_set_attributes() {
   cudaError_t e;
   for (const WarpRowEntry& r : kWarpRows) {
-    const int sf = ((r.rows_fwd + 2) * r.buf + r.stage) * (int)sizeof(float2);
-    const int si = r.rows_inv * r.buf * (int)sizeof(float2);
+    const int sf = ((r.rows_fwd + 2) * r.buf + r.stage + 2 * r.M) * (int)sizeof(float2);
+    const int si = (r.rows_inv * r.buf + 2 * r.M) * (int)sizeof(float2);
     for (int pen = 0; pen < kPenalties; ++pen) {
       if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
     for (int m = 0; m < kEpilogues; ++m)
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
-    const int sa = (r.rows_fwd + 2) * r.buf * (int)sizeof(float2);
+    const int sa = ((r.rows_fwd + 2) * r.buf + 2 * r.M) * (int)sizeof(float2);
     for (int pen = 0; pen < 2; ++pen)
       if ((e = cudaFuncSetAttribute(r.adj[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sa))) return e;
   }
@@ -534,7 +603,7 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
                              cudaStream_t stream) {
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage) * sizeof(float2);
+  const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage + 2 * r.M) * sizeof(float2);
   const int pen = mp.pen;
   FwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
   return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
@@ -546,7 +615,7 @@ cudaError_t warp_row_adjoint(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   if (mp.pen != 0 && mp.pen != 1) return cudaErrorInvalidValue;
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  const size_t smem = (size_t)(r.rows_fwd + 2) * r.buf * sizeof(float2);
+  const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + 2 * r.M) * sizeof(float2);
   return launch_k(d.pdl, r.adj[mp.pen], blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, spec_in, u_n,
                   fbar, (int)fbar_first, gu0, (int)last, spec_out);
 }
@@ -555,7 +624,7 @@ cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const
                              cudaStream_t stream, const Epilogue& epi) {
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
-  const size_t smem = (size_t)r.rows_inv * r.buf * sizeof(float2);
+  const size_t smem = ((size_t)r.rows_inv * r.buf + 2 * r.M) * sizeof(float2);
   return launch_k(d.pdl, r.inv[epi.mode], blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u, epi);
 }
 

@@ -166,7 +166,8 @@ class Plan:
 
     def smooth_checkpointed(self, f: torch.Tensor, out: torch.Tensor | None = None,
                             u0: torch.Tensor | None = None, stream=None):
-        """Forward pass that also returns the iterates u^0..u^{N-1} (N x C x H x W) for backward()."""
+        """Forward pass that also returns the iterates u^0..u^{N-1} (N x C x H x W, caller-owned)
+        for backward_ckpt()."""
         f3 = self._as3d(f)
         _check_image(f3, self.shape, "f")
         if out is None:
@@ -180,18 +181,37 @@ class Plan:
         _lib.check(st, "ils_smooth_checkpointed")
         return out, ckpt
 
-    def backward(self, ckpt: torch.Tensor, grad_u: torch.Tensor, separate_u0: bool = False, stream=None):
-        """dL/df (and dL/du^0 if separate_u0) from dL/du^N and the forward's checkpoints."""
+    def backward_ckpt(self, ckpt: torch.Tensor, grad_u: torch.Tensor, separate_u0: bool = False, stream=None):
+        """dL/df (and dL/du^0 if separate_u0) from dL/du^N and caller-owned checkpoints
+        (ils_backward_ckpt)."""
         _check_image(self._as3d(grad_u), self.shape, "grad_u")
         if ckpt.dtype != torch.float32 or not ckpt.is_cuda or not ckpt.is_contiguous() or \
                 tuple(ckpt.shape) != (max(self.N, 1),) + self.shape:
             raise ValueError("ckpt must come from smooth_checkpointed of this plan")
         grad_f = torch.empty_like(grad_u)
         grad_u0 = torch.empty_like(grad_u) if separate_u0 else None
-        st = _lib.lib().ils_backward(self._h, ckpt.data_ptr(), grad_u.data_ptr(), grad_f.data_ptr(),
-                                     0 if grad_u0 is None else grad_u0.data_ptr(), _stream_ptr(stream))
-        _lib.check(st, "ils_backward")
+        st = _lib.lib().ils_backward_ckpt(self._h, ckpt.data_ptr(), grad_u.data_ptr(), grad_f.data_ptr(),
+                                          0 if grad_u0 is None else grad_u0.data_ptr(), _stream_ptr(stream))
+        _lib.check(st, "ils_backward_ckpt")
         return (grad_f, grad_u0) if separate_u0 else grad_f
+
+    def set_checkpointing(self, on: bool) -> None:
+        """Plan-owned checkpoints (ils_set_checkpointing): later smooth() calls keep their
+        iterates for backward()."""
+        _lib.check(_lib.lib().ils_set_checkpointing(self._h, 1 if on else 0), "ils_set_checkpointing")
+
+    def backward(self, f: torch.Tensor, grad_u: torch.Tensor, grad_f: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+        """dL/df through the last smooth() of this f made with checkpointing on (ils_backward)."""
+        _check_image(self._as3d(f), self.shape, "f")
+        _check_image(self._as3d(grad_u), self.shape, "grad_u")
+        if grad_f is None:
+            grad_f = torch.empty_like(grad_u)
+        _check_image(self._as3d(grad_f), self.shape, "grad_f")
+        st = _lib.lib().ils_backward(self._h, f.data_ptr(), grad_u.data_ptr(), grad_f.data_ptr(),
+                                     _stream_ptr(stream))
+        _lib.check(st, "ils_backward")
+        return grad_f
 
     def set_profiling(self, on: bool) -> None:
         _lib.check(_lib.lib().ils_set_profiling(self._h, 1 if on else 0), "ils_set_profiling")
@@ -299,9 +319,9 @@ class ILSFunction(torch.autograd.Function):
         (ckpt,) = ctx.saved_tensors
         g = grad_u.contiguous()
         if ctx.has_u0:
-            gf, gu0 = ctx.plan.backward(ckpt, g, separate_u0=True)
+            gf, gu0 = ctx.plan.backward_ckpt(ckpt, g, separate_u0=True)
             return gf, None, gu0
-        return ctx.plan.backward(ckpt, g), None, None
+        return ctx.plan.backward_ckpt(ckpt, g), None, None
 
 
 def ils_function(f: torch.Tensor, plan: Plan, u0: torch.Tensor | None = None) -> torch.Tensor:

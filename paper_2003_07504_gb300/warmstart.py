@@ -165,12 +165,28 @@ class WarmSmoother:
         self.shape = (C, H, W)
 
     def smooth(self, f: torch.Tensor, out: torch.Tensor | None = None):
+        """(u, fallback taken, delta): waits for the call's stream to report the decision."""
         out = torch.empty_like(f) if out is None else out
         fb = ctypes.c_int()
         d = ctypes.c_float()
         _lib.check(_lib.lib().ils_warm_smooth(self._h, f.data_ptr(), out.data_ptr(), ctypes.byref(fb), ctypes.byref(d),
                                               _stream_ptr()), "ils_warm_smooth")
-        return out, bool(fb.value), float(d.value)
+        return out, fb.value == _lib.ILS_ERR_FALLBACK_TAKEN, float(d.value)
+
+    def smooth_async(self, f: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """u without waiting: the fallback decision is taken on the device; result() reads it
+        once the stream has been synchronized."""
+        out = torch.empty_like(f) if out is None else out
+        _lib.check(_lib.lib().ils_warm_smooth(self._h, f.data_ptr(), out.data_ptr(), None, None, _stream_ptr()),
+                   "ils_warm_smooth")
+        return out
+
+    def result(self):
+        """(fallback taken, delta) of the last call (after its stream has been synchronized)."""
+        fb = ctypes.c_int()
+        d = ctypes.c_float()
+        _lib.check(_lib.lib().ils_warm_result(self._h, ctypes.byref(fb), ctypes.byref(d)), "ils_warm_result")
+        return fb.value == _lib.ILS_ERR_FALLBACK_TAKEN, float(d.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -282,20 +298,36 @@ def load_params(path: str = DEFAULT_WEIGHTS) -> np.ndarray:
 
 def converged_ils(plan_factory, f: torch.Tensor, max_iters: int = 1000, tol: float = 1e-6, chunk: int = 50):
     """ILS from f iterated until max|u^{n+1} - u^n| < tol (or max_iters): the 'converged ILS'
-    reference of the equal-error comparison.  Runs in chunks of `chunk` iterations."""
+    reference of the equal-error comparison.  Runs in chunks of `chunk` iterations.
+    Returns (u, iterations, last change max|u^{n+1} - u^n|)."""
     C, H, W = f.shape
     with plan_factory(H, W, C, chunk) as big, plan_factory(H, W, C, 1) as one:
         u = f.clone()
         done = 0
+        change = float("inf")
         while done < max_iters:
             u = big.smooth(f, u0=u)
             done += chunk
             nxt = one.smooth(f, u0=u)
-            if float((nxt - u).abs().max()) < tol:
-                return nxt, done + 1
-            u = nxt
+            change = float((nxt - u).abs().max())
             done += 1
-        return u, done
+            u = nxt
+            if change < tol:
+                break
+        return u, done, change
+
+
+def stationarity_residual(u: torch.Tensor, f: torch.Tensor, lam: float, p: float, eps: float) -> float:
+    """max |(u - f) + (lambda/2) sum_* grad_*^T phi_p'(grad_* u)| over the image, in FP64 on the host:
+    half the gradient of Eq. 1 (periodic forward differences), zero at a stationary point."""
+    uu = u.detach().double().cpu().numpy()
+    ff = f.detach().double().cpu().numpy()
+    res = uu - ff
+    for ax in (-1, -2):
+        g = np.roll(uu, -1, axis=ax) - uu
+        d = p * g * (g * g + eps) ** (p / 2.0 - 1.0)
+        res += 0.5 * lam * (np.roll(d, 1, axis=ax) - d)
+    return float(np.abs(res).max())
 
 
 def main(argv=None):

@@ -26,9 +26,50 @@ def test_binding_signatures_cover_the_header():
     assert set(declared_symbols()) <= set(_lib.SIGNATURES), set(declared_symbols()) - set(_lib.SIGNATURES)
 
 
+# The boundary calls of the hot path: plans (Eq. 11's c), Algorithm 1 from f or from a given
+# u^0, uneven-frame batches, plan-owned checkpoints and the adjoint by f, status names.
+BOUNDARY = {
+    "ils_plan_create": 8, "ils_plan_destroy": 1, "ils_smooth": 4, "ils_smooth_from": 5,
+    "ils_smooth_batched": 3, "ils_set_checkpointing": 2, "ils_backward": 5, "ils_status_string": 1,
+    "ils_plan_c": 1,
+}
+
+
+def test_header_declares_the_boundary_calls():
+    import os
+    import re
+    from tests._util import ROOT
+    text = open(os.path.join(ROOT, "include", "ils.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for name, nargs in BOUNDARY.items():
+        m = re.search(r"\b" + name + r"\s*\(([^)]*)\)\s*;", text)
+        assert m is not None, f"{name} is not declared"
+        assert len(m.group(1).split(",")) == nargs, (name, m.group(1))
+    assert re.search(r"ILS_ERR_FALLBACK_TAKEN\s*=\s*6", text)
+
+
+def test_boundary_calls_validate_without_a_gpu(L):
+    assert L.ils_set_checkpointing(None, 1) == 1
+    assert L.ils_backward(None, None, None, None, None) == 1
+    assert L.ils_backward_ckpt(None, None, None, None, None, None) == 1
+
+
+def test_noalloc_source_calls_no_allocator():
+    """The allocation-free entry point's translation unit names no allocating routine."""
+    import os
+    import re
+    from tests._util import ROOT
+    src = open(os.path.join(ROOT, "paper_2003_07504_gb300", "csrc", "ils_noalloc.cu")).read()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    for bad in (r"\bcudaMalloc\w*", r"\bcudaFree\w*", r"\bcuMem\w*", r"\bmalloc\s*\(", r"\bcalloc\s*\(",
+                r"\brealloc\s*\(", r"\bnew\b", r"\bstd::vector\b", r"\bstd::string\b", r"\bdev_alloc\b"):
+        assert re.search(bad, code) is None, bad
+
+
 def test_status_strings(L):
     for code, name in ((0, b"ILS_OK"), (1, b"ILS_ERR_INVALID_ARG"), (2, b"ILS_ERR_UNSUPPORTED_SIZE"),
-                       (3, b"ILS_ERR_OOM"), (4, b"ILS_ERR_CUDA"), (5, b"ILS_ERR_TIMEOUT")):
+                       (3, b"ILS_ERR_OOM"), (4, b"ILS_ERR_CUDA"), (5, b"ILS_ERR_TIMEOUT"),
+                       (6, b"ILS_ERR_FALLBACK_TAKEN")):
         assert L.ils_status_string(code) == name
 
 

@@ -40,7 +40,7 @@ def gpu_grad(ils, f, w, lam=1.0, p=0.8, N=4, u0=None, separate=False):
         plain = plan.smooth(ft, u0=u0t)
         torch.cuda.synchronize()
         assert torch.equal(u, plain)   # checkpointing does not change the forward
-        out = plan.backward(ck, torch.from_numpy(w).cuda(), separate_u0=separate)
+        out = plan.backward_ckpt(ck, torch.from_numpy(w).cuda(), separate_u0=separate)
         torch.cuda.synchronize()
         if separate:
             return out[0].cpu().numpy(), out[1].cpu().numpy()
@@ -145,6 +145,107 @@ def test_welsch_adjoint_matches_fp64_reverse_mode(ils, H, W, lam, gamma, N):
     w = synth.random_field(f.shape, seed=9)
     with ils.Plan(H, W, 1, lam, N=N, penalty="welsch", gamma=gamma) as plan:
         u, ck = plan.smooth_checkpointed(torch.from_numpy(f).cuda())
-        g = plan.backward(ck, torch.from_numpy(w).cuda()).cpu().numpy()
+        g = plan.backward_ckpt(ck, torch.from_numpy(w).cuda()).cpu().numpy()
     want = O.ils_backward_welsch(f[0].astype(np.float64), w[0].astype(np.float64), lam, gamma, N)
     assert rel_err(g[0], want) <= REL_TOL
+
+
+def test_plan_owned_checkpoints_and_backward_by_f(ils):
+    """ils_set_checkpointing + ils_smooth + ils_backward(plan, f, grad_u, grad_f): the gradient
+    of the last checkpointed call, checked against the FP64 reverse mode."""
+    import torch
+    from paper_2003_07504_gb300 import _lib
+    C, H, W, lam, p, N = 2, 45, 64, 1.0, 0.8, 4
+    f = synth.preset_image(H, W, C, "small", 5)
+    w = synth.random_field(f.shape, seed=8)
+    want = np.stack([O.ils_backward(f[c].astype(np.float64), w[c].astype(np.float64), lam, p, 1e-4, N)
+                     for c in range(C)])
+    with ils.Plan(H, W, C, lam, p, 1e-4, N) as plan:
+        ft = torch.from_numpy(f).cuda()
+        other = ft.clone()
+        wt = torch.from_numpy(w).cuda()
+        with pytest.raises(_lib.ILSError):     # no checkpoints yet
+            plan.backward(ft, wt)
+        plan.set_checkpointing(True)
+        plan.smooth(other)
+        u = plan.smooth(ft)                     # the last checkpointed call: f
+        ref = ils.Plan(H, W, C, lam, p, 1e-4, N).smooth(ft)
+        torch.cuda.synchronize()
+        assert torch.equal(u, ref)              # checkpointing does not change the forward
+        g = plan.backward(ft, wt).cpu().numpy()
+        with pytest.raises(_lib.ILSError):     # another f than the last checkpointed call
+            plan.backward(other, wt)
+        plan.set_checkpointing(False)
+        with pytest.raises(_lib.ILSError):
+            plan.backward(ft, wt)
+    assert rel_err(g, want) <= 1e-4
+
+
+def test_c99_program_backward_through_the_abi(ils, tmp_path):
+    """A C99 program (CUDA runtime API for device memory, no torch) calls ils_set_checkpointing,
+    ils_smooth and ils_backward through libils.so; its dL/df matches the FP64 reverse mode."""
+    import os
+    import shutil
+    import subprocess
+    from paper_2003_07504_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if cc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime_api.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    C, H, W, lam, p, N = 1, 30, 48, 1.0, 0.8, 3
+    f = synth.preset_image(H, W, C, "small", 11)
+    w = synth.random_field(f.shape, seed=12)
+    f.astype(np.float32).tofile(tmp_path / "f.bin")
+    w.astype(np.float32).tofile(tmp_path / "g.bin")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib_dir = os.path.dirname(_lib.LIB_PATH)
+    src = tmp_path / "bwd.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stdlib.h>
+#include <cuda_runtime_api.h>
+#include "ils.h"
+#define CK(x) do { if ((x) != 0) { fprintf(stderr, "failed: %s\n", #x); return 1; } } while (0)
+int main(int argc, char** argv) {
+  (void)argc;
+  const int H = atoi(argv[1]), W = atoi(argv[2]), C = atoi(argv[3]), N = atoi(argv[4]);
+  const float lam = (float)atof(argv[5]), p = (float)atof(argv[6]);
+  const size_t n = (size_t)C * H * W;
+  float* hf = malloc(n * sizeof(float));
+  float* hg = malloc(n * sizeof(float));
+  FILE* fp = fopen(argv[7], "rb"); if (!fp || fread(hf, sizeof(float), n, fp) != n) return 2; fclose(fp);
+  fp = fopen(argv[8], "rb"); if (!fp || fread(hg, sizeof(float), n, fp) != n) return 3; fclose(fp);
+  float *f, *u, *g, *gf;
+  CK(cudaMalloc((void**)&f, n * 4)); CK(cudaMalloc((void**)&u, n * 4));
+  CK(cudaMalloc((void**)&g, n * 4)); CK(cudaMalloc((void**)&gf, n * 4));
+  CK(cudaMemcpy(f, hf, n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(g, hg, n * 4, cudaMemcpyHostToDevice));
+  ils_plan* plan = NULL;
+  CK(ils_plan_create(H, W, C, lam, p, 1e-4f, N, &plan));
+  if (ils_backward(plan, f, g, gf, NULL) != ILS_ERR_INVALID_ARG) return 4;  /* no checkpoints */
+  CK(ils_set_checkpointing(plan, 1));
+  CK(ils_smooth(plan, f, u, NULL));
+  CK(ils_backward(plan, f, g, gf, NULL));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(hg, gf, n * 4, cudaMemcpyDeviceToHost));
+  CK(ils_plan_destroy(plan));
+  fp = fopen(argv[9], "wb"); if (!fp || fwrite(hg, sizeof(float), n, fp) != n) return 5; fclose(fp);
+  cudaFree(f); cudaFree(u); cudaFree(g); cudaFree(gf);
+  free(hf); free(hg);
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "bwd"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                    "-I", os.path.join(cuda, "include"), str(src), "-o", str(exe), "-L", lib_dir, "-lils",
+                    f"-Wl,-rpath,{lib_dir}", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+                    f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}"], check=True)
+    r = subprocess.run([str(exe), str(H), str(W), str(C), str(N), str(lam), str(p), str(tmp_path / "f.bin"),
+                        str(tmp_path / "g.bin"), str(tmp_path / "gf.bin")], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+    got = np.fromfile(tmp_path / "gf.bin", dtype=np.float32).reshape(f.shape)
+    want = np.stack([O.ils_backward(f[c].astype(np.float64), w[c].astype(np.float64), lam, p, 1e-4, N)
+                     for c in range(C)])
+    assert rel_err(got, want) <= 1e-4

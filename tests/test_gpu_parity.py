@@ -542,7 +542,7 @@ def test_hqs_has_no_adjoint_and_checks_parameters(ils):
         f = torch.rand(1, 16, 16, device="cuda")
         u, ck = plan.smooth_checkpointed(f)
         with pytest.raises(ILSError):
-            plan.backward(ck, torch.ones_like(f))
+            plan.backward_ckpt(ck, torch.ones_like(f))
     for lam, kappa in ((0.0, 2.0), (0.25, 0.5), (-1.0, 2.0)):
         with pytest.raises(ILSError):
             ils.Plan(16, 16, 1, lam, N=2, penalty="hqs", kappa=kappa)

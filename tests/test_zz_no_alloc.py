@@ -5,13 +5,14 @@ device synchronization, a plugin whose host owns all device memory) get the
 same smoothing with the workspace in the library's fixed static device array.
 Checked through the C ABI against the plan-based ils_smooth, within the parity
 tolerance, on two calls in a row (the second call reuses the array the first
-one left behind).  This file is collected last on purpose.
+one left behind), against the FP64 oracle on a small RGB image, and for the
+property that defines it: a call leaves the device's free memory unchanged.
+This file is collected last on purpose.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2003_07504_gb300 import synth
 from tests._util import MAX_ABS_TOL, RMS_TOL, err_stats
 
@@ -39,13 +40,42 @@ def test_noalloc_matches_plan_path_on_two_calls(env):
     cases = [(3, 240, 320, 41, 1.0, 0.8), (1, 1080, 1920, 42, 2.0, 1.0)]   # second: a whole 1080p channel
     for C, H, W, seed, lam, p in cases:
         f = torch.from_numpy(synth.preset_image(H, W, C, "hd", seed)).cuda()
-        u_na = torch.full_like(f, float("nan"))
-        assert _noalloc(torch, _lib, f, u_na, lam, p) == 0
         with ils.Plan(H, W, C, lam, p, 1e-4, 4) as plan:
             u_ref = plan.smooth(f)
         torch.cuda.synchronize()
-        mx, rms = err_stats(u_na.cpu().numpy(), u_ref.cpu().numpy())
+        outs = []
+        for _ in range(2):
+            u_na = torch.full_like(f, float("nan"))
+            assert _noalloc(torch, _lib, f, u_na, lam, p) == 0
+            torch.cuda.synchronize()
+            outs.append(u_na.cpu().numpy())
+        np.testing.assert_array_equal(outs[0], outs[1])
+        mx, rms = err_stats(outs[1], u_ref.cpu().numpy())
         assert mx <= MAX_ABS_TOL and rms <= RMS_TOL, (C, H, W, mx, rms)
+
+
+def test_noalloc_matches_oracle(env):
+    torch, _lib, ils = env
+    f = synth.preset_image(240, 320, 3, "hd", 43)
+    fd = torch.from_numpy(f).cuda()
+    u = torch.empty_like(fd)
+    assert _noalloc(torch, _lib, fd, u) == 0
+    want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
+    mx, rms = err_stats(u.cpu().numpy(), want)
+    assert mx <= MAX_ABS_TOL and rms <= RMS_TOL, (mx, rms)
+
+
+def test_noalloc_allocates_nothing(env):
+    torch, _lib, ils = env
+    f = torch.from_numpy(synth.preset_image(540, 960, 2, "hd", 44)).cuda()
+    u = torch.empty_like(f)
+    assert _noalloc(torch, _lib, f, u) == 0      # first call in this context: set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert _noalloc(torch, _lib, f, u) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(env):
