@@ -127,7 +127,10 @@ void cache_store(const char* path, const std::string& dev, int H, int W, int C, 
   std::fclose(fp);
 }
 
-// Mean time (ms) of one N=1 smoothing of a class-sized frame with geometry g.
+// Median time (ms) over kTuneRuns separately timed N=1 smoothings of a class-sized frame with
+// geometry g (after two untimed runs): one slow sample - another tenant's burst, a clock step -
+// does not decide the choice.
+constexpr int kTuneRuns = 7;
 float time_geometry(const BatchClass& c, const Geometry& g, const BatchFrame& proto, float* f, float* u, float2* s0,
                     float2* s1, cudaStream_t st) {
   BatchClass cc = c;
@@ -136,20 +139,28 @@ float time_geometry(const BatchClass& c, const Geometry& g, const BatchFrame& pr
   fr.N = 1;
   fr.f = f;
   fr.u = u;
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  for (int i = 0; i < 2; ++i) enqueue_frame(cc, fr, s0, s1, st);
-  cudaEventRecord(a, st);
-  const int reps = 5;
-  for (int i = 0; i < reps; ++i) enqueue_frame(cc, fr, s0, s1, st);
-  cudaEventRecord(b, st);
+  cudaEvent_t ev[kTuneRuns + 1];
+  int made = 0;
+  for (; made <= kTuneRuns; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
   float ms = 1e30f;
-  if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (made == kTuneRuns + 1) {
+    for (int i = 0; i < 2; ++i) enqueue_frame(cc, fr, s0, s1, st);
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < kTuneRuns; ++i) {
+      enqueue_frame(cc, fr, s0, s1, st);
+      cudaEventRecord(ev[i + 1], st);
+    }
+    if (cudaEventSynchronize(ev[kTuneRuns]) == cudaSuccess) {
+      std::vector<float> t(kTuneRuns, 1e30f);
+      for (int i = 0; i < kTuneRuns; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+      std::nth_element(t.begin(), t.begin() + kTuneRuns / 2, t.end());
+      ms = t[kTuneRuns / 2];
+    }
+  }
+  for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
   if (cudaGetLastError() != cudaSuccess) return 1e30f;
-  return ms / reps;
+  return ms;
 }
 
 // Pick the row and column kernels for a class: every compile-time tile shape for its

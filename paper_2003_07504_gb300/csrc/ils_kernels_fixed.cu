@@ -21,41 +21,13 @@ namespace {
 
 __device__ __forceinline__ int wrap_row(int y, int H) { return y < 0 ? y + H : (y >= H ? y - H : y); }
 
-// Asynchronous global -> shared copies of 8 and 4 bytes (cp.async.ca); the caller waits.
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all_() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Shared memory of a column-pass CTA: the tile of G columns (padded by smem_idx), then the
-// plan's stage twiddle table and the H-entry y part of the Eq. 9 denominator, copied once
-// per CTA so that every twiddle and denominator read of the transforms is a shared-memory
-// load instead of a dependent global load.
-// Staged only where MINB CTAs per SM still fit (the 2160-point plans read the tables from
-// global memory instead).
+// Shared memory of a column-pass CTA: the tile of G columns, padded by smem_idx.  (Copying the
+// plan's stage-twiddle table and the y denominator into shared memory as well measured 4 %
+// slower at 1080 rows: those reads hit L1 and are shared by the tile's columns.)
 template <class PL, int G>
-constexpr size_t col_tile_bytes() {  // smem_elems(N G) complex (one padding slot per 16)
+constexpr size_t col_smem_bytes() {  // smem_elems(N G) complex (one padding slot per 16)
   return (size_t)(PL::N * G + (PL::N * G - 1) / 16) * sizeof(float2);
 }
-template <class PL, int G, int MINB>
-constexpr bool col_stages_tables() {
-  return MINB * (col_tile_bytes<PL, G>() + (size_t)StageTw<PL>::SIZE * sizeof(float2) +
-                 (size_t)PL::N * sizeof(float) + 1024) <= (size_t)227 * 1024;
-}
-template <class PL, int G, int MINB>
-constexpr size_t col_smem_bytes() {
-  return col_tile_bytes<PL, G>() + (col_stages_tables<PL, G, MINB>()
-                                        ? (size_t)StageTw<PL>::SIZE * sizeof(float2) + (size_t)PL::N * sizeof(float)
-                                        : 0);
-}
-
-
-
 
 // In place on nrows smem rows of packed half spectra X (slot 0 = (X[0], X[M])): replace X
 // by Z, the half-length sequence whose unnormalized inverse FFT is W (x[2m] + i x[2m+1]):
@@ -106,17 +78,8 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
   griddep_wait();
   constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, RL = PL::RL;
   constexpr int NS0 = N / R0, NS1 = N / R1, NSL = N / RL;
-  using TW = StageTw<PL>;  // twc: this plan's stage twiddle tables (copied to tws)
+  using TW = StageTw<PL>;  // twc: this plan's stage twiddle tables
   extern __shared__ float2 sm[];
-  constexpr bool STAGE_TW = col_stages_tables<PL, G, MINB>();
-  float2* tws_s = sm + smem_elems(N * G);
-  float* bys_s = reinterpret_cast<float*>(tws_s + TW::SIZE);
-  if constexpr (STAGE_TW) {
-    for (int i = threadIdx.x; i < TW::SIZE; i += blockDim.x) cp_async8(tws_s + i, twc + i);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async4(bys_s + i, by + i);
-  }
-  const float2* tws = STAGE_TW ? tws_s : twc;
-  const float* bys = STAGE_TW ? bys_s : by;
   const int tiles_per_ch = (M + G - 1) / G;
   const int ntiles = tiles_per_ch * C;
   {
@@ -147,7 +110,6 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
         for (int q = 0; q < BATCH; ++q)
           if (q0 + q < PER && t + (q0 + q) * T < N * G) sm[smem_idx(t + (q0 + q) * T)] = ld[q];
       }
-      cp_async_wait_all_();  // this thread's table copies
       __syncthreads();
       float2 v[R0];
       if (j < NS0) {
@@ -167,7 +129,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly_tab<R1, R0, false>(v, j, tws + TW::FWD_MID);
+        bfly_tab<R1, R0, false>(v, j, twc + TW::FWD_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -182,7 +144,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NSL) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) v[r] = S(j + r * NSL);
-        bfly_tab<RL, NSL, false>(v, j, tws + TW::FWD_LAST);
+        bfly_tab<RL, NSL, false>(v, j, twc + TW::FWD_LAST);
       }
       if (k0 == 0) {
         // Column 0 packs two real columns: Z = A + iB with A = F(X[:,0]), B = F(X[:,M]).
@@ -199,7 +161,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
           for (int r = 0; r < RL; ++r) {
             const int l = j + r * NSL;
             const float2 zm = S(l == 0 ? 0 : N - l);
-            const float byl = (bys[l]);
+            const float byl = __ldg(&by[l]);
             const float ia = __fdividef(1.0f, 1.0f + byl);
             const float ib = __fdividef(1.0f, 1.0f + axM + byl);
             const float sp = 0.5f * scale * (ia + ib), sn = 0.5f * scale * (ia - ib);
@@ -211,7 +173,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
         const float axk = __ldg(&ax[live ? k : 0]);
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
-          const float s = __fdividef(scale, 1.0f + axk + (bys[j + r * NSL]));
+          const float s = __fdividef(scale, 1.0f + axk + __ldg(&by[j + r * NSL]));
           v[r] = cscale(v[r], s);
         }
       }
@@ -228,7 +190,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = S(j + r * NS1);
-        bfly_tab<R1, RL, true>(v, j, tws + TW::INV_MID);
+        bfly_tab<R1, RL, true>(v, j, twc + TW::INV_MID);
       }
       __syncthreads();
       if (j < NS1) {
@@ -243,7 +205,7 @@ col_fixed_kernel(int M, int C, const float2* __restrict__ twc, const float* __re
       if (j < NS0) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) v[r] = S(j + r * NS0);
-        bfly_tab<R0, NS0, true>(v, j, tws + TW::INV_LAST);
+        bfly_tab<R0, NS0, true>(v, j, twc + TW::INV_LAST);
         if (live) {
 #pragma unroll
           for (int r = 0; r < R0; ++r) col[(size_t)(j + r * NS0) * M] = v[r];
@@ -561,7 +523,7 @@ constexpr RowEntry row_entry() {
 template <class PL, int G, int MINB = 1>
 constexpr ColEntry col_entry() {
   return ColEntry{PL::N,  PL::TPS, G, col_fixed_kernel<PL, G, MINB>, PL::R0, PL::R1, PL::R2, StageTw<PL>::SIZE,
-                  col_smem_bytes<PL, G, MINB>()};
+                  col_smem_bytes<PL, G>()};
 }
 
 // Several entries may share a length: the first is the default, the others are
@@ -593,6 +555,8 @@ const ColEntry kCols[] = {
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
     col_entry<FixedPlan<1080, 36, 30>, 4, 3>(),
     col_entry<FixedPlan<1080, 30, 36>, 8>(),
+    col_entry<FixedPlan<1080, 36, 30>, 6, 3>(),
+    col_entry<FixedPlan<1080, 36, 30>, 4, 4>(),
     col_entry<FixedPlan<720, 24, 30>, 4, 3>(),
     col_entry<FixedPlan<480, 20, 24>, 4, 4>(),
     col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),

@@ -365,21 +365,25 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   }
   if constexpr (!SHARED) {
     // Stencil (Eq. 7 and the divergence of Eq. 9's numerator) per pixel pair from the
-    // strip rows alone: mu of the pair's four gradients and of the left neighbour's.
+    // strip rows alone: mu of the pair's three x gradients and four y gradients; the x
+    // gradient left of a pair is the left lane's right one (shuffle; lane 0 takes lane 31's
+    // from the previous block of 32 pairs, and pixel 0's wrap-around term is added last).
     if (out_live) {
       const float2* fr = reinterpret_cast<const float2*>(f) + orow;
+      float carry = 0.0f;
 #pragma unroll
       for (int n2 = 0; n2 < L; ++n2) {
         const int m = lane + 32 * n2;
         const float2 c = U(w, m);
-        const float ul = U(w, m == 0 ? M - 1 : m - 1).y;
         const float ur = U(w, m == M - 1 ? 0 : m + 1).x;
         const float2 up = U(w - 1, m);
         const float2 dn = U(w + 1, m);
-        const float2 fv = fr[m];
-        const float mx_l = mu_pen<PEN>(c.x - ul, mp);
+        const float2 fv = f_is_u ? c : fr[m];
         const float mx_c = mu_pen<PEN>(c.y - c.x, mp);
         const float mx_r = mu_pen<PEN>(ur - c.y, mp);
+        const float left = __shfl_up_sync(kFull, mx_r, 1);
+        const float mx_l = lane == 0 ? carry : left;
+        carry = __shfl_sync(kFull, mx_r, 31);
         const float my0u = mu_pen<PEN>(c.x - up.x, mp);
         const float my0d = mu_pen<PEN>(dn.x - c.x, mp);
         const float my1u = mu_pen<PEN>(c.y - up.y, mp);
@@ -388,6 +392,8 @@ row_warp_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
                    fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
         if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[orow + m] = c;
       }
+      // pixel 0's left neighbour is pixel 2M-1, whose x gradient is the last carry
+      if (lane == 0) v[0].x = fmaf(mp.half_lambda, carry, v[0].x);
     }
     __syncthreads();
     if (out_live) WR::forward_row_to_global(v, spec_out + orow, buf, lane, tw);
