@@ -296,7 +296,7 @@ def load_params(path: str = DEFAULT_WEIGHTS) -> np.ndarray:
     return np.load(path).astype(np.float32)
 
 
-def converged_ils(plan_factory, f: torch.Tensor, max_iters: int = 1000, tol: float = 1e-6, chunk: int = 50):
+def converged_ils(plan_factory, f: torch.Tensor, max_iters: int = 20000, tol: float = 1e-6, chunk: int = 50):
     """ILS from f iterated until max|u^{n+1} - u^n| < tol (or max_iters): the 'converged ILS'
     reference of the equal-error comparison.  Runs in chunks of `chunk` iterations.
     Returns (u, iterations, last change max|u^{n+1} - u^n|)."""
