@@ -16,6 +16,9 @@
 // flipped in space and transposed in channels (kernels dgrad_*); the weight gradient is
 // a GEMM over pixels (dW = sum_p dY(p)^T im2col(X)(p)) computed with the same MMA and
 // reduced into FP32 with atomics.  ReLU masks use the stored post-ReLU activations.
+// With tcgen05 available, the 32 -> 32 layers' forward, input gradients and weight
+// gradients run on the tcgen05 kernels of ils_cnn_tc.cu; these kernels remain for the
+// 3-channel first and last layers (and as the whole network without tcgen05).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -754,6 +757,7 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = grid.x * grid.y * grid.z;
   const int wg_grid = tiles < 2 * sms ? tiles : 2 * sms;
+  cudaError_t tc_err = cudaSuccess;
   auto wgrad = [&](int l, const bf16* dy_nhwc, const float* dy_planar) {
     WgradArgs w{};
     w.B = B; w.H = H; w.W = W; w.dy_nhwc = dy_nhwc; w.dy_planar = dy_planar;
@@ -765,6 +769,10 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
       w.in_nhwc = n->act[l - 1];
       if (dy_planar != nullptr)
         conv_wgrad_kernel<false, true><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
+      else if (n->tc) {  // the 32 -> 32 layers on tcgen05
+        const cudaError_t e = ils::launch_wgrad32_tc(B, H, W, n->act[l - 1], dy_nhwc, n->gw[l], n->gb[l], n->err, st);
+        if (e != cudaSuccess && tc_err == cudaSuccess) tc_err = e;
+      }
       else
         conv_wgrad_kernel<false, false><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
     }
@@ -794,6 +802,7 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
     cur ^= 1;
   }
   wgrad(0, n->gact[cur], nullptr);
+  if (tc_err != cudaSuccess) return cnn_fail(tc_err, "tensor-core weight-gradient launch");
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn backward launch");
 }

@@ -222,6 +222,155 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dW[co][(3 dy + dx) 32 + ci] += sum_p dY[p][co] X[p + (dy - 1, dx - 1)][ci] and db[co] +=
+// sum_p dY[p][co] over every pixel p of the batch (the 32 -> 32 layers' weight gradients).
+//
+// GEMM view per tile of 128 pixels of one image row: D_dy[M = (dx, ci), N = co] += A x B with
+// K = the tile's pixels, one tensor-memory accumulator per dy (96 of 128 rows used).  Both
+// operands are MN-major (the M or N index is the one contiguous in a 16-byte unit):
+//   A: three TMA copies of the input rows y-1 .. y+1, shifted by dx - 1 pixels, one per dx,
+//      each in four 8-channel planes (plane dx * 4 + chunk, byte (row, pixel) = (row * 128 +
+//      pixel) * 16); the 8-row groups of M are then uniformly PLANE_X apart, the K groups of 8
+//      pixels 128 bytes apart, and dy is a start-address offset of one plane row.  M rows
+//      96-103 read a plane of ones, so row 96 of the dy = 0 accumulator collects db.
+//   B: dY of the 128 pixels, four 8-channel planes of 128 x 16 bytes.
+// Out-of-image pixels come from TMA's zero fill (zero dY contributes nothing).  Each CTA
+// accumulates all its tiles in tensor memory and adds the result to dW and db with FP32
+// atomics at the end.  One thread issues the copies and the MMAs, one tile at a time; two
+// CTAs per SM overlap each other's copies.  Every wait is bounded (error flag, drain, free).
+constexpr int WG_TILE = 128;
+constexpr int WG_PLANE_X = 3 * WG_TILE * 16;          // 6144: rows y-1..y+1, 128 pixels, 8 channels
+constexpr int WG_PLANES_X = 16;                        // 12 shifted input planes, ones, 3 zero planes
+constexpr int WG_A_BYTES = WG_PLANES_X * WG_PLANE_X;  // 98304
+constexpr int WG_PLANE_DY = WG_TILE * 16;             // 2048
+constexpr int WG_B_BYTES = 4 * WG_PLANE_DY;           // 8192
+constexpr int WG_TMA_BYTES = 12 * WG_PLANE_X + 4 * WG_PLANE_DY;
+constexpr int WG_SMEM = WG_A_BYTES + WG_B_BYTES + 64;
+constexpr int WG_NTHR = 128;
+// kind::f16 with both operands MN-major (transpose bits 15 and 16), M = 128, N = 32
+constexpr uint32_t kIdescWg = tc::idesc_bf16(128, 32) | (1u << 15) | (1u << 16);
+
+struct WgArgs {
+  int B, H, W;
+  float* dw;    // [32 co][288] FP32, column (3 dy + dx) 32 + ci (accumulated)
+  float* db;    // [32] FP32 (accumulated)
+  int* error;
+  uint32_t spin;
+};
+
+__global__ void __launch_bounds__(WG_NTHR, 2)
+conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_constant__ CUtensorMap dy_map,
+                       WgArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + WG_A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + WG_A_BYTES + WG_B_BYTES);
+  __shared__ uint32_t tmem_base_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full = saddr(&bars[0]), done = saddr(&bars[1]);
+  // planes 12-15: ones (the bias-gradient rows), then zeros
+  for (int q = threadIdx.x; q < 4 * WG_PLANE_X / 16; q += blockDim.x) {
+    const uint32_t one2 = 0x3F803F80u;  // two BF16 1.0
+    const uint4 v = q < WG_PLANE_X / 16 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(sA + 12 * WG_PLANE_X)[q] = v;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(saddr(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+
+  const int tiles_x = (a.W + WG_TILE - 1) / WG_TILE;
+  const int ntiles = a.B * a.H * tiles_x;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  __shared__ int failed_s;
+  if (threadIdx.x == 0) failed_s = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool failed = false;
+    int issued = 0, loaded = 0;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int tile = blockIdx.x + i * gridDim.x;
+      const int b = tile / (a.H * tiles_x);
+      const int rr = tile - b * a.H * tiles_x;
+      const int y = rr / tiles_x, x0 = (rr - y * tiles_x) * WG_TILE;
+      mbar_expect_tx(full, WG_TMA_BYTES);
+      for (int dx = 0; dx < 3; ++dx)
+        for (int c = 0; c < 4; ++c)
+          tma_load_4d(saddr(sA + (dx * 4 + c) * WG_PLANE_X), &x_map, c * 8, x0 - 1 + dx, y - 1, b, full);
+      for (int c = 0; c < 4; ++c) tma_load_4d(saddr(sB + c * WG_PLANE_DY), &dy_map, c * 8, x0, y, b, full);
+      loaded = i + 1;
+      if (!mbar_wait(full, i & 1, a.spin)) { failed = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+        for (int ks = 0; ks < WG_TILE / 16; ++ks) {
+          // A: M groups PLANE_X apart (SBO), K groups of 8 pixels 128 B apart (LBO)
+          const uint64_t da = smem_desc(saddr(sA) + dy * WG_TILE * 16 + ks * 256, 128, WG_PLANE_X);
+          const uint64_t db = smem_desc(saddr(sB) + ks * 256, 128, WG_PLANE_DY);
+          tc::mma_f16(tmem + dy * 32, da, db, kIdescWg, (i > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(done);
+      issued = i + 1;
+      // the next tile's copies overwrite the operands: wait for this tile's MMAs
+      if (!mbar_wait(done, i & 1, a.spin)) { failed = true; break; }
+    }
+    // drain before tensor memory is freed or the CTA ends (bounded)
+    if (failed) {
+      if (loaded > 0) mbar_wait(full, (loaded - 1) & 1);
+      if (issued > 0) mbar_wait(done, (issued - 1) & 1);
+      failed_s = 1;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (failed_s) {
+    if (threadIdx.x == 0) atomicExch(a.error, 1);
+  } else if (my_tiles > 0) {
+    // thread -> accumulator row m = 32 warp + lane: (dx, ci) = (m / 32, m % 32) for m < 96,
+    // m = 96 the bias gradient (dy = 0 accumulator only)
+    const int m = warp * 32 + lane;
+#pragma unroll 1
+    for (int dy = 0; dy < 3; ++dy) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + dy * 32 + ((uint32_t)(warp * 32) << 16);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < 96) {
+        const int k = (dy * 3 + m / 32) * 32 + (m % 32);
+#pragma unroll
+        for (int co = 0; co < 32; ++co) atomicAdd(&a.dw[co * 288 + k], __uint_as_float(r[co]));
+      } else if (m == 96 && dy == 0) {
+#pragma unroll
+        for (int co = 0; co < 32; ++co) atomicAdd(&a.db[co], __uint_as_float(r[co]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 }  // namespace cnn_tc
 
 // ---------------------------------------------------------------- host side
@@ -262,8 +411,36 @@ bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int
 }
 
 cudaError_t conv32_tc_set_attributes() {
-  return cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              cnn_tc::SMEM_PIPE);
+  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       cnn_tc::SMEM_PIPE);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cnn_tc::conv32_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              cnn_tc::WG_SMEM);
+}
+
+// dW += weight gradient, db += bias gradient of a 32 -> 32 conv3x3 from its NHWC BF16 input x
+// and output gradient dy (B x H x W x 32 each); dw is [32][288] FP32, db [32] FP32.
+cudaError_t launch_wgrad32_tc(int B, int H, int W, const void* x, const void* dy, float* dw, float* db, int* error,
+                              cudaStream_t st) {
+  using namespace cnn_tc;
+  if (encode_fn() == nullptr) return cudaErrorNotSupported;
+  CUtensorMap xm, dm;
+  if (!make_nhwc32_map(&xm, x, B, H, W, WG_TILE, 3) || !make_nhwc32_map(&dm, dy, B, H, W, WG_TILE, 1))
+    return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = B * H * ((W + WG_TILE - 1) / WG_TILE);
+  const int grid = tiles < 2 * sms ? tiles : 2 * sms;   // two persistent CTAs per SM
+  WgArgs a{};
+  a.B = B; a.H = H; a.W = W;
+  a.dw = dw;
+  a.db = db;
+  a.error = error;
+  const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
+  a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
+  conv32_wgrad_tc_kernel<<<grid, WG_NTHR, WG_SMEM, st>>>(xm, dm, a);
+  return cudaGetLastError();
 }
 
 // out = conv3x3_{32->32}(in) (+bias, ReLU | mask) on NHWC BF16 tensors of B x H x W x 32.
