@@ -45,6 +45,7 @@ using tc::mbar_init;
 using tc::mbar_wait;
 using tc::saddr;
 using tc::smem_desc;
+using tc::smem_desc_sw64;
 using tc::tma_load_4d;
 
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 32);
@@ -228,25 +229,30 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 //
 // GEMM view per tile of 128 pixels of one image row: D_dy[M = (dx, ci), N = co] += A x B with
 // K = the tile's pixels, one tensor-memory accumulator per dy (96 of 128 rows used).  Both
-// operands are MN-major (the M or N index is the one contiguous in a 16-byte unit):
-//   A: three TMA copies of the input rows y-1 .. y+1, shifted by dx - 1 pixels, one per dx,
-//      each in four 8-channel planes (plane dx * 4 + chunk, byte (row, pixel) = (row * 128 +
-//      pixel) * 16); the 8-row groups of M are then uniformly PLANE_X apart, the K groups of 8
-//      pixels 128 bytes apart, and dy is a start-address offset of one plane row.  M rows
-//      96-103 read a plane of ones, so row 96 of the dy = 0 accumulator collects db.
-//   B: dY of the 128 pixels, four 8-channel planes of 128 x 16 bytes.
-// Out-of-image pixels come from TMA's zero fill (zero dY contributes nothing).  Each CTA
-// accumulates all its tiles in tensor memory and adds the result to dW and db with FP32
-// atomics at the end.  One thread issues the copies and the MMAs, one tile at a time; two
-// CTAs per SM overlap each other's copies.  Every wait is bounded (error flag, drain, free).
+// operands are MN-major in the 64-byte swizzled canonical layout, which is an NHWC row of 32
+// channels (64 bytes per pixel) as TMA writes it with the 64-byte swizzle:
+//   A: a row slot holds one input row four times - shifted by dx - 1 pixels for dx = 0, 1, 2,
+//      and a block of ones - 8 KB apart, so the four 32-row blocks of M are LBO = 8 KB apart,
+//      the K groups of 8 pixels SBO = 512 bytes apart, and dy selects the slot (row y in slot
+//      y mod WG_SLOTS).  M rows 96-127 read ones: row 96 of the dy = 0 accumulator collects db.
+//   B: dY of the tile's 128 pixels, one 8 KB block, WG_DSLOTS slots.
+// (The unswizzled MN-major form, 8-channel planes 12 KB apart, ran each MMA ~5x slower.)
+// Each CTA takes a contiguous range of the batch's tiles, ordered by (image, 128-pixel
+// column, row).  Within a column a tile needs one new input row: the copies run WG_AHEAD tiles
+// ahead of the MMAs (a new column starts with its first rows loaded after the MMAs in flight
+// are done).  Out-of-image pixels come from TMA's zero fill.  Each CTA accumulates its tiles in
+// tensor memory and adds the result to dW and db with FP32 atomics at the end.  One thread
+// issues the copies and the MMAs; every wait is bounded (error flag, drain, free), and no
+// mbarrier ever has more than one phase pending.
 constexpr int WG_TILE = 128;
-constexpr int WG_PLANE_X = 3 * WG_TILE * 16;          // 6144: rows y-1..y+1, 128 pixels, 8 channels
-constexpr int WG_PLANES_X = 16;                        // 12 shifted input planes, ones, 3 zero planes
-constexpr int WG_A_BYTES = WG_PLANES_X * WG_PLANE_X;  // 98304
-constexpr int WG_PLANE_DY = WG_TILE * 16;             // 2048
-constexpr int WG_B_BYTES = 4 * WG_PLANE_DY;           // 8192
-constexpr int WG_TMA_BYTES = 12 * WG_PLANE_X + 4 * WG_PLANE_DY;
-constexpr int WG_SMEM = WG_A_BYTES + WG_B_BYTES + 64;
+constexpr int WG_AHEAD = 3;                            // tiles of copies in flight ahead of the MMAs
+constexpr int WG_SLOTS = WG_AHEAD + 3;                 // input row slots
+constexpr int WG_DSLOTS = WG_AHEAD + 1;                // dY slots (also the number of barrier pairs)
+constexpr int WG_BLK = WG_TILE * 64;                   // 8192: 128 pixels x 32 BF16 channels
+constexpr int WG_SLOT = 4 * WG_BLK;                    // dx = 0, 1, 2 and the ones block
+constexpr int WG_A_BYTES = WG_SLOTS * WG_SLOT;         // 196608
+constexpr int WG_D_BYTES = WG_DSLOTS * WG_BLK;         // 32768
+constexpr int WG_SMEM = 1024 + WG_A_BYTES + WG_D_BYTES + 2 * WG_DSLOTS * 8;  // + alignment slack
 constexpr int WG_NTHR = 128;
 // kind::f16 with both operands MN-major (transpose bits 15 and 16), M = 128, N = 32
 constexpr uint32_t kIdescWg = tc::idesc_bf16(128, 32) | (1u << 15) | (1u << 16);
@@ -259,25 +265,29 @@ struct WgArgs {
   uint32_t spin;
 };
 
-__global__ void __launch_bounds__(WG_NTHR, 2)
+__device__ __forceinline__ int wg_slot(int y) { return ((y % WG_SLOTS) + WG_SLOTS) % WG_SLOTS; }
+
+__global__ void __launch_bounds__(WG_NTHR, 1)
 conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_constant__ CUtensorMap dy_map,
                        WgArgs a) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* sA = sm;
-  unsigned char* sB = sm + WG_A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + WG_A_BYTES + WG_B_BYTES);
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  // the swizzle pattern repeats every 512 bytes: operands start on a 1024-byte boundary
+  // dY first: every operand address of both blocks stays inside the two (sD + WG_D_BYTES + WG_A_BYTES)
+  unsigned char* sD = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);
+  unsigned char* sA = sD + WG_D_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + WG_A_BYTES);  // full[WG_DSLOTS], done[WG_DSLOTS]
   __shared__ uint32_t tmem_base_slot;
+  __shared__ int failed_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full = saddr(&bars[0]), done = saddr(&bars[1]);
-  // planes 12-15: ones (the bias-gradient rows), then zeros
-  for (int q = threadIdx.x; q < 4 * WG_PLANE_X / 16; q += blockDim.x) {
+  // the ones block of every slot (the bias-gradient rows; the swizzle permutes ones into ones)
+  for (int q = threadIdx.x; q < WG_SLOTS * WG_BLK / 16; q += blockDim.x) {
     const uint32_t one2 = 0x3F803F80u;  // two BF16 1.0
-    const uint4 v = q < WG_PLANE_X / 16 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
-    reinterpret_cast<uint4*>(sA + 12 * WG_PLANE_X)[q] = v;
+    const int sl = q / (WG_BLK / 16), o = q - sl * (WG_BLK / 16);
+    reinterpret_cast<uint4*>(sA + sl * WG_SLOT + 3 * WG_BLK)[o] = make_uint4(one2, one2, one2, one2);
   }
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(done, 1);
+    failed_s = 0;
+    for (int i = 0; i < 2 * WG_DSLOTS; ++i) mbar_init(saddr(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -291,55 +301,90 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
   const uint32_t tmem = tmem_base_slot;
 
   const int tiles_x = (a.W + WG_TILE - 1) / WG_TILE;
-  const int ntiles = a.B * a.H * tiles_x;
-  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  __shared__ int failed_s;
-  if (threadIdx.x == 0) failed_s = 0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  const long long total = (long long)a.B * tiles_x * a.H;  // tile g: column g / H, row g % H
+  const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+  if (threadIdx.x == 0 && t1 > t0) {
+    uint32_t full_issued[WG_DSLOTS] = {}, full_used[WG_DSLOTS] = {}, done_issued[WG_DSLOTS] = {},
+             done_waited[WG_DSLOTS] = {};
     bool failed = false;
-    int issued = 0, loaded = 0;
-    for (int i = 0; i < my_tiles; ++i) {
-      const int tile = blockIdx.x + i * gridDim.x;
-      const int b = tile / (a.H * tiles_x);
-      const int rr = tile - b * a.H * tiles_x;
-      const int y = rr / tiles_x, x0 = (rr - y * tiles_x) * WG_TILE;
-      mbar_expect_tx(full, WG_TMA_BYTES);
-      for (int dx = 0; dx < 3; ++dx)
-        for (int c = 0; c < 4; ++c)
-          tma_load_4d(saddr(sA + (dx * 4 + c) * WG_PLANE_X), &x_map, c * 8, x0 - 1 + dx, y - 1, b, full);
-      for (int c = 0; c < 4; ++c) tma_load_4d(saddr(sB + c * WG_PLANE_DY), &dy_map, c * 8, x0, y, b, full);
-      loaded = i + 1;
-      if (!mbar_wait(full, i & 1, a.spin)) { failed = true; break; }
+    auto full = [&](int j) { return saddr(&bars[j]); };
+    auto done = [&](int j) { return saddr(&bars[WG_DSLOTS + j]); };
+    // waits for the last commit on done[j] if it has not been waited for (bounded)
+    auto settle = [&](int j, uint32_t lim) -> bool {
+      if (done_waited[j] == done_issued[j]) return true;
+      if (!mbar_wait(done(j), (done_issued[j] - 1) & 1, lim)) return false;
+      done_waited[j] = done_issued[j];
+      return true;
+    };
+    // copies for tile g (local index i = g - t0) on full[i % WG_DSLOTS]: dY row y, and the input
+    // rows y - 1 .. y + 1 (first tile of a column run) or y + 1 alone
+    auto load_tile = [&](long long g, bool first) {
+      const int col = (int)(g / a.H), y = (int)(g - (long long)col * a.H);
+      const int b = col / tiles_x, x0 = (col - b * tiles_x) * WG_TILE;
+      const int j = (int)((g - t0) % WG_DSLOTS);
+      const int nrows = first ? 3 : 1;
+      mbar_expect_tx(full(j), (nrows * 3 + 1) * WG_BLK);
+      ++full_issued[j];
+      for (int yy = first ? y - 1 : y + 1; yy <= y + 1; ++yy)
+        for (int dx = 0; dx < 3; ++dx)
+          tma_load_4d(saddr(sA + wg_slot(yy) * WG_SLOT + dx * WG_BLK), &x_map, 0, x0 - 1 + dx, yy, b, full(j));
+      tma_load_4d(saddr(sD + j * WG_BLK), &dy_map, 0, x0, y, b, full(j));
+    };
+    long long loaded = t0;  // next tile to load
+    for (long long g = t0; g < t1 && !failed; ++g) {
+      const int i = (int)(g - t0), j = i % WG_DSLOTS;
+      const int col = (int)(g / a.H), y = (int)(g - (long long)col * a.H);
+      const long long col_end = (long long)(col + 1) * a.H;  // first tile of the next column
+      if (g == t0 || y == 0) {
+        // a new column run: every MMA in flight must be done before its rows take the slots
+        for (int s = 0; s < WG_DSLOTS; ++s)
+          if (!settle(s, a.spin)) failed = true;
+        if (failed) break;
+        load_tile(g, true);
+        for (loaded = g + 1; loaded < t1 && loaded < col_end && loaded < g + WG_AHEAD; ++loaded)
+          load_tile(loaded, false);
+      }
+      // this tile's operands
+      if (!mbar_wait(full(j), full_used[j] & 1, a.spin)) { failed = true; break; }
+      ++full_used[j];
+      // the barrier about to be committed to must have no phase pending (tile g - WG_DSLOTS)
+      if (!settle(j, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
       for (int dy = 0; dy < 3; ++dy) {
+        const uint32_t arow = saddr(sA) + (uint32_t)(wg_slot(y - 1 + dy) * WG_SLOT);
 #pragma unroll
         for (int ks = 0; ks < WG_TILE / 16; ++ks) {
-          // A: M groups PLANE_X apart (SBO), K groups of 8 pixels 128 B apart (LBO)
-          const uint64_t da = smem_desc(saddr(sA) + dy * WG_TILE * 16 + ks * 256, 128, WG_PLANE_X);
-          const uint64_t db = smem_desc(saddr(sB) + ks * 256, 128, WG_PLANE_DY);
-          tc::mma_f16(tmem + dy * 32, da, db, kIdescWg, (i > 0 || ks > 0) ? 1u : 0u);
+          // 16 pixels (1 KB) per K step; M blocks of 32 LBO = 8 KB apart, K groups SBO = 512 B apart
+          const uint64_t da = smem_desc_sw64(arow + ks * 1024, WG_BLK, 512);
+          const uint64_t dd = smem_desc_sw64(saddr(sD) + j * WG_BLK + ks * 1024, WG_BLK, 512);
+          tc::mma_f16(tmem + dy * 32, da, dd, kIdescWg, (g > t0 || ks > 0) ? 1u : 0u);
         }
       }
-      mma_commit(done);
-      issued = i + 1;
-      // the next tile's copies overwrite the operands: wait for this tile's MMAs
-      if (!mbar_wait(done, i & 1, a.spin)) { failed = true; break; }
+      mma_commit(done(j));
+      ++done_issued[j];
+      // with this tile's MMAs queued, prefetch tile g + WG_AHEAD: it takes the input and dY slots
+      // of tile g - 1, so wait for tile g - 1's MMAs first (done at a column's first tile)
+      if (loaded < t1 && loaded < col_end && loaded == g + WG_AHEAD) {
+        if (!settle((i - 1 + WG_DSLOTS) % WG_DSLOTS, a.spin)) { failed = true; break; }
+        load_tile(loaded, false);
+        ++loaded;
+      }
     }
-    // drain before tensor memory is freed or the CTA ends (bounded)
-    if (failed) {
-      if (loaded > 0) mbar_wait(full, (loaded - 1) & 1);
-      if (issued > 0) mbar_wait(done, (issued - 1) & 1);
-      failed_s = 1;
-    }
+    // drain (bounded): copies still in flight, then every MMA issued
+    for (int s = 0; s < WG_DSLOTS; ++s)
+      for (; full_used[s] < full_issued[s]; ++full_used[s])
+        if (!mbar_wait(full(s), full_used[s] & 1)) failed = true;
+    for (int s = 0; s < WG_DSLOTS; ++s)
+      if (!settle(s, tc::kSpinLimit)) failed = true;
+    if (failed) failed_s = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (failed_s) {
     if (threadIdx.x == 0) atomicExch(a.error, 1);
-  } else if (my_tiles > 0) {
+  } else if (t1 > t0) {
     // thread -> accumulator row m = 32 warp + lane: (dx, ci) = (m / 32, m % 32) for m < 96,
     // m = 96 the bias gradient (dy = 0 accumulator only)
     const int m = warp * 32 + lane;
@@ -410,6 +455,18 @@ bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+  const cuuint32_t box[4] = {32, (cuuint32_t)box_x, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(act), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t conv32_tc_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cnn_tc::SMEM_PIPE);
@@ -425,13 +482,13 @@ cudaError_t launch_wgrad32_tc(int B, int H, int W, const void* x, const void* dy
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
   CUtensorMap xm, dm;
-  if (!make_nhwc32_map(&xm, x, B, H, W, WG_TILE, 3) || !make_nhwc32_map(&dm, dy, B, H, W, WG_TILE, 1))
+  if (!make_nhwc32_map_sw64(&xm, x, B, H, W, WG_TILE) || !make_nhwc32_map_sw64(&dm, dy, B, H, W, WG_TILE))
     return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles = B * H * ((W + WG_TILE - 1) / WG_TILE);
-  const int grid = tiles < 2 * sms ? tiles : 2 * sms;   // two persistent CTAs per SM
+  const long long tiles = (long long)B * ((W + WG_TILE - 1) / WG_TILE) * H;
+  const int grid = tiles < sms ? (int)tiles : sms;   // one persistent CTA per SM
   WgArgs a{};
   a.B = B; a.H = H; a.W = W;
   a.dw = dw;

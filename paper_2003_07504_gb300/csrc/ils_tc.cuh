@@ -57,6 +57,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
+// The same descriptor for the 64-byte swizzled canonical layout (swizzle mode 4 in bits
+// 61-63): the data as TMA writes it with CU_TENSOR_MAP_SWIZZLE_64B; the start address must
+// be 512-byte aligned (matrix base offset 0).  For an MN-major operand LBO is the distance
+// between blocks of 32 MN elements and SBO between groups of 8 K rows (64 bytes apart each).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(addr, lbo, sbo) | (4ull << 61);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
 // M >> 4 in bits 24-28.
@@ -84,5 +92,8 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // pixels x box_y rows x 1 image, zero fill out of bounds (host; false when the driver entry
 // point is missing or the encoding fails).
 bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y);
+// The same tensor with a box of all 32 channels x box_x pixels x 1 row, written to shared
+// memory with the 64-byte swizzle.
+bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x);
 
 }  // namespace ils
