@@ -227,35 +227,39 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 // dW[co][(3 dy + dx) 32 + ci] += sum_p dY[p][co] X[p + (dy - 1, dx - 1)][ci] and db[co] +=
 // sum_p dY[p][co] over every pixel p of the batch (the 32 -> 32 layers' weight gradients).
 //
-// GEMM view per tile of 128 pixels of one image row: D_dy[M = (dx, ci), N = co] += A x B with
-// K = the tile's pixels, one tensor-memory accumulator per dy (96 of 128 rows used).  Both
-// operands are MN-major in the 64-byte swizzled canonical layout, which is an NHWC row of 32
-// channels (64 bytes per pixel) as TMA writes it with the 64-byte swizzle:
-//   A: a row slot holds one input row four times - shifted by dx - 1 pixels for dx = 0, 1, 2,
-//      and a block of ones - 8 KB apart, so the four 32-row blocks of M are LBO = 8 KB apart,
-//      the K groups of 8 pixels SBO = 512 bytes apart, and dy selects the slot (row y in slot
-//      y mod WG_SLOTS).  M rows 96-127 read ones: row 96 of the dy = 0 accumulator collects db.
-//   B: dY of the tile's 128 pixels, one 8 KB block, WG_DSLOTS slots.
-// (The unswizzled MN-major form, 8-channel planes 12 KB apart, ran each MMA ~5x slower.)
-// Each CTA takes a contiguous range of the batch's tiles, ordered by (image, 128-pixel
-// column, row).  Within a column a tile needs one new input row: the copies run WG_AHEAD tiles
-// ahead of the MMAs (a new column starts with its first rows loaded after the MMAs in flight
-// are done).  Out-of-image pixels come from TMA's zero fill.  Each CTA accumulates its tiles in
-// tensor memory and adds the result to dW and db with FP32 atomics at the end.  One thread
-// issues the copies and the MMAs; every wait is bounded (error flag, drain, free), and no
-// mbarrier ever has more than one phase pending.
+// Written per input row q = p + (dy - 1, 0): the tile of 128 pixels of input row yq contributes
+// D[M = (dx, ci)][N = (kb, co)] += sum_x X[yq][x + dx - 1][ci] dY[yq - 1 + kb][x][co], and the
+// block kb of N belongs to dy = 2 - kb.  An M = 128 MMA costs about the same whatever its N up
+// to 256, so N = 96 (three dY rows) does the work of the three N = 32 products of the dy
+// taps in one instruction: 8 MMAs of K = 16 pixels per tile.  Both operands are MN-major in
+// the 64-byte swizzled canonical layout, an NHWC row of 32 channels (64 bytes per pixel) as
+// TMA writes it with the 64-byte swizzle:
+//   A: an input slot holds the tile's input row three times, shifted by dx - 1 pixels, then a
+//      block of ones, 8 KB apart: the four 32-row blocks of M are LBO = 8 KB apart, the K
+//      groups of 8 pixels SBO = 512 bytes apart.  M rows 96-127 read ones, so row 96 collects
+//      sum_p dY[p]: its kb = 1 block (dY row yq itself) is db.
+//   B: a ring of dY rows (row r in slot r mod WG_RING) with slots 0 and 1 mirrored after the
+//      ring, so rows yq - 1, yq, yq + 1 always sit in three consecutive 8 KB blocks (LBO).
+// Each CTA takes a contiguous range of the batch's tiles, ordered by (image, 128-pixel column,
+// input row); within a column a tile needs one new dY row.  The copies run WG_AHEAD tiles
+// ahead of the MMAs (a new column starts after the MMAs in flight are done).  Out-of-image
+// pixels come from TMA's zero fill; the input rows -1 and H, which only zero padding would
+// pair with, are never walked.  The CTA accumulates its tiles in tensor memory and adds the
+// result to dW and db with FP32 atomics at the end.  One thread issues the copies and the
+// MMAs; every wait is bounded (error flag, drain, free), and no mbarrier ever has more than
+// one phase pending.
 constexpr int WG_TILE = 128;
 constexpr int WG_AHEAD = 3;                            // tiles of copies in flight ahead of the MMAs
-constexpr int WG_SLOTS = WG_AHEAD + 3;                 // input row slots
-constexpr int WG_DSLOTS = WG_AHEAD + 1;                // dY slots (also the number of barrier pairs)
+constexpr int WG_XSLOTS = WG_AHEAD + 1;                // input slots (also the number of barrier pairs)
+constexpr int WG_RING = WG_AHEAD + 3;                  // dY ring slots (+2 mirrors)
 constexpr int WG_BLK = WG_TILE * 64;                   // 8192: 128 pixels x 32 BF16 channels
-constexpr int WG_SLOT = 4 * WG_BLK;                    // dx = 0, 1, 2 and the ones block
-constexpr int WG_A_BYTES = WG_SLOTS * WG_SLOT;         // 196608
-constexpr int WG_D_BYTES = WG_DSLOTS * WG_BLK;         // 32768
-constexpr int WG_SMEM = 1024 + WG_A_BYTES + WG_D_BYTES + 2 * WG_DSLOTS * 8;  // + alignment slack
+constexpr int WG_XSLOT = 4 * WG_BLK;                   // dx = 0, 1, 2 and the ones block
+constexpr int WG_D_BYTES = (WG_RING + 2) * WG_BLK;     // 65536
+constexpr int WG_X_BYTES = WG_XSLOTS * WG_XSLOT;       // 131072
+constexpr int WG_SMEM = 1024 + WG_D_BYTES + WG_X_BYTES + 2 * WG_XSLOTS * 8;  // + alignment slack
 constexpr int WG_NTHR = 128;
-// kind::f16 with both operands MN-major (transpose bits 15 and 16), M = 128, N = 32
-constexpr uint32_t kIdescWg = tc::idesc_bf16(128, 32) | (1u << 15) | (1u << 16);
+// kind::f16 with both operands MN-major (transpose bits 15 and 16), M = 128, N = 96
+constexpr uint32_t kIdescWg = tc::idesc_bf16(128, 96) | (1u << 15) | (1u << 16);
 
 struct WgArgs {
   int B, H, W;
@@ -265,29 +269,29 @@ struct WgArgs {
   uint32_t spin;
 };
 
-__device__ __forceinline__ int wg_slot(int y) { return ((y % WG_SLOTS) + WG_SLOTS) % WG_SLOTS; }
+__device__ __forceinline__ int wg_ring(int r) { return ((r % WG_RING) + WG_RING) % WG_RING; }
 
 __global__ void __launch_bounds__(WG_NTHR, 1)
 conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_constant__ CUtensorMap dy_map,
                        WgArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  // the swizzle pattern repeats every 512 bytes: operands start on a 1024-byte boundary
-  // dY first: every operand address of both blocks stays inside the two (sD + WG_D_BYTES + WG_A_BYTES)
+  // the swizzle pattern repeats every 512 bytes: operands start on a 1024-byte boundary; the dY
+  // ring comes first so that every operand address stays inside the two regions
   unsigned char* sD = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);
-  unsigned char* sA = sD + WG_D_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + WG_A_BYTES);  // full[WG_DSLOTS], done[WG_DSLOTS]
+  unsigned char* sX = sD + WG_D_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + WG_X_BYTES);  // full[WG_XSLOTS], done[WG_XSLOTS]
   __shared__ uint32_t tmem_base_slot;
   __shared__ int failed_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the ones block of every slot (the bias-gradient rows; the swizzle permutes ones into ones)
-  for (int q = threadIdx.x; q < WG_SLOTS * WG_BLK / 16; q += blockDim.x) {
+  // the ones block of every input slot (the swizzle permutes ones into ones)
+  for (int q = threadIdx.x; q < WG_XSLOTS * WG_BLK / 16; q += blockDim.x) {
     const uint32_t one2 = 0x3F803F80u;  // two BF16 1.0
     const int sl = q / (WG_BLK / 16), o = q - sl * (WG_BLK / 16);
-    reinterpret_cast<uint4*>(sA + sl * WG_SLOT + 3 * WG_BLK)[o] = make_uint4(one2, one2, one2, one2);
+    reinterpret_cast<uint4*>(sX + sl * WG_XSLOT + 3 * WG_BLK)[o] = make_uint4(one2, one2, one2, one2);
   }
   if (threadIdx.x == 0) {
     failed_s = 0;
-    for (int i = 0; i < 2 * WG_DSLOTS; ++i) mbar_init(saddr(&bars[i]), 1);
+    for (int i = 0; i < 2 * WG_XSLOTS; ++i) mbar_init(saddr(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -301,14 +305,14 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
   const uint32_t tmem = tmem_base_slot;
 
   const int tiles_x = (a.W + WG_TILE - 1) / WG_TILE;
-  const long long total = (long long)a.B * tiles_x * a.H;  // tile g: column g / H, row g % H
+  const long long total = (long long)a.B * tiles_x * a.H;  // tile g: column g / H, input row g % H
   const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
   if (threadIdx.x == 0 && t1 > t0) {
-    uint32_t full_issued[WG_DSLOTS] = {}, full_used[WG_DSLOTS] = {}, done_issued[WG_DSLOTS] = {},
-             done_waited[WG_DSLOTS] = {};
+    uint32_t full_issued[WG_XSLOTS] = {}, full_used[WG_XSLOTS] = {}, done_issued[WG_XSLOTS] = {},
+             done_waited[WG_XSLOTS] = {};
     bool failed = false;
     auto full = [&](int j) { return saddr(&bars[j]); };
-    auto done = [&](int j) { return saddr(&bars[WG_DSLOTS + j]); };
+    auto done = [&](int j) { return saddr(&bars[WG_XSLOTS + j]); };
     // waits for the last commit on done[j] if it has not been waited for (bounded)
     auto settle = [&](int j, uint32_t lim) -> bool {
       if (done_waited[j] == done_issued[j]) return true;
@@ -316,28 +320,33 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
       done_waited[j] = done_issued[j];
       return true;
     };
-    // copies for tile g (local index i = g - t0) on full[i % WG_DSLOTS]: dY row y, and the input
-    // rows y - 1 .. y + 1 (first tile of a column run) or y + 1 alone
+    // copies for tile g (local index i = g - t0) on full[i % WG_XSLOTS]: its input row three
+    // times, and dY rows yq - 1 .. yq + 1 (first tile of a column run) or yq + 1 alone, each into
+    // its ring slot and, for slots 0 and 1, the mirror after the ring
     auto load_tile = [&](long long g, bool first) {
-      const int col = (int)(g / a.H), y = (int)(g - (long long)col * a.H);
+      const int col = (int)(g / a.H), yq = (int)(g - (long long)col * a.H);
       const int b = col / tiles_x, x0 = (col - b * tiles_x) * WG_TILE;
-      const int j = (int)((g - t0) % WG_DSLOTS);
-      const int nrows = first ? 3 : 1;
-      mbar_expect_tx(full(j), (nrows * 3 + 1) * WG_BLK);
+      const int j = (int)((g - t0) % WG_XSLOTS);
+      uint32_t bytes = 3 * WG_BLK;
+      for (int r = first ? yq - 1 : yq + 1; r <= yq + 1; ++r) bytes += (wg_ring(r) < 2 ? 2 : 1) * WG_BLK;
+      mbar_expect_tx(full(j), bytes);
       ++full_issued[j];
-      for (int yy = first ? y - 1 : y + 1; yy <= y + 1; ++yy)
-        for (int dx = 0; dx < 3; ++dx)
-          tma_load_4d(saddr(sA + wg_slot(yy) * WG_SLOT + dx * WG_BLK), &x_map, 0, x0 - 1 + dx, yy, b, full(j));
-      tma_load_4d(saddr(sD + j * WG_BLK), &dy_map, 0, x0, y, b, full(j));
+      for (int dx = 0; dx < 3; ++dx)
+        tma_load_4d(saddr(sX + j * WG_XSLOT + dx * WG_BLK), &x_map, 0, x0 - 1 + dx, yq, b, full(j));
+      for (int r = first ? yq - 1 : yq + 1; r <= yq + 1; ++r) {
+        const int sl = wg_ring(r);
+        tma_load_4d(saddr(sD + sl * WG_BLK), &dy_map, 0, x0, r, b, full(j));
+        if (sl < 2) tma_load_4d(saddr(sD + (WG_RING + sl) * WG_BLK), &dy_map, 0, x0, r, b, full(j));
+      }
     };
     long long loaded = t0;  // next tile to load
     for (long long g = t0; g < t1 && !failed; ++g) {
-      const int i = (int)(g - t0), j = i % WG_DSLOTS;
-      const int col = (int)(g / a.H), y = (int)(g - (long long)col * a.H);
+      const int i = (int)(g - t0), j = i % WG_XSLOTS;
+      const int col = (int)(g / a.H), yq = (int)(g - (long long)col * a.H);
       const long long col_end = (long long)(col + 1) * a.H;  // first tile of the next column
-      if (g == t0 || y == 0) {
+      if (g == t0 || yq == 0) {
         // a new column run: every MMA in flight must be done before its rows take the slots
-        for (int s = 0; s < WG_DSLOTS; ++s)
+        for (int s = 0; s < WG_XSLOTS; ++s)
           if (!settle(s, a.spin)) failed = true;
         if (failed) break;
         load_tile(g, true);
@@ -347,35 +356,32 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
       // this tile's operands
       if (!mbar_wait(full(j), full_used[j] & 1, a.spin)) { failed = true; break; }
       ++full_used[j];
-      // the barrier about to be committed to must have no phase pending (tile g - WG_DSLOTS)
+      // the barrier about to be committed to must have no phase pending (tile g - WG_XSLOTS)
       if (!settle(j, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-      for (int dy = 0; dy < 3; ++dy) {
-        const uint32_t arow = saddr(sA) + (uint32_t)(wg_slot(y - 1 + dy) * WG_SLOT);
+      const uint32_t xa = saddr(sX) + (uint32_t)(j * WG_XSLOT), da0 = saddr(sD) + (uint32_t)(wg_ring(yq - 1) * WG_BLK);
 #pragma unroll
-        for (int ks = 0; ks < WG_TILE / 16; ++ks) {
-          // 16 pixels (1 KB) per K step; M blocks of 32 LBO = 8 KB apart, K groups SBO = 512 B apart
-          const uint64_t da = smem_desc_sw64(arow + ks * 1024, WG_BLK, 512);
-          const uint64_t dd = smem_desc_sw64(saddr(sD) + j * WG_BLK + ks * 1024, WG_BLK, 512);
-          tc::mma_f16(tmem + dy * 32, da, dd, kIdescWg, (g > t0 || ks > 0) ? 1u : 0u);
-        }
+      for (int ks = 0; ks < WG_TILE / 16; ++ks) {
+        // 16 pixels (1 KB) per K step; blocks of 32 M or N LBO = 8 KB apart, K groups SBO = 512 B apart
+        const uint64_t da = smem_desc_sw64(xa + ks * 1024, WG_BLK, 512);
+        const uint64_t dd = smem_desc_sw64(da0 + ks * 1024, WG_BLK, 512);
+        tc::mma_f16(tmem, da, dd, kIdescWg, (g > t0 || ks > 0) ? 1u : 0u);
       }
       mma_commit(done(j));
       ++done_issued[j];
-      // with this tile's MMAs queued, prefetch tile g + WG_AHEAD: it takes the input and dY slots
-      // of tile g - 1, so wait for tile g - 1's MMAs first (done at a column's first tile)
+      // with this tile's MMAs queued, prefetch tile g + WG_AHEAD: it takes the input slot and the
+      // dY ring slot of tile g - 1, so wait for tile g - 1's MMAs first
       if (loaded < t1 && loaded < col_end && loaded == g + WG_AHEAD) {
-        if (!settle((i - 1 + WG_DSLOTS) % WG_DSLOTS, a.spin)) { failed = true; break; }
+        if (!settle((i - 1 + WG_XSLOTS) % WG_XSLOTS, a.spin)) { failed = true; break; }
         load_tile(loaded, false);
         ++loaded;
       }
     }
     // drain (bounded): copies still in flight, then every MMA issued
-    for (int s = 0; s < WG_DSLOTS; ++s)
+    for (int s = 0; s < WG_XSLOTS; ++s)
       for (; full_used[s] < full_issued[s]; ++full_used[s])
         if (!mbar_wait(full(s), full_used[s] & 1)) failed = true;
-    for (int s = 0; s < WG_DSLOTS; ++s)
+    for (int s = 0; s < WG_XSLOTS; ++s)
       if (!settle(s, tc::kSpinLimit)) failed = true;
     if (failed) failed_s = 1;
   }
@@ -385,13 +391,13 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
   if (failed_s) {
     if (threadIdx.x == 0) atomicExch(a.error, 1);
   } else if (t1 > t0) {
-    // thread -> accumulator row m = 32 warp + lane: (dx, ci) = (m / 32, m % 32) for m < 96,
-    // m = 96 the bias gradient (dy = 0 accumulator only)
+    // thread -> accumulator row m = 32 warp + lane: (dx, ci) = (m / 32, m % 32) for m < 96, m = 96
+    // the sums of dY; column block kb holds dy = 2 - kb (db: block kb = 1 of row 96)
     const int m = warp * 32 + lane;
 #pragma unroll 1
-    for (int dy = 0; dy < 3; ++dy) {
+    for (int kb = 0; kb < 3; ++kb) {
       uint32_t r[32];
-      const uint32_t taddr = tmem + dy * 32 + ((uint32_t)(warp * 32) << 16);
+      const uint32_t taddr = tmem + kb * 32 + ((uint32_t)(warp * 32) << 16);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -402,10 +408,10 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (m < 96) {
-        const int k = (dy * 3 + m / 32) * 32 + (m % 32);
+        const int k = ((2 - kb) * 3 + m / 32) * 32 + (m % 32);
 #pragma unroll
         for (int co = 0; co < 32; ++co) atomicAdd(&a.dw[co * 288 + k], __uint_as_float(r[co]));
-      } else if (m == 96 && dy == 0) {
+      } else if (m == 96 && kb == 1) {
 #pragma unroll
         for (int co = 0; co < 32; ++co) atomicAdd(&a.db[co], __uint_as_float(r[co]));
       }
