@@ -16,9 +16,10 @@
 // flipped in space and transposed in channels (kernels dgrad_*); the weight gradient is
 // a GEMM over pixels (dW = sum_p dY(p)^T im2col(X)(p)) computed with the same MMA and
 // reduced into FP32 with atomics.  ReLU masks use the stored post-ReLU activations.
-// With tcgen05 available, the 32 -> 32 layers' forward, input gradients and weight
-// gradients run on the tcgen05 kernels of ils_cnn_tc.cu; these kernels remain for the
-// 3-channel first and last layers (and as the whole network without tcgen05).
+// With tcgen05 available, the 32 -> 32 layers' forward and input gradients and every
+// layer's weight gradient run on the tcgen05 kernels of ils_cnn_tc.cu (a 3-channel side
+// packed into 8-channel NHWC rows first); these kernels remain for the forward and input
+// gradient of the 3-channel first and last layers (and as the whole network without tcgen05).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -355,38 +356,83 @@ __global__ void __launch_bounds__(NTHREADS) conv_wgrad_kernel(WgradArgs a) {
 
 // ---------------------------------------------------------------- small helpers
 
+// Every weight array of the network in one launch: job j covers the flat indices
+// [start[j], start[j + 1]) (at most kMaxJobs jobs; a thread finds its job by a linear scan).
+constexpr int kMaxJobs = 12;
+
+__device__ __forceinline__ int find_job(const int* start, int count, int i) {
+  int j = 0;
+  while (j + 1 < count && i >= start[j + 1]) ++j;
+  return j;
+}
+
+struct PackJob {
+  const float* w;   // FP32 master weights [co_n][kpad]
+  bf16* out;        // [co_pad][kcols] BF16
+  int co_n, ci_n, co_pad, kcols, transpose_flip;
+};
+struct PackSet {
+  int count;
+  int start[kMaxJobs + 1];
+  PackJob job[kMaxJobs];
+};
+
 // Master FP32 weights [co][kpad] (column k = tap * ci_n + ci, tap = 3 ky + kx) -> BF16 GEMM
 // rows for the forward conv ([co_pad][kcols], rows >= co_n zero) or, with transpose_flip,
 // for the input-gradient conv: it maps the co_n-channel gradient to ci_n channels, so row
-// r = ci and column k' = tap' * co_n + co read the weight of tap 8 - tap' (the flipped kernel).
-__global__ void pack_weights_kernel(const float* __restrict__ w, int co_n, int ci_n, int co_pad, int kcols,
-                                    int transpose_flip, bf16* __restrict__ out) {
-  const int kpad = ci_n == 3 ? KIN : KMID;
-  const int total = co_pad * kcols;
+// r = ci and column k' = tap' * co_n + co read the weight of tap 8 - tap' (the flipped
+// kernel).  Every layer's arrays in one launch.
+__global__ void pack_all_kernel(PackSet s) {
+  const int total = s.start[s.count];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-    const int r = q / kcols, k = q - r * kcols;
+    const int j = find_job(s.start, s.count, q);
+    const PackJob& pj = s.job[j];
+    const int e = q - s.start[j];
+    const int kpad = pj.ci_n == 3 ? KIN : KMID;
+    const int r = e / pj.kcols, k = e - r * pj.kcols;
     float v = 0.0f;
-    if (!transpose_flip) {
-      if (r < co_n && k < 9 * ci_n) v = w[r * kpad + k];
+    if (!pj.transpose_flip) {
+      if (r < pj.co_n && k < 9 * pj.ci_n) v = pj.w[r * kpad + k];
     } else {
-      const int tapp = k / co_n, co = k - tapp * co_n;
-      if (r < ci_n && tapp < 9) v = w[co * kpad + (8 - tapp) * ci_n + r];
+      const int tapp = k / pj.co_n, co = k - tapp * pj.co_n;
+      if (r < pj.ci_n && tapp < 9) v = pj.w[co * kpad + (8 - tapp) * pj.ci_n + r];
     }
-    out[q] = __float2bfloat16_rn(v);
+    pj.out[e] = __float2bfloat16_rn(v);
   }
 }
 
+struct ParamSet {
+  int count;
+  int start[kMaxJobs + 1];
+  float* w[kMaxJobs];
+  float* g[kMaxJobs];
+  float* m[kMaxJobs];
+  float* v[kMaxJobs];
+};
+
 // Adam on FP32 master weights: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
-// w -= lr * mhat / (sqrt(vhat) + eps), with bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t.
-__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+// w -= lr * mhat / (sqrt(vhat) + eps), with bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t
+// (every weight and bias array of the network in one launch).
+__global__ void adam_all_kernel(ParamSet s, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int total = s.start[s.count];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int j = find_job(s.start, s.count, q);
+    const int i = q - s.start[j];
+    const float gi = s.g[j][i];
+    const float mi = b1 * s.m[j][i] + (1.0f - b1) * gi;
+    const float vi = b2 * s.v[j][i] + (1.0f - b2) * gi * gi;
+    s.m[j][i] = mi;
+    s.v[j][i] = vi;
+    s.w[j][i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// zeroes the gradient arrays g[j] of the set (one launch)
+__global__ void zero_all_kernel(ParamSet s) {
+  const int total = s.start[s.count];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int j = find_job(s.start, s.count, q);
+    s.g[j][q - s.start[j]] = 0.0f;
   }
 }
 
@@ -452,6 +498,7 @@ struct ils_cnn {
   bf16* wd[kLayers];     // input-gradient BF16 weights [cin][dg_kpad] (layers 1..5)
   bf16* act[kLayers - 1];  // post-ReLU activations of layers 0..4, NHWC BF16 [max_px][32]
   bf16* gact[2];           // gradient ping-pong, NHWC BF16
+  bf16* pk8;               // a 3-channel plane set as NHWC rows of 8 BF16 (tcgen05 weight gradients)
   int step;
   bool packed;
   int* err;    // device flag raised by a tensor-core kernel whose bounded wait gave up
@@ -474,17 +521,72 @@ void cnn_free(ils_cnn* n) {
   for (int l = 0; l < kLayers - 1; ++l) cudaFree(n->act[l]);
   cudaFree(n->gact[0]);
   cudaFree(n->gact[1]);
+  cudaFree(n->pk8);
   cudaFree(n->err);
   delete n;
 }
 
-cudaError_t cnn_pack(ils_cnn* n, cudaStream_t st) {
-  for (int l = 0; l < kLayers; ++l) {
-    pack_weights_kernel<<<64, 256, 0, st>>>(n->w[l], kCout[l], kCin[l], copad(l), kpad(l), 0, n->wf[l]);
-    if (l > 0) pack_weights_kernel<<<64, 256, 0, st>>>(n->w[l], kCout[l], kCin[l], 32, dg_kpad(l), 1, n->wd[l]);
+// planar FP32 [B][3][H][W] -> NHWC BF16 rows of 8 channels (3 values, then 5 zeros), the
+// layout the tensor-core weight gradient reads a 3-channel side in
+__global__ void planar3_to_nhwc8_kernel(const float* __restrict__ in, size_t hw, size_t n_px, bf16* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_px; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / hw, r = i - b * hw;
+    const float* src = in + b * 3 * hw + r;
+    __nv_bfloat162 c01 = __floats2bfloat162_rn(src[0], src[hw]);
+    __nv_bfloat162 c2z = __floats2bfloat162_rn(src[2 * hw], 0.0f);
+    uint4 v;
+    v.x = *reinterpret_cast<uint32_t*>(&c01);
+    v.y = *reinterpret_cast<uint32_t*>(&c2z);
+    v.z = 0u;
+    v.w = 0u;
+    reinterpret_cast<uint4*>(out)[i] = v;
   }
+}
+
+void planar3_to_nhwc8(const float* in, int B, int H, int W, bf16* out, cudaStream_t st) {
+  const size_t hw = (size_t)H * W, n_px = (size_t)B * hw;
+  const size_t blocks = (n_px + 255) / 256;
+  planar3_to_nhwc8_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(in, hw, n_px, out);
+}
+
+cudaError_t cnn_pack(ils_cnn* n, cudaStream_t st) {
+  // forward weights of every layer, input-gradient weights of layers 1..5
+  PackSet ps{};
+  int at = 0;
+  auto add = [&](const PackJob& j) {
+    ps.start[ps.count] = at;
+    ps.job[ps.count++] = j;
+    at += j.co_pad * j.kcols;
+  };
+  for (int l = 0; l < kLayers; ++l) {
+    add(PackJob{n->w[l], n->wf[l], kCout[l], kCin[l], copad(l), kpad(l), 0});
+    if (l > 0) add(PackJob{n->w[l], n->wd[l], kCout[l], kCin[l], 32, dg_kpad(l), 1});
+  }
+  ps.start[ps.count] = at;
+  pack_all_kernel<<<(at + 255) / 256, 256, 0, st>>>(ps);
   n->packed = true;
   return cudaGetLastError();
+}
+
+// the weights and biases of every layer with their gradients and Adam moments
+ParamSet cnn_params(ils_cnn* n) {
+  ParamSet s{};
+  int at = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const int sizes[2] = {kCout[l] * kpad(l), kCout[l]};
+    float* w[2] = {n->w[l], n->b[l]};
+    float* g[2] = {n->gw[l], n->gb[l]};
+    float* m[2] = {n->mw[l], n->mb[l]};
+    float* v[2] = {n->vw[l], n->vb[l]};
+    for (int t = 0; t < 2; ++t) {
+      const int j = s.count++;
+      s.start[j] = at;
+      s.w[j] = w[t]; s.g[j] = g[t]; s.m[j] = m[t]; s.v[j] = v[t];
+      at += sizes[t];
+    }
+  }
+  s.start[s.count] = at;
+  return s;
 }
 
 dim3 tile_grid(int B, int H, int W) { return dim3((W + TW - 1) / TW, (H + TH - 1) / TH, B); }
@@ -524,6 +626,7 @@ ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
   n->tc = ils::conv32_tc_available() && !(tcenv != nullptr && tcenv[0] == '0');
   if (e == cudaSuccess && n->tc) e = ils::conv32_tc_set_attributes();
   if (e == cudaSuccess && n->tc) e = ils::warm_fused_set_attributes();
+  if (e == cudaSuccess && n->tc) e = cudaMalloc((void**)&n->pk8, n->max_px * 8 * sizeof(bf16));
   if (e == cudaSuccess) {
     cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)conv_smem(false, 4));
@@ -738,10 +841,8 @@ int ils_cnn_uses_tcgen05(const ils_cnn* n) { return n != nullptr && n->tc ? 1 : 
 ils_status ils_cnn_zero_grad(ils_cnn* n, void* stream) {
   if (n == nullptr) return ILS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (int l = 0; l < kLayers; ++l) {
-    cudaMemsetAsync(n->gw[l], 0, (size_t)kCout[l] * kpad(l) * 4, st);
-    cudaMemsetAsync(n->gb[l], 0, (size_t)kCout[l] * 4, st);
-  }
+  const ParamSet ps = cnn_params(n);
+  zero_all_kernel<<<(ps.start[ps.count] + 255) / 256, 256, 0, st>>>(ps);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "zero_grad");
 }
@@ -762,17 +863,28 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
     WgradArgs w{};
     w.B = B; w.H = H; w.W = W; w.dy_nhwc = dy_nhwc; w.dy_planar = dy_planar;
     w.dw = n->gw[l]; w.db = n->gb[l]; w.cout = kCout[l]; w.tiles_x = grid.x; w.tiles_y = grid.y;
-    if (l == 0) {
+    if (n->tc) {
+      // every layer on tcgen05; a 3-channel side (f for layer 0, dL/du0 for layer 5) is first
+      // packed into NHWC rows of 8 channels, rounded to BF16 as the mma.sync path stages it
+      cudaError_t e;
+      if (l == 0) {
+        planar3_to_nhwc8(f, B, H, W, n->pk8, st);
+        e = ils::launch_wgrad_tc(B, H, W, n->pk8, 3, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
+      } else if (dy_planar != nullptr) {
+        planar3_to_nhwc8(dy_planar, B, H, W, n->pk8, st);
+        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, n->pk8, kCout[l], n->gw[l], kpad(l), n->gb[l], n->err,
+                                 st);
+      } else {
+        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
+      }
+      if (e != cudaSuccess && tc_err == cudaSuccess) tc_err = e;
+    } else if (l == 0) {
       w.in_planar = f;
       conv_wgrad_kernel<true, false><<<wg_grid, NTHREADS, wgrad_smem(true), st>>>(w);
     } else {
       w.in_nhwc = n->act[l - 1];
       if (dy_planar != nullptr)
         conv_wgrad_kernel<false, true><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
-      else if (n->tc) {  // the 32 -> 32 layers on tcgen05
-        const cudaError_t e = ils::launch_wgrad32_tc(B, H, W, n->act[l - 1], dy_nhwc, n->gw[l], n->gb[l], n->err, st);
-        if (e != cudaSuccess && tc_err == cudaSuccess) tc_err = e;
-      }
       else
         conv_wgrad_kernel<false, false><<<wg_grid, NTHREADS, wgrad_smem(false), st>>>(w);
     }
@@ -814,12 +926,8 @@ ils_status ils_cnn_adam_step(ils_cnn* n, float lr, float beta1, float beta2, flo
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   n->step += 1;
   const float c1 = 1.0f - std::pow(beta1, (float)n->step), c2 = 1.0f - std::pow(beta2, (float)n->step);
-  for (int l = 0; l < kLayers; ++l) {
-    const int nw = kCout[l] * kpad(l);
-    adam_kernel<<<(nw + 255) / 256, 256, 0, st>>>(n->w[l], n->gw[l], n->mw[l], n->vw[l], nw, lr, beta1, beta2, eps,
-                                                  c1, c2);
-    adam_kernel<<<1, 64, 0, st>>>(n->b[l], n->gb[l], n->mb[l], n->vb[l], kCout[l], lr, beta1, beta2, eps, c1, c2);
-  }
+  const ParamSet ps = cnn_params(n);
+  adam_all_kernel<<<(ps.start[ps.count] + 255) / 256, 256, 0, st>>>(ps, lr, beta1, beta2, eps, c1, c2);
   cudaError_t e = cnn_pack(n, st);
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "adam step");
 }

@@ -224,8 +224,11 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 }
 
 // ---------------------------------------------------------------- weight gradient
-// dW[co][(3 dy + dx) 32 + ci] += sum_p dY[p][co] X[p + (dy - 1, dx - 1)][ci] and db[co] +=
-// sum_p dY[p][co] over every pixel p of the batch (the 32 -> 32 layers' weight gradients).
+// dW[co][(3 dy + dx) ci_n + ci] += sum_p dY[p][co] X[p + (dy - 1, dx - 1)][ci] and db[co] +=
+// sum_p dY[p][co] over every pixel p of the batch: the weight gradient of a conv3x3 with
+// ci_n <= 32 input and co_n <= 32 output channels (the 32 -> 32 layers; the 3 -> 32 and
+// 32 -> 3 layers with their 3-channel side packed to 8-channel NHWC rows, channels 3-7 zero,
+// which the tensor map's zero fill widens to 32).
 //
 // Written per input row q = p + (dy - 1, 0): the tile of 128 pixels of input row yq contributes
 // D[M = (dx, ci)][N = (kb, co)] += sum_x X[yq][x + dx - 1][ci] dY[yq - 1 + kb][x][co], and the
@@ -263,8 +266,9 @@ constexpr uint32_t kIdescWg = tc::idesc_bf16(128, 96) | (1u << 15) | (1u << 16);
 
 struct WgArgs {
   int B, H, W;
-  float* dw;    // [32 co][288] FP32, column (3 dy + dx) 32 + ci (accumulated)
-  float* db;    // [32] FP32 (accumulated)
+  int ci_n, co_n, kpad;  // input and output channels (<= 32), row length of dW
+  float* dw;    // [co_n][kpad] FP32, column (3 dy + dx) ci_n + ci (accumulated)
+  float* db;    // [co_n] FP32 (accumulated)
   int* error;
   uint32_t spin;
 };
@@ -407,13 +411,15 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (m < 96) {
-        const int k = ((2 - kb) * 3 + m / 32) * 32 + (m % 32);
+      if (m < 96 && (m % 32) < a.ci_n) {
+        const int k = ((2 - kb) * 3 + m / 32) * a.ci_n + (m % 32);
 #pragma unroll
-        for (int co = 0; co < 32; ++co) atomicAdd(&a.dw[co * 288 + k], __uint_as_float(r[co]));
+        for (int co = 0; co < 32; ++co)
+          if (co < a.co_n) atomicAdd(&a.dw[co * a.kpad + k], __uint_as_float(r[co]));
       } else if (m == 96 && kb == 1) {
 #pragma unroll
-        for (int co = 0; co < 32; ++co) atomicAdd(&a.db[co], __uint_as_float(r[co]));
+        for (int co = 0; co < 32; ++co)
+          if (co < a.co_n) atomicAdd(&a.db[co], __uint_as_float(r[co]));
       }
     }
   }
@@ -461,11 +467,14 @@ bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x) {
+bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int ch) {
   EncodeTiledFn enc = encode_fn();
-  if (enc == nullptr) return false;
-  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+  if (enc == nullptr || (ch != 8 && ch != 32)) return false;
+  // ch = 8: rows of 8 channels (16 bytes per pixel); the 32-channel box reads channels 8-31
+  // as zeros (out of the tensor)
+  const cuuint64_t px = (cuuint64_t)ch * 2;
+  const cuuint64_t dims[4] = {(cuuint64_t)ch, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {px, (cuuint64_t)W * px, (cuuint64_t)H * W * px};
   const cuuint32_t box[4] = {32, (cuuint32_t)box_x, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(act), dims, strides, box, estr,
@@ -481,14 +490,17 @@ cudaError_t conv32_tc_set_attributes() {
                               cnn_tc::WG_SMEM);
 }
 
-// dW += weight gradient, db += bias gradient of a 32 -> 32 conv3x3 from its NHWC BF16 input x
-// and output gradient dy (B x H x W x 32 each); dw is [32][288] FP32, db [32] FP32.
-cudaError_t launch_wgrad32_tc(int B, int H, int W, const void* x, const void* dy, float* dw, float* db, int* error,
-                              cudaStream_t st) {
+// dW += weight gradient, db += bias gradient of a conv3x3 from its NHWC BF16 input x and
+// output gradient dy (B x H x W x 32, or x 8 for a 3-channel side packed with zeros in
+// channels 3-7); dw is [co_n][kpad] FP32 with column (3 dy + dx) ci_n + ci, db [co_n] FP32.
+cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int ci_n, const void* dy, int co_n, float* dw,
+                            int kpad, float* db, int* error, cudaStream_t st) {
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
+  if (ci_n < 1 || ci_n > 32 || co_n < 1 || co_n > 32 || kpad < 9 * ci_n) return cudaErrorInvalidValue;
   CUtensorMap xm, dm;
-  if (!make_nhwc32_map_sw64(&xm, x, B, H, W, WG_TILE) || !make_nhwc32_map_sw64(&dm, dy, B, H, W, WG_TILE))
+  if (!make_nhwc32_map_sw64(&xm, x, B, H, W, WG_TILE, ci_n <= 8 ? 8 : 32) ||
+      !make_nhwc32_map_sw64(&dm, dy, B, H, W, WG_TILE, co_n <= 8 ? 8 : 32))
     return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -497,6 +509,7 @@ cudaError_t launch_wgrad32_tc(int B, int H, int W, const void* x, const void* dy
   const int grid = tiles < sms ? (int)tiles : sms;   // one persistent CTA per SM
   WgArgs a{};
   a.B = B; a.H = H; a.W = W;
+  a.ci_n = ci_n; a.co_n = co_n; a.kpad = kpad;
   a.dw = dw;
   a.db = db;
   a.error = error;

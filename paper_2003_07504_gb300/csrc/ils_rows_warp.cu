@@ -563,7 +563,7 @@ constexpr WarpRowEntry warp_entry() {
 // CTA also holds its 2M-entry twiddle table (16 B per complex point of a row), which is what
 // limits the 1920-wide rows to the per-pair stencil without f staging at two CTAs per SM.
 const WarpRowEntry kWarpRows[] = {
-    warp_entry<4, 14, 16, true, true>(),     // W = 256
+    warp_entry<4, 6, 8, true, true, 3>(),    // W = 256: 8-warp CTAs, three per SM (80 registers)
     warp_entry<8, 14, 16, true, true>(),     // W = 512
     warp_entry<10, 14, 16, true, true>(),    // W = 640
     warp_entry<20, 6, 8, true, true>(),      // W = 1280
@@ -575,6 +575,7 @@ const WarpRowEntry kWarpRows[] = {
     warp_entry<30, 6, 8, false, true, 2, false, true>(),    // W = 1920, shared-mu stencil
     warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
     warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
+    warp_entry<4, 14, 16, true, true>(),     // W = 256, 16-warp CTAs, one per SM (89 registers)
 };
 
 }  // namespace

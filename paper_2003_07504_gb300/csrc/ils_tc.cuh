@@ -92,8 +92,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // pixels x box_y rows x 1 image, zero fill out of bounds (host; false when the driver entry
 // point is missing or the encoding fails).
 bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y);
-// The same tensor with a box of all 32 channels x box_x pixels x 1 row, written to shared
-// memory with the 64-byte swizzle.
-bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x);
+// An NHWC BF16 tensor of B x H x W x ch (ch = 32, or 8) with a box of 32 channels x box_x
+// pixels x 1 row, written to shared memory with the 64-byte swizzle (for ch = 8 the box's
+// channels 8-31 are the zero fill).
+bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int ch);
 
 }  // namespace ils

@@ -294,7 +294,7 @@ def test_column_plan_variants_agree(ils, monkeypatch, H, W):
             assert_parity(frames[0][1].cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512)])
+@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512), (20, 256)])
 def test_row_plan_variants_agree(ils, monkeypatch, H, W):
     # every warp-per-row and fixed-plan row variant of the length against the oracle
     f = image(H, W, 2, seed=W + H, preset="hd")
