@@ -485,6 +485,17 @@ def batch_leg(ils, torch, dev, steps, flush):
     for pl in plans:
         pl.close()
     serial_ms = tot / steps
+    # what a persistent work-queue kernel could reach at best: every frame at its size class's
+    # saturated rate, measured as one 24-channel plan call per class (the passes fill the GPU,
+    # so fill, drain and launch gaps are small against the work), summed over the batch
+    per_px = {}
+    for hh, ww in BATCH_SIZES:
+        fc = torch.from_numpy(synth.preset_image(hh, ww, 24, "hd", 4100)).to(dev)
+        uc = torch.empty_like(fc)
+        with ils.Plan(hh, ww, 24, 1.0, 0.8, EPS, N_ITERS) as pl:
+            per_px[(hh, ww)] = _timed_smooth(pl, fc, uc, torch, max(3, steps), flush) / (24 * hh * ww)
+        del fc, uc
+    bound_ms = sum(per_px[(f.shape[1], f.shape[2])] * 3 * f.shape[1] * f.shape[2] for f, *_ in frames)
     nbytes = sum(bytes_model(f.shape[1], f.shape[2], 3, N_ITERS)[1] for f, *_ in frames)
     peak, _ = load_peaks()
     return {"workload": "64 RGB FP32 frames, sizes uniform over 640x480 / 1280x720 / 1920x1080 / 2048x1536, "
@@ -492,7 +503,11 @@ def batch_leg(ils, torch, dev, steps, flush):
             "ms_per_batch": ms, "frames_per_s": 64 / (ms / 1000.0), "mpix_per_s": px / (ms / 1000.0) / 1e6,
             "algorithmic_gbs": nbytes / (ms / 1000.0) / 1e9, "frac_of_hbm_peak": nbytes / (ms / 1000.0) / 1e9 / peak,
             "frames_one_after_another_ms": serial_ms,
-            "note": "frames_one_after_another_ms: the same 64 frames as 64 plan calls on one stream"}
+            "saturated_class_bound_ms": bound_ms,
+            "saturated_us_per_mpix_channel": {f"{hh}x{ww}": 1e9 * v for (hh, ww), v in per_px.items()},
+            "note": "frames_one_after_another_ms: the same 64 frames as 64 plan calls on one stream; "
+                    "saturated_class_bound_ms: sum over the frames of 3 H W x the per-pixel time of a "
+                    "24-channel plan call of the frame's size (a persistent kernel's best case)"}
 
 
 def batch_4k_leg(ils, torch, dev, steps, flush):

@@ -786,9 +786,15 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   const dim3 grid = tile_grid(B, H, W);
   ConvArgs a{};
   a.B = B; a.H = H; a.W = W;
-  // layer 0: planar 3 -> 32, ReLU
-  a.in_planar = f; a.wt = n->wf[0]; a.bias = n->b[0]; a.out_nhwc = n->act[0]; a.relu = 1; a.cout = 32;
-  conv_fwd_kernel<true, 4, false><<<grid, NTHREADS, conv_smem(true, 4), st>>>(a);
+  // layer 0: planar 3 -> 32, ReLU (tcgen05: f packed into 8-channel NHWC rows first)
+  if (n->tc) {
+    planar3_to_nhwc8(f, B, H, W, n->pk8, st);
+    cudaError_t e = ils::launch_conv3_tc(B, H, W, n->pk8, n->wf[0], n->b[0], n->act[0], nullptr, 1, n->err, st);
+    if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
+  } else {
+    a.in_planar = f; a.wt = n->wf[0]; a.bias = n->b[0]; a.out_nhwc = n->act[0]; a.relu = 1; a.cout = 32;
+    conv_fwd_kernel<true, 4, false><<<grid, NTHREADS, conv_smem(true, 4), st>>>(a);
+  }
   for (int l = 1; l < kLayers - 1; ++l) {
     if (n->tc) {
       cudaError_t e = ils::launch_conv32_tc(B, H, W, n->act[l - 1], n->wf[l], n->b[l], n->act[l], nullptr, 1, n->err, st);
@@ -891,7 +897,12 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
   };
   // layer 5 (32 -> 3): its output gradient is dL/du0 (the residual passes f through)
   wgrad(kLayers - 1, nullptr, grad_u0);
-  {
+  if (n->tc) {
+    // the weight gradient above left dL/du0 packed in pk8
+    cudaError_t e = ils::launch_conv3_tc(B, H, W, n->pk8, n->wd[kLayers - 1], nullptr, n->gact[0], n->act[kLayers - 2],
+                                         0, n->err, st);
+    if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
+  } else {
     ConvArgs a{};
     a.B = B; a.H = H; a.W = W; a.in_planar = grad_u0; a.wt = n->wd[kLayers - 1];
     a.out_nhwc = n->gact[0]; a.mask = n->act[kLayers - 2]; a.cout = 32;

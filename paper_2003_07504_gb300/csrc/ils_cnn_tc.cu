@@ -57,7 +57,8 @@ using tc::mma_commit;
 
 struct TcArgs {
   int B, H, W;
-  const bf16* wt;     // [32 co][288] BF16, column k = tap * 32 + ci (as for the mma.sync kernels)
+  const bf16* wt;     // [32 co][288] BF16, column k = tap * 32 + ci (as for the mma.sync kernels);
+                      // IN8: [32 co][32], column k = tap * 3 + ci (k < 27)
   const float* bias;  // [32] or null
   bf16* out;          // NHWC BF16
   const bf16* mask;   // NHWC BF16, or null: output zeroed where mask <= 0
@@ -70,27 +71,65 @@ constexpr int STAGES = 3;                               // input tiles in flight
 constexpr int SMEM_PIPE = STAGES * A_BYTES + B_BYTES + 128;
 constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
+// The 3-channel variant (IN8): the input is an NHWC row of 8 channels (3 values, 5 zeros), one
+// chunk plane per stage.  A tap is then half a K = 16 step, so step j pairs taps 2j and 2j + 1:
+// the descriptor starts at the first tap's pixel and its K-direction stride (LBO) is the byte
+// distance to the second tap's pixel.  The ninth tap pairs with tap 7 under zero weights, so
+// every operand byte read is a copied pixel.  Weights: 10 K-chunks [chunk][co][8], chunk 2j + h
+// holding tap 2j + h (chunk 8 zero, chunk 9 tap 8), channels 3-7 zero.
+constexpr int IN8_STEPS = 5;
+constexpr int IN8_CHUNKS = 2 * IN8_STEPS;
+constexpr int IN8_A_BYTES = PLANE;
+constexpr int IN8_TMA_BYTES = 3 * HALO_W * 16;             // 6240
+constexpr int IN8_B_BYTES = IN8_CHUNKS * 32 * 16;          // 5120
+constexpr int IN8_STAGES = 6;
+constexpr int SMEM_PIPE_IN8 = IN8_STAGES * IN8_A_BYTES + IN8_B_BYTES + 128;
+
+__host__ __device__ constexpr int in8_tap(int chunk) { return chunk < 8 ? chunk : (chunk == 8 ? -1 : 8); }
+
 // Persistent, warp-specialized pipeline.  Tile i uses input stage i % STAGES and
 // accumulator i % 2 (32 tensor-memory columns each).  Barriers (phase parity from the
 // use count): full[s] TMA -> MMA, empty[s] MMA -> TMA (tcgen05.commit), accf[b] MMA ->
 // epilogue, acce[b] epilogue -> MMA (128 arrivals).
+template <bool IN8>
 __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
+  constexpr int NST = IN8 ? IN8_STAGES : STAGES;
+  constexpr int ABYTES = IN8 ? IN8_A_BYTES : A_BYTES;
+  constexpr int BBYTES = IN8 ? IN8_B_BYTES : B_BYTES;
   extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* sB = sm + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + STAGES * A_BYTES + B_BYTES);
+  unsigned char* sB = sm + NST * ABYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NST * ABYTES + BBYTES);
   __shared__ uint32_t tmem_base_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto full = [&](int s) { return saddr(&bars[s]); };
-  auto empty = [&](int s) { return saddr(&bars[STAGES + s]); };
-  auto accf = [&](int b) { return saddr(&bars[2 * STAGES + b]); };
-  auto acce = [&](int b) { return saddr(&bars[2 * STAGES + 2 + b]); };
+  auto empty = [&](int s) { return saddr(&bars[NST + s]); };
+  auto accf = [&](int b) { return saddr(&bars[2 * NST + b]); };
+  auto acce = [&](int b) { return saddr(&bars[2 * NST + 2 + b]); };
 
-  for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
-    const int kc = q >> 5, co = q & 31;
-    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
+  if (IN8) {
+    for (int q = threadIdx.x; q < IN8_CHUNKS * 32; q += blockDim.x) {
+      const int kc = q >> 5, co = q & 31, tap = in8_tap(kc);
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (tap >= 0) {
+        const bf16* src = a.wt + co * 32 + tap * 3;
+        __nv_bfloat162 c01, c2z;
+        c01.x = src[0];
+        c01.y = src[1];
+        c2z.x = src[2];
+        c2z.y = __float2bfloat16_rn(0.0f);
+        w[0] = *reinterpret_cast<uint32_t*>(&c01);
+        w[1] = *reinterpret_cast<uint32_t*>(&c2z);
+      }
+      *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
+      const int kc = q >> 5, co = q & 31;
+      *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
+    }
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
@@ -123,34 +162,46 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       const int b = tile / (a.H * tiles_x);
       const int rr = tile - b * a.H * tiles_x;
       const int y = rr / tiles_x, x0 = (rr - y * tiles_x) * TILE;
-      const int s = i % STAGES;
-      if (i >= STAGES && !mbar_wait(empty(s), ((i / STAGES) & 1) ^ 1, a.spin)) { failed = true; break; }
-      mbar_expect_tx(full(s), TMA_BYTES);
-      for (int c = 0; c < 4; ++c)
-        tma_load_4d(saddr(sm + s * A_BYTES + c * PLANE), &in_map, c * 8, x0 - 1, y - 1, b, full(s));
+      const int s = i % NST;
+      if (i >= NST && !mbar_wait(empty(s), ((i / NST) & 1) ^ 1, a.spin)) { failed = true; break; }
+      mbar_expect_tx(full(s), IN8 ? IN8_TMA_BYTES : TMA_BYTES);
+      for (int c = 0; c < (IN8 ? 1 : 4); ++c)
+        tma_load_4d(saddr(sm + s * ABYTES + c * PLANE), &in_map, c * 8, x0 - 1, y - 1, b, full(s));
       issued = i + 1;
     }
     // before the CTA may end, every copy issued must have landed (bounded)
-    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
-      if (!mbar_wait(full(i % STAGES), (i / STAGES) & 1)) failed = true;
+    for (int i = (issued > NST ? issued - NST : 0); i < issued; ++i)
+      if (!mbar_wait(full(i % NST), (i / NST) & 1)) failed = true;
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     int issued = 0;
     for (int i = 0; i < my_tiles; ++i) {
-      const int s = i % STAGES, acc = i & 1;
-      if (!mbar_wait(full(s), (i / STAGES) & 1, a.spin)) { failed = true; break; }
+      const int s = i % NST, acc = i & 1;
+      if (!mbar_wait(full(s), (i / NST) & 1, a.spin)) { failed = true; break; }
       if (i >= 2 && !mbar_wait(acce(acc), ((i >> 1) & 1) ^ 1, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = saddr(sm + s * A_BYTES), b0 = saddr(sB), d = tmem + acc * 32;
+      const uint32_t a0 = saddr(sm + s * ABYTES), b0 = saddr(sB), d = tmem + acc * 32;
+      if (IN8) {
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const uint32_t at = a0 + (uint32_t)((dy * HALO_W + dx) * 16);
+        for (int j = 0; j < IN8_STEPS; ++j) {
+          // taps t0 (K half 0) and t1 (K half 1) of this step; byte offset of tap t's pixel 0
+          const int t0 = j < 4 ? 2 * j : 7, t1 = j < 4 ? 2 * j + 1 : 8;
+          const int o0 = ((t0 / 3) * HALO_W + t0 % 3) * 16, o1 = ((t1 / 3) * HALO_W + t1 % 3) * 16;
+          const uint64_t da = smem_desc(a0 + (uint32_t)o0, (uint32_t)(o1 - o0), 128);
+          const uint64_t db = smem_desc(b0 + (uint32_t)(2 * j * 512), 512, 128);
+          mma_f16(d, da, db, j ? 1u : 0u);
+        }
+      } else {
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint64_t da = smem_desc(at + kk * 2 * PLANE, PLANE, 128);
-          const uint64_t db = smem_desc(b0 + (uint32_t)((tap * 4 + kk * 2) * 512), 512, 128);
-          mma_f16(d, da, db, (tap | kk) ? 1u : 0u);
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+          const uint32_t at = a0 + (uint32_t)((dy * HALO_W + dx) * 16);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t da = smem_desc(at + kk * 2 * PLANE, PLANE, 128);
+            const uint64_t db = smem_desc(b0 + (uint32_t)((tap * 4 + kk * 2) * 512), 512, 128);
+            mma_f16(d, da, db, (tap | kk) ? 1u : 0u);
+          }
         }
       }
       mma_commit(empty(s));
@@ -454,12 +505,13 @@ EncodeTiledFn encode_fn() {
 
 bool conv32_tc_available() { return encode_fn() != nullptr; }
 
-bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y) {
+bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y, int ch) {
   EncodeTiledFn enc = encode_fn();
-  if (enc == nullptr) return false;
+  if (enc == nullptr || (ch != 8 && ch != 32)) return false;
   // dims (innermost first): channel, x, y, image; box: 8 channels x box_x pixels x box_y rows x 1
-  const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+  const cuuint64_t px = (cuuint64_t)ch * 2;
+  const cuuint64_t dims[4] = {(cuuint64_t)ch, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {px, (cuuint64_t)W * px, (cuuint64_t)H * W * px};
   const cuuint32_t box[4] = {8, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(act), dims, strides, box, estr,
@@ -483,8 +535,11 @@ bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W
 }
 
 cudaError_t conv32_tc_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cnn_tc::SMEM_PIPE);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           cnn_tc::SMEM_PIPE_IN8);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(cnn_tc::conv32_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               cnn_tc::WG_SMEM);
@@ -519,13 +574,16 @@ cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int ci_n, const 
   return cudaGetLastError();
 }
 
-// out = conv3x3_{32->32}(in) (+bias, ReLU | mask) on NHWC BF16 tensors of B x H x W x 32.
-cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
-                             const void* mask, int relu, int* error, cudaStream_t st) {
+namespace {
+
+// out = conv3x3_{cin->32}(in) (+bias, ReLU | mask): in is NHWC BF16 with 32 channels, or
+// (in8) 8 channels of which the first 3 are the input
+cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
+                           const void* mask, int relu, int* error, cudaStream_t st) {
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
   CUtensorMap map;
-  if (!make_nhwc32_map(&map, in, B, H, W, HALO_W, 3)) return cudaErrorInvalidValue;
+  if (!make_nhwc32_map(&map, in, B, H, W, HALO_W, 3, in8 ? 8 : 32)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -541,8 +599,26 @@ cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt
   a.error = error;
   const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
   a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
-  conv32_tc_kernel<<<grid, NTHR, SMEM_PIPE, st>>>(map, a);
+  if (in8)
+    conv32_tc_kernel<true><<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, a);
+  else
+    conv32_tc_kernel<false><<<grid, NTHR, SMEM_PIPE, st>>>(map, a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+// out = conv3x3_{32->32}(in) (+bias, ReLU | mask) on NHWC BF16 tensors of B x H x W x 32.
+cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
+                             const void* mask, int relu, int* error, cudaStream_t st) {
+  return launch_conv_tc(false, B, H, W, in, wt, bias, out, mask, relu, error, st);
+}
+
+// out = conv3x3_{3->32}(in) (+bias, ReLU | mask): in is NHWC BF16 rows of 8 channels (3 values,
+// then zeros), wt [32][32] BF16 with column tap * 3 + ci, out NHWC BF16 x 32.
+cudaError_t launch_conv3_tc(int B, int H, int W, const void* in8, const void* wt, const float* bias, void* out,
+                            const void* mask, int relu, int* error, cudaStream_t st) {
+  return launch_conv_tc(true, B, H, W, in8, wt, bias, out, mask, relu, error, st);
 }
 
 }  // namespace ils

@@ -233,6 +233,10 @@ bool conv32_tc_available();
 cudaError_t conv32_tc_set_attributes();
 cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,
                              const void* mask, int relu, int* error, cudaStream_t st);
+// 3->32 channel conv3x3 on tcgen05: in is NHWC BF16 rows of 8 channels (3 values, then zeros),
+// wt [32][32] BF16 with column tap * 3 + ci (k < 27)
+cudaError_t launch_conv3_tc(int B, int H, int W, const void* in8, const void* wt, const float* bias, void* out,
+                            const void* mask, int relu, int* error, cudaStream_t st);
 // weight and bias gradients of a conv3x3 with ci_n, co_n <= 32 on tcgen05, accumulated into
 // dw [co_n][kpad] (column (3 dy + dx) ci_n + ci) and db [co_n]; x and dy are NHWC BF16 rows of
 // 32 channels, or of 8 (channels beyond ci_n / co_n zero) for a side with at most 8

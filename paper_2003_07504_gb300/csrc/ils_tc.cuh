@@ -88,10 +88,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 
 }  // namespace tc
 
-// Tensor map of an NHWC BF16 tensor of B x H x W x 32 with a box of 8 channels x box_x
-// pixels x box_y rows x 1 image, zero fill out of bounds (host; false when the driver entry
-// point is missing or the encoding fails).
-bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y);
+// Tensor map of an NHWC BF16 tensor of B x H x W x ch (ch = 32, or 8) with a box of 8 channels
+// x box_x pixels x box_y rows x 1 image, zero fill out of bounds (host; false when the driver
+// entry point is missing or the encoding fails).
+bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int box_y, int ch = 32);
 // An NHWC BF16 tensor of B x H x W x ch (ch = 32, or 8) with a box of 32 channels x box_x
 // pixels x 1 row, written to shared memory with the 64-byte swizzle (for ch = 8 the box's
 // channels 8-31 are the zero fill).

@@ -191,8 +191,9 @@ def test_warm_smoother_paths(ws):
 
 @pytest.mark.parametrize("B,H,W", [(1, 12, 128), (2, 9, 200), (1, 40, 384)])
 def test_tcgen05_layers_match_the_mma_sync_kernels(ws, monkeypatch, B, H, W):
-    # the 32 -> 32 layers on tcgen05 (TMA + tensor memory) against the mma.sync kernels:
-    # same BF16 inputs, FP32 accumulation in a different order -> BF16-rounding-level agreement
+    # the tcgen05 kernels (TMA + tensor memory: every convolution but the last layer's forward,
+    # every weight gradient) against the mma.sync kernels: same BF16 inputs, FP32 accumulation
+    # in a different order -> BF16-rounding-level agreement
     import torch
     p = random_params(ws, 7)
     f = torch.from_numpy(synth.preset_image(H, W, 3 * B, "small", 3 + W).reshape(B, 3, H, W)).cuda()
