@@ -437,10 +437,27 @@ __global__ void zero_all_kernel(ParamSet s) {
 }
 
 // grad = 2 (u0 - target) / n_total; loss partial sums of (u0 - target)^2 into *loss
+// (16-byte accesses when the three arrays allow them, the remainder element-wise)
 __global__ void mse_kernel(const float* u0, const float* target, float* grad, size_t n, float scale,
                            float* loss) {
   float s = 0.0f;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(u0) | reinterpret_cast<uintptr_t>(target) | reinterpret_cast<uintptr_t>(grad)) &
+       15) == 0) {
+    const size_t n4 = n / 4;
+    const float4* a = reinterpret_cast<const float4*>(u0);
+    const float4* b = reinterpret_cast<const float4*>(target);
+    float4* g = reinterpret_cast<float4*>(grad);
+    for (size_t i = t0; i < n4; i += stride) {
+      const float4 x = a[i], y = b[i];
+      const float d0 = x.x - y.x, d1 = x.y - y.y, d2 = x.z - y.z, d3 = x.w - y.w;
+      g[i] = make_float4(2.0f * d0 * scale, 2.0f * d1 * scale, 2.0f * d2 * scale, 2.0f * d3 * scale);
+      s += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+    }
+    done = n4 * 4;
+  }
+  for (size_t i = done + t0; i < n; i += stride) {
     const float d = u0[i] - target[i];
     grad[i] = 2.0f * d * scale;
     s += d * d;
@@ -498,7 +515,8 @@ struct ils_cnn {
   bf16* wd[kLayers];     // input-gradient BF16 weights [cin][dg_kpad] (layers 1..5)
   bf16* act[kLayers - 1];  // post-ReLU activations of layers 0..4, NHWC BF16 [max_px][32]
   bf16* gact[2];           // gradient ping-pong, NHWC BF16
-  bf16* pk8;               // a 3-channel plane set as NHWC rows of 8 BF16 (tcgen05 weight gradients)
+  bf16* pk8;               // a 3-channel plane set as NHWC rows of 8 BF16 (dL/du0 in the backward)
+  bf16* pkf;               // f as NHWC rows of 8 BF16, written by the forward (layer 0's input)
   int step;
   bool packed;
   int* err;    // device flag raised by a tensor-core kernel whose bounded wait gave up
@@ -522,6 +540,7 @@ void cnn_free(ils_cnn* n) {
   cudaFree(n->gact[0]);
   cudaFree(n->gact[1]);
   cudaFree(n->pk8);
+  cudaFree(n->pkf);
   cudaFree(n->err);
   delete n;
 }
@@ -627,6 +646,7 @@ ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
   if (e == cudaSuccess && n->tc) e = ils::conv32_tc_set_attributes();
   if (e == cudaSuccess && n->tc) e = ils::warm_fused_set_attributes();
   if (e == cudaSuccess && n->tc) e = cudaMalloc((void**)&n->pk8, n->max_px * 8 * sizeof(bf16));
+  if (e == cudaSuccess && n->tc) e = cudaMalloc((void**)&n->pkf, n->max_px * 8 * sizeof(bf16));
   if (e == cudaSuccess) {
     cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)conv_smem(false, 4));
@@ -788,8 +808,8 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   a.B = B; a.H = H; a.W = W;
   // layer 0: planar 3 -> 32, ReLU (tcgen05: f packed into 8-channel NHWC rows first)
   if (n->tc) {
-    planar3_to_nhwc8(f, B, H, W, n->pk8, st);
-    cudaError_t e = ils::launch_conv3_tc(B, H, W, n->pk8, n->wf[0], n->b[0], n->act[0], nullptr, 1, n->err, st);
+    planar3_to_nhwc8(f, B, H, W, n->pkf, st);
+    cudaError_t e = ils::launch_conv3_tc(B, H, W, n->pkf, n->wf[0], n->b[0], n->act[0], nullptr, 1, n->err, st);
     if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
   } else {
     a.in_planar = f; a.wt = n->wf[0]; a.bias = n->b[0]; a.out_nhwc = n->act[0]; a.relu = 1; a.cout = 32;
@@ -870,12 +890,11 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
     w.B = B; w.H = H; w.W = W; w.dy_nhwc = dy_nhwc; w.dy_planar = dy_planar;
     w.dw = n->gw[l]; w.db = n->gb[l]; w.cout = kCout[l]; w.tiles_x = grid.x; w.tiles_y = grid.y;
     if (n->tc) {
-      // every layer on tcgen05; a 3-channel side (f for layer 0, dL/du0 for layer 5) is first
+      // every layer on tcgen05; a 3-channel side (f for layer 0, dL/du0 for layer 5) is
       // packed into NHWC rows of 8 channels, rounded to BF16 as the mma.sync path stages it
       cudaError_t e;
-      if (l == 0) {
-        planar3_to_nhwc8(f, B, H, W, n->pk8, st);
-        e = ils::launch_wgrad_tc(B, H, W, n->pk8, 3, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
+      if (l == 0) {  // f as the forward packed it (the activations are the forward's too)
+        e = ils::launch_wgrad_tc(B, H, W, n->pkf, 3, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
       } else if (dy_planar != nullptr) {
         planar3_to_nhwc8(dy_planar, B, H, W, n->pk8, st);
         e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, n->pk8, kCout[l], n->gw[l], kpad(l), n->gb[l], n->err,
@@ -946,7 +965,7 @@ ils_status ils_cnn_adam_step(ils_cnn* n, float lr, float beta1, float beta2, flo
 // grad = 2 (u0 - target) / n; *loss (device FP32, caller zeroes it) += mean squared error
 ils_status ils_mse(const float* u0, const float* target, float* grad, long long n, float* loss, void* stream) {
   if (u0 == nullptr || target == nullptr || grad == nullptr || loss == nullptr || n < 1) return ILS_ERR_INVALID_ARG;
-  mse_kernel<<<512, 256, 0, static_cast<cudaStream_t>(stream)>>>(u0, target, grad, (size_t)n, 1.0f / (float)n, loss);
+  mse_kernel<<<1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(u0, target, grad, (size_t)n, 1.0f / (float)n, loss);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "mse");
 }
