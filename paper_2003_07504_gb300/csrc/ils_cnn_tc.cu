@@ -4,14 +4,20 @@
 //
 // GEMM view per tile: M = 128 consecutive output pixels of one image row, N = 32 output
 // channels, K = 9 taps x 32 input channels, issued as 18 MMAs of K = 16 (BF16 in, FP32
-// accumulate).  The input rows y-1, y, y+1 over pixels x0-1 .. x0+128 are loaded by four
-// TMA copies, one per 8-channel chunk, into a chunk-major, pixel-minor shared layout:
-// byte (chunk c, row r, pixel p) = c * PLANE + (r * 130 + p) * 16.  In that layout the
-// canonical no-swizzle K-major operand (8-row x 16-byte core matrices, K-direction core
-// stride LBO, M-direction stride SBO) of tap (dy, dx) starts at (dy * 130 + dx) * 16: a
-// tap is a descriptor offset, and out-of-image pixels come from TMA's zero fill (the
-// convolution's zero padding).  The weights, [K-chunk][output channel][8], stay in
-// shared memory for all tiles of a persistent CTA.
+// accumulate).  The input rows y-1, y, y+1 over pixels x0-1 .. x0+128 arrive as three TMA
+// copies of 130 pixels x 64 bytes (all 32 channels of a pixel in one 64-byte row) with the
+// 64-byte swizzle, each into its own 1024-byte-aligned row buffer.  That is the canonical
+// 64-byte-swizzled K-major operand (8-pixel groups 512 bytes apart): tap (dy, dx) starts at
+// pixel dx of row buffer dy and the second K half 32 bytes further.  The hardware applies the
+// swizzle to the absolute shared-memory address on both sides (TMA write, MMA read), so a
+// start inside the 512-byte pattern needs no base offset in the descriptor (measured: the
+// offset (start >> 7) & 7 gives wrong results, 0 gives the mma.sync kernels' results).  Four
+// copies of 16-byte channel chunks into a chunk-major layout (the no-swizzle form) moved the
+// same bytes as 1,560 16-byte rows per tile with twice the sectors; on the 16 x 256 x 256
+// training batch a launch took 67 us that way and the training step 1.31 ms, against 1.11 ms
+// now.  Out-of-image pixels come from TMA's zero fill (the convolution's zero padding).  The
+// weights, [K-chunk][output channel][8] (no swizzle), stay in shared memory for all tiles of a
+// persistent CTA.  A 3-channel input (IN8) keeps the chunk-major form: one 8-channel plane.
 //
 // The kernel is a persistent pipeline: one warp issues the TMA copies into a ring of input
 // stages, one issues the MMAs into two tensor-memory accumulators, four drain them.
@@ -34,8 +40,7 @@ typedef __nv_bfloat16 bf16;
 constexpr int TILE = 128;                  // pixels per tile (M)
 constexpr int HALO_W = TILE + 2;           // 130
 constexpr int PLANE = 6272;                // bytes per 8-channel chunk plane (3 x 130 x 16 = 6240, padded)
-constexpr int A_BYTES = 4 * PLANE;         // 25088
-constexpr int TMA_BYTES = 4 * 3 * HALO_W * 16;  // 24960 bytes delivered per tile
+constexpr int TMA_BYTES = 3 * HALO_W * 64;      // 24960 bytes delivered per tile
 constexpr int B_CHUNKS = 36;               // K = 288 = 36 chunks of 8
 constexpr int B_BYTES = B_CHUNKS * 32 * 16;  // 18432
 using tc::kSpinLimit;
@@ -67,8 +72,12 @@ struct TcArgs {
   uint32_t spin;      // poll limit of the per-tile waits (a test sets it tiny to exercise the timeout path)
 };
 
+// 32-channel input: the rows y-1, y, y+1 over pixels x0-1 .. x0+128 as three TMA copies of
+// 130 pixels x 64 bytes with the 64-byte swizzle, one 1024-byte-aligned buffer per row
+constexpr int RB = 9216;                                // bytes per row buffer (130 x 64 = 8320 used)
+constexpr int A32_BYTES = 3 * RB;                       // 27648
 constexpr int STAGES = 3;                               // input tiles in flight
-constexpr int SMEM_PIPE = STAGES * A_BYTES + B_BYTES + 128;
+constexpr int SMEM_PIPE = 1024 + STAGES * A32_BYTES + B_BYTES + 128 + 128;
 constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
 // The 3-channel variant (IN8): the input is an NHWC row of 8 channels (3 values, 5 zeros), one
@@ -83,7 +92,7 @@ constexpr int IN8_A_BYTES = PLANE;
 constexpr int IN8_TMA_BYTES = 3 * HALO_W * 16;             // 6240
 constexpr int IN8_B_BYTES = IN8_CHUNKS * 32 * 16;          // 5120
 constexpr int IN8_STAGES = 6;
-constexpr int SMEM_PIPE_IN8 = IN8_STAGES * IN8_A_BYTES + IN8_B_BYTES + 128;
+constexpr int SMEM_PIPE_IN8 = 1024 + IN8_STAGES * IN8_A_BYTES + IN8_B_BYTES + 128 + 128;
 
 __host__ __device__ constexpr int in8_tap(int chunk) { return chunk < 8 ? chunk : (chunk == 8 ? -1 : 8); }
 
@@ -94,11 +103,14 @@ __host__ __device__ constexpr int in8_tap(int chunk) { return chunk < 8 ? chunk 
 template <bool IN8>
 __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
   constexpr int NST = IN8 ? IN8_STAGES : STAGES;
-  constexpr int ABYTES = IN8 ? IN8_A_BYTES : A_BYTES;
+  constexpr int ABYTES = IN8 ? IN8_A_BYTES : A32_BYTES;
   constexpr int BBYTES = IN8 ? IN8_B_BYTES : B_BYTES;
-  extern __shared__ __align__(128) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // stages on a 1024-byte boundary: the 64-byte swizzle pattern repeats every 512 bytes
+  unsigned char* sm = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);
   unsigned char* sB = sm + NST * ABYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NST * ABYTES + BBYTES);
+  float* sbias = reinterpret_cast<float*>(sm + NST * ABYTES + BBYTES + 128);
   __shared__ uint32_t tmem_base_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto full = [&](int s) { return saddr(&bars[s]); };
@@ -128,6 +140,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
     }
   }
+  if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias != nullptr ? a.bias[threadIdx.x] : 0.0f;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
@@ -165,8 +178,10 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       const int s = i % NST;
       if (i >= NST && !mbar_wait(empty(s), ((i / NST) & 1) ^ 1, a.spin)) { failed = true; break; }
       mbar_expect_tx(full(s), IN8 ? IN8_TMA_BYTES : TMA_BYTES);
-      for (int c = 0; c < (IN8 ? 1 : 4); ++c)
-        tma_load_4d(saddr(sm + s * ABYTES + c * PLANE), &in_map, c * 8, x0 - 1, y - 1, b, full(s));
+      if (IN8)
+        tma_load_4d(saddr(sm + s * ABYTES), &in_map, 0, x0 - 1, y - 1, b, full(s));
+      else
+        for (int r = 0; r < 3; ++r) tma_load_4d(saddr(sm + s * ABYTES + r * RB), &in_map, 0, x0 - 1, y - 1 + r, b, full(s));
       issued = i + 1;
     }
     // before the CTA may end, every copy issued must have landed (bounded)
@@ -195,10 +210,11 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
           const int dy = tap / 3, dx = tap % 3;
-          const uint32_t at = a0 + (uint32_t)((dy * HALO_W + dx) * 16);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t da = smem_desc(at + kk * 2 * PLANE, PLANE, 128);
+            // pixel dx of row buffer dy, channels 16 kk .. 16 kk + 15; 8-pixel groups 512 bytes apart
+            const uint32_t st = a0 + (uint32_t)(dy * RB + dx * 64 + kk * 32);
+            const uint64_t da = smem_desc_sw64(st, 16, 512);
             const uint64_t db = smem_desc(b0 + (uint32_t)((tap * 4 + kk * 2) * 512), 512, 128);
             mma_f16(d, da, db, (tap | kk) ? 1u : 0u);
           }
@@ -246,11 +262,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
         uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
         for (int c = 0; c < 32; c += 2) {
-          float v0 = __uint_as_float(r[c]), v1 = __uint_as_float(r[c + 1]);
-          if (a.bias != nullptr) {
-            v0 += a.bias[c];
-            v1 += a.bias[c + 1];
-          }
+          float v0 = __uint_as_float(r[c]) + sbias[c], v1 = __uint_as_float(r[c + 1]) + sbias[c + 1];
           if (a.relu) {
             v0 = fmaxf(v0, 0.0f);
             v1 = fmaxf(v1, 0.0f);
@@ -583,7 +595,8 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
   CUtensorMap map;
-  if (!make_nhwc32_map(&map, in, B, H, W, HALO_W, 3, in8 ? 8 : 32)) return cudaErrorInvalidValue;
+  if (in8 ? !make_nhwc32_map(&map, in, B, H, W, HALO_W, 3, 8) : !make_nhwc32_map_sw64(&map, in, B, H, W, HALO_W, 32))
+    return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
