@@ -17,7 +17,9 @@
 // training batch a launch took 67 us that way and the training step 1.31 ms, against 1.11 ms
 // now.  Out-of-image pixels come from TMA's zero fill (the convolution's zero padding).  The
 // weights, [K-chunk][output channel][8] (no swizzle), stay in shared memory for all tiles of a
-// persistent CTA.  A 3-channel input (IN8) keeps the chunk-major form: one 8-channel plane.
+// persistent CTA.  A 3-channel input (IN8) keeps the chunk-major form (one 8-channel plane, 16
+// bytes per pixel, rows 136 pixels apart), each image row loaded as copies of 64 and 66 pixels
+// of 8-byte elements (1-KB rows instead of 130 rows of 16 bytes).
 //
 // The kernel is a persistent pipeline: one warp issues the TMA copies into a ring of input
 // stages, one issues the MMAs into two tensor-memory accumulators, four drain them.
@@ -39,7 +41,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TILE = 128;                  // pixels per tile (M)
 constexpr int HALO_W = TILE + 2;           // 130
-constexpr int PLANE = 6272;                // bytes per 8-channel chunk plane (3 x 130 x 16 = 6240, padded)
 constexpr int TMA_BYTES = 3 * HALO_W * 64;      // 24960 bytes delivered per tile
 constexpr int B_CHUNKS = 36;               // K = 288 = 36 chunks of 8
 constexpr int B_BYTES = B_CHUNKS * 32 * 16;  // 18432
@@ -86,9 +87,11 @@ constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MM
 // distance to the second tap's pixel.  The ninth tap pairs with tap 7 under zero weights, so
 // every operand byte read is a copied pixel.  Weights: 10 K-chunks [chunk][co][8], chunk 2j + h
 // holding tap 2j + h (chunk 8 zero, chunk 9 tap 8), channels 3-7 zero.
+constexpr int IN8_RPX = 136;                               // row stride in pixels (2176 bytes, 128-aligned)
+constexpr int IN8_C0 = 64, IN8_C1 = HALO_W - IN8_C0;       // pixels of a row's two copies (64, 66)
 constexpr int IN8_STEPS = 5;
 constexpr int IN8_CHUNKS = 2 * IN8_STEPS;
-constexpr int IN8_A_BYTES = PLANE;
+constexpr int IN8_A_BYTES = 3 * IN8_RPX * 16;              // 6528
 constexpr int IN8_TMA_BYTES = 3 * HALO_W * 16;             // 6240
 constexpr int IN8_B_BYTES = IN8_CHUNKS * 32 * 16;          // 5120
 constexpr int IN8_STAGES = 6;
@@ -101,7 +104,8 @@ __host__ __device__ constexpr int in8_tap(int chunk) { return chunk < 8 ? chunk 
 // use count): full[s] TMA -> MMA, empty[s] MMA -> TMA (tcgen05.commit), accf[b] MMA ->
 // epilogue, acce[b] epilogue -> MMA (128 arrivals).
 template <bool IN8>
-__global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
+__global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                            const __grid_constant__ CUtensorMap in_map2, TcArgs a) {
   constexpr int NST = IN8 ? IN8_STAGES : STAGES;
   constexpr int ABYTES = IN8 ? IN8_A_BYTES : A32_BYTES;
   constexpr int BBYTES = IN8 ? IN8_B_BYTES : B_BYTES;
@@ -178,8 +182,12 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       const int s = i % NST;
       if (i >= NST && !mbar_wait(empty(s), ((i / NST) & 1) ^ 1, a.spin)) { failed = true; break; }
       mbar_expect_tx(full(s), IN8 ? IN8_TMA_BYTES : TMA_BYTES);
-      if (IN8)
-        tma_load_4d(saddr(sm + s * ABYTES), &in_map, 0, x0 - 1, y - 1, b, full(s));
+      if (IN8)  // per row a copy of 64 and one of 66 pixels (x in 8-byte units: always even)
+        for (int r = 0; r < 3; ++r) {
+          const uint32_t row = saddr(sm + s * ABYTES + r * IN8_RPX * 16);
+          tc::tma_load_3d(row, &in_map, 2 * (x0 - 1), y - 1 + r, b, full(s));
+          tc::tma_load_3d(row + IN8_C0 * 16, &in_map2, 2 * (x0 - 1 + IN8_C0), y - 1 + r, b, full(s));
+        }
       else
         for (int r = 0; r < 3; ++r) tma_load_4d(saddr(sm + s * ABYTES + r * RB), &in_map, 0, x0 - 1, y - 1 + r, b, full(s));
       issued = i + 1;
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
         for (int j = 0; j < IN8_STEPS; ++j) {
           // taps t0 (K half 0) and t1 (K half 1) of this step; byte offset of tap t's pixel 0
           const int t0 = j < 4 ? 2 * j : 7, t1 = j < 4 ? 2 * j + 1 : 8;
-          const int o0 = ((t0 / 3) * HALO_W + t0 % 3) * 16, o1 = ((t1 / 3) * HALO_W + t1 % 3) * 16;
+          const int o0 = ((t0 / 3) * IN8_RPX + t0 % 3) * 16, o1 = ((t1 / 3) * IN8_RPX + t1 % 3) * 16;
           const uint64_t da = smem_desc(a0 + (uint32_t)o0, (uint32_t)(o1 - o0), 128);
           const uint64_t db = smem_desc(b0 + (uint32_t)(2 * j * 512), 512, 128);
           mma_f16(d, da, db, j ? 1u : 0u);
@@ -546,6 +554,18 @@ bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_nhwc8_row_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_px) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+  const cuuint32_t box[3] = {(cuuint32_t)box_px * 2, 1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(act), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t conv32_tc_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cnn_tc::SMEM_PIPE);
@@ -594,9 +614,11 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
                            const void* mask, int relu, int* error, cudaStream_t st) {
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
-  CUtensorMap map;
-  if (in8 ? !make_nhwc32_map(&map, in, B, H, W, HALO_W, 3, 8) : !make_nhwc32_map_sw64(&map, in, B, H, W, HALO_W, 32))
+  CUtensorMap map, map2;
+  if (in8 ? !make_nhwc8_row_map(&map, in, B, H, W, IN8_C0) || !make_nhwc8_row_map(&map2, in, B, H, W, IN8_C1)
+          : !make_nhwc32_map_sw64(&map, in, B, H, W, HALO_W, 32))
     return cudaErrorInvalidValue;
+  if (!in8) map2 = map;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -613,9 +635,9 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
   const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
   a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
   if (in8)
-    conv32_tc_kernel<true><<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, a);
+    conv32_tc_kernel<true><<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, map2, a);
   else
-    conv32_tc_kernel<false><<<grid, NTHR, SMEM_PIPE, st>>>(map, a);
+    conv32_tc_kernel<false><<<grid, NTHR, SMEM_PIPE, st>>>(map, map2, a);
   return cudaGetLastError();
 }
 

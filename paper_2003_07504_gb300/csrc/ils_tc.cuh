@@ -48,6 +48,13 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 | version 1 << 46,
 // no swizzle (layout type 0 in bits 61-63).  For the K-major operands used here, LBO is
 // the byte distance between the two 8-element K halves of a K = 16 step and SBO the
@@ -96,5 +103,8 @@ bool make_nhwc32_map(CUtensorMap* map, const void* act, int B, int H, int W, int
 // pixels x 1 row, written to shared memory with the 64-byte swizzle (for ch = 8 the box's
 // channels 8-31 are the zero fill).
 bool make_nhwc32_map_sw64(CUtensorMap* map, const void* act, int B, int H, int W, int box_x, int ch);
+// An NHWC BF16 tensor of B x H x W x 8 seen as rows of 8-byte elements (two per pixel), with a
+// box of box_px pixels x 1 row x 1 image: one copy moves box_px x 16 contiguous bytes.
+bool make_nhwc8_row_map(CUtensorMap* map, const void* act, int B, int H, int W, int box_px);
 
 }  // namespace ils
