@@ -380,61 +380,86 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
   const uint32_t tmem = tmem_base_slot;
 
   const int tiles_x = (a.W + WG_TILE - 1) / WG_TILE;
-  const long long total = (long long)a.B * tiles_x * a.H;  // tile g: column g / H, input row g % H
-  const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+  const int total = a.B * tiles_x * a.H;  // tile g: column g / H, input row g % H
+  const int t0 = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int t1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   if (threadIdx.x == 0 && t1 > t0) {
-    uint32_t full_issued[WG_XSLOTS] = {}, full_used[WG_XSLOTS] = {}, done_issued[WG_XSLOTS] = {},
-             done_waited[WG_XSLOTS] = {};
+    // per input slot j (bit j): parity of the next wait on full[j], a copy outstanding on full[j],
+    // parity of the commits made on done[j], a commit not yet waited for
+    uint32_t fullpar = 0, fullout = 0, donebit = 0, donepend = 0;
     bool failed = false;
     auto full = [&](int j) { return saddr(&bars[j]); };
     auto done = [&](int j) { return saddr(&bars[WG_XSLOTS + j]); };
+    auto next_slot = [](int j) { return j + 1 == WG_XSLOTS ? 0 : j + 1; };
     // waits for the last commit on done[j] if it has not been waited for (bounded)
     auto settle = [&](int j, uint32_t lim) -> bool {
-      if (done_waited[j] == done_issued[j]) return true;
-      if (!mbar_wait(done(j), (done_issued[j] - 1) & 1, lim)) return false;
-      done_waited[j] = done_issued[j];
+      if (!((donepend >> j) & 1u)) return true;
+      if (!mbar_wait(done(j), ((donebit >> j) & 1u) ^ 1u, lim)) return false;
+      donepend &= ~(1u << j);
       return true;
     };
-    // copies for tile g (local index i = g - t0) on full[i % WG_XSLOTS]: its input row three
-    // times, and dY rows yq - 1 .. yq + 1 (first tile of a column run) or yq + 1 alone, each into
-    // its ring slot and, for slots 0 and 1, the mirror after the ring
-    auto load_tile = [&](long long g, bool first) {
-      const int col = (int)(g / a.H), yq = (int)(g - (long long)col * a.H);
-      const int b = col / tiles_x, x0 = (col - b * tiles_x) * WG_TILE;
-      const int j = (int)((g - t0) % WG_XSLOTS);
-      uint32_t bytes = 3 * WG_BLK;
-      for (int r = first ? yq - 1 : yq + 1; r <= yq + 1; ++r) bytes += (wg_ring(r) < 2 ? 2 : 1) * WG_BLK;
-      mbar_expect_tx(full(j), bytes);
-      ++full_issued[j];
-      for (int dx = 0; dx < 3; ++dx)
-        tma_load_4d(saddr(sX + j * WG_XSLOT + dx * WG_BLK), &x_map, 0, x0 - 1 + dx, yq, b, full(j));
-      for (int r = first ? yq - 1 : yq + 1; r <= yq + 1; ++r) {
-        const int sl = wg_ring(r);
-        tma_load_4d(saddr(sD + sl * WG_BLK), &dy_map, 0, x0, r, b, full(j));
-        if (sl < 2) tma_load_4d(saddr(sD + (WG_RING + sl) * WG_BLK), &dy_map, 0, x0, r, b, full(j));
+    // a tile's position (column col of image b at pixel x0, input row yq), advanced one tile at
+    // a time: a division only when a column ends
+    struct Pos {
+      int col, yq, b, x0;
+    };
+    auto set_col = [&](Pos& p) {
+      p.b = p.col / tiles_x;
+      p.x0 = (p.col - p.b * tiles_x) * WG_TILE;
+    };
+    auto advance = [&](Pos& p) {
+      if (++p.yq == a.H) {
+        p.yq = 0;
+        ++p.col;
+        set_col(p);
       }
     };
-    long long loaded = t0;  // next tile to load
-    for (long long g = t0; g < t1 && !failed; ++g) {
-      const int i = (int)(g - t0), j = i % WG_XSLOTS;
-      const int col = (int)(g / a.H), yq = (int)(g - (long long)col * a.H);
-      const long long col_end = (long long)(col + 1) * a.H;  // first tile of the next column
-      if (g == t0 || yq == 0) {
+    // copies for a tile on full[j]: its input row three times, and dY rows yq - 1 .. yq + 1
+    // (first tile of a column run) or yq + 1 alone, each into its ring slot and, for slots 0 and
+    // 1, the mirror after the ring
+    auto load_tile = [&](const Pos& p, int j, bool first) {
+      uint32_t bytes = 3 * WG_BLK;
+      for (int r = first ? p.yq - 1 : p.yq + 1; r <= p.yq + 1; ++r) bytes += (wg_ring(r) < 2 ? 2 : 1) * WG_BLK;
+      mbar_expect_tx(full(j), bytes);
+      fullout |= 1u << j;
+      for (int dx = 0; dx < 3; ++dx)
+        tma_load_4d(saddr(sX + j * WG_XSLOT + dx * WG_BLK), &x_map, 0, p.x0 - 1 + dx, p.yq, p.b, full(j));
+      for (int r = first ? p.yq - 1 : p.yq + 1; r <= p.yq + 1; ++r) {
+        const int sl = wg_ring(r);
+        tma_load_4d(saddr(sD + sl * WG_BLK), &dy_map, 0, p.x0, r, p.b, full(j));
+        if (sl < 2) tma_load_4d(saddr(sD + (WG_RING + sl) * WG_BLK), &dy_map, 0, p.x0, r, p.b, full(j));
+      }
+    };
+    Pos cur, ld;  // the tile being multiplied, the next tile to load
+    cur.col = t0 / a.H;
+    cur.yq = t0 - cur.col * a.H;
+    set_col(cur);
+    ld = cur;
+    int loaded = t0, lj = 0;  // next tile to load and its input slot
+    int j = 0;                // input slot of tile g: (g - t0) mod WG_XSLOTS
+    for (int g = t0; g < t1 && !failed; ++g) {
+      const int col_end = (cur.col + 1) * a.H;  // first tile of the next column
+      if (g == t0 || cur.yq == 0) {
         // a new column run: every MMA in flight must be done before its rows take the slots
-        for (int s = 0; s < WG_XSLOTS; ++s)
-          if (!settle(s, a.spin)) failed = true;
+        for (int sl = 0; sl < WG_XSLOTS; ++sl)
+          if (!settle(sl, a.spin)) failed = true;
         if (failed) break;
-        load_tile(g, true);
-        for (loaded = g + 1; loaded < t1 && loaded < col_end && loaded < g + WG_AHEAD; ++loaded)
-          load_tile(loaded, false);
+        ld = cur;
+        lj = j;
+        load_tile(ld, lj, true);
+        for (loaded = g + 1, advance(ld), lj = next_slot(lj); loaded < t1 && loaded < col_end && loaded < g + WG_AHEAD;
+             ++loaded, advance(ld), lj = next_slot(lj))
+          load_tile(ld, lj, false);
       }
       // this tile's operands
-      if (!mbar_wait(full(j), full_used[j] & 1, a.spin)) { failed = true; break; }
-      ++full_used[j];
+      if (!mbar_wait(full(j), (fullpar >> j) & 1u, a.spin)) { failed = true; break; }
+      fullpar ^= 1u << j;
+      fullout &= ~(1u << j);
       // the barrier about to be committed to must have no phase pending (tile g - WG_XSLOTS)
       if (!settle(j, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t xa = saddr(sX) + (uint32_t)(j * WG_XSLOT), da0 = saddr(sD) + (uint32_t)(wg_ring(yq - 1) * WG_BLK);
+      const uint32_t xa = saddr(sX) + (uint32_t)(j * WG_XSLOT);
+      const uint32_t da0 = saddr(sD) + (uint32_t)(wg_ring(cur.yq - 1) * WG_BLK);
 #pragma unroll
       for (int ks = 0; ks < WG_TILE / 16; ++ks) {
         // 16 pixels (1 KB) per K step; blocks of 32 M or N LBO = 8 KB apart, K groups SBO = 512 B apart
@@ -443,21 +468,25 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
         tc::mma_f16(tmem, da, dd, kIdescWg, (g > t0 || ks > 0) ? 1u : 0u);
       }
       mma_commit(done(j));
-      ++done_issued[j];
+      donebit ^= 1u << j;
+      donepend |= 1u << j;
       // with this tile's MMAs queued, prefetch tile g + WG_AHEAD: it takes the input slot and the
       // dY ring slot of tile g - 1, so wait for tile g - 1's MMAs first
       if (loaded < t1 && loaded < col_end && loaded == g + WG_AHEAD) {
-        if (!settle((i - 1 + WG_XSLOTS) % WG_XSLOTS, a.spin)) { failed = true; break; }
-        load_tile(loaded, false);
+        if (!settle(j == 0 ? WG_XSLOTS - 1 : j - 1, a.spin)) { failed = true; break; }
+        load_tile(ld, lj, false);
         ++loaded;
+        advance(ld);
+        lj = next_slot(lj);
       }
+      advance(cur);
+      j = next_slot(j);
     }
     // drain (bounded): copies still in flight, then every MMA issued
-    for (int s = 0; s < WG_XSLOTS; ++s)
-      for (; full_used[s] < full_issued[s]; ++full_used[s])
-        if (!mbar_wait(full(s), full_used[s] & 1)) failed = true;
-    for (int s = 0; s < WG_XSLOTS; ++s)
-      if (!settle(s, tc::kSpinLimit)) failed = true;
+    for (int sl = 0; sl < WG_XSLOTS; ++sl)
+      if (((fullout >> sl) & 1u) && !mbar_wait(full(sl), (fullpar >> sl) & 1u)) failed = true;
+    for (int sl = 0; sl < WG_XSLOTS; ++sl)
+      if (!settle(sl, tc::kSpinLimit)) failed = true;
     if (failed) failed_s = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
