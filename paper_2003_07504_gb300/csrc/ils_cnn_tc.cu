@@ -197,40 +197,52 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       if (!mbar_wait(full(i % NST), (i / NST) & 1)) failed = true;
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    int issued = 0;
+    // The weights' descriptors are the same for every tile, and a tile's A descriptors differ
+    // from its first one only in the start-address field (address >> 4, 14 bits; every address
+    // here is below 256 KB, so adding a tap's offset >> 4 never carries out of the field): one
+    // 64-bit add per MMA instead of a descriptor build.
+    constexpr int NMMA = IN8 ? IN8_STEPS : 18;
+    const uint32_t b0 = saddr(sB);
+    uint64_t db[NMMA];
+#pragma unroll
+    for (int q = 0; q < NMMA; ++q)
+      db[q] = IN8 ? smem_desc(b0 + (uint32_t)(2 * q * 512), 512, 128)
+                  : smem_desc(b0 + (uint32_t)(((q >> 1) * 4 + (q & 1) * 2) * 512), 512, 128);
+    int issued = 0, s = 0, sphase = 0;  // stage of tile i and the parity of its full barrier
     for (int i = 0; i < my_tiles; ++i) {
-      const int s = i % NST, acc = i & 1;
-      if (!mbar_wait(full(s), (i / NST) & 1, a.spin)) { failed = true; break; }
+      const int acc = i & 1;
+      if (!mbar_wait(full(s), sphase, a.spin)) { failed = true; break; }
       if (i >= 2 && !mbar_wait(acce(acc), ((i >> 1) & 1) ^ 1, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = saddr(sm + s * ABYTES), b0 = saddr(sB), d = tmem + acc * 32;
+      const uint32_t a0 = saddr(sm + s * ABYTES), d = tmem + acc * 32;
       if (IN8) {
+        const uint64_t da0 = smem_desc(a0, 16, 128);
 #pragma unroll
         for (int j = 0; j < IN8_STEPS; ++j) {
           // taps t0 (K half 0) and t1 (K half 1) of this step; byte offset of tap t's pixel 0
           const int t0 = j < 4 ? 2 * j : 7, t1 = j < 4 ? 2 * j + 1 : 8;
           const int o0 = ((t0 / 3) * IN8_RPX + t0 % 3) * 16, o1 = ((t1 / 3) * IN8_RPX + t1 % 3) * 16;
-          const uint64_t da = smem_desc(a0 + (uint32_t)o0, (uint32_t)(o1 - o0), 128);
-          const uint64_t db = smem_desc(b0 + (uint32_t)(2 * j * 512), 512, 128);
-          mma_f16(d, da, db, j ? 1u : 0u);
+          // the K stride (LBO, bits 16-29) is the distance between the two taps
+          const uint64_t da = (da0 & ~(0x3FFFull << 16)) + (uint64_t)(o0 >> 4) + ((uint64_t)((o1 - o0) >> 4) << 16);
+          mma_f16(d, da, db[j], j ? 1u : 0u);
         }
       } else {
+        const uint64_t da0 = smem_desc_sw64(a0, 16, 512);
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            // pixel dx of row buffer dy, channels 16 kk .. 16 kk + 15; 8-pixel groups 512 bytes apart
-            const uint32_t st = a0 + (uint32_t)(dy * RB + dx * 64 + kk * 32);
-            const uint64_t da = smem_desc_sw64(st, 16, 512);
-            const uint64_t db = smem_desc(b0 + (uint32_t)((tap * 4 + kk * 2) * 512), 512, 128);
-            mma_f16(d, da, db, (tap | kk) ? 1u : 0u);
-          }
+        for (int q = 0; q < 18; ++q) {
+          // tap q / 2 = (dy, dx): pixel dx of row buffer dy; channels 16 (q % 2) .. + 15
+          const int tap = q >> 1, dy = tap / 3, dx = tap % 3, kk = q & 1;
+          const uint64_t da = da0 + (uint64_t)((dy * RB + dx * 64 + kk * 32) >> 4);
+          mma_f16(d, da, db[q], q ? 1u : 0u);
         }
       }
       mma_commit(empty(s));
       mma_commit(accf(acc));
       issued = i + 1;
+      if (++s == NST) {
+        s = 0;
+        sphase ^= 1;
+      }
     }
     // the MMAs issued must complete before tensor memory is freed (bounded)
     for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
