@@ -294,12 +294,13 @@ def test_column_plan_variants_agree(ils, monkeypatch, H, W):
             assert_parity(frames[0][1].cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("H,W", [(12, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512), (20, 256)])
+@pytest.mark.parametrize("H,W", [(12, 1920), (40, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512), (20, 256)])
 def test_row_plan_variants_agree(ils, monkeypatch, H, W):
-    # every warp-per-row and fixed-plan row variant of the length against the oracle
+    # every warp-per-row and fixed-plan row variant of the length against the oracle (40 x 1920:
+    # seven 6-row strips, the last one ragged)
     f = image(H, W, 2, seed=W + H, preset="hd")
     want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
-    for impl in [f"warp{k}" for k in range(6)] + [f"fixed{k}" for k in range(3)]:
+    for impl in [f"warp{k}" for k in range(8)] + [f"fixed{k}" for k in range(3)]:
         monkeypatch.setenv("ILS_ROW_IMPL", impl)
         assert_parity(run_gpu(ils, f), want)
 
