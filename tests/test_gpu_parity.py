@@ -282,7 +282,7 @@ def test_column_plan_variants_agree(ils, monkeypatch, H, W):
     for C in (1, 3):
         f = image(H, W, C, seed=H + 7 + C, preset="hd")
         want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
-        for k in range(6):   # ILS_COL_IMPL=k beyond the plans of H selects the default
+        for k in range(8):   # ILS_COL_IMPL=k beyond the plans of H selects the default
             monkeypatch.setenv("ILS_COL_IMPL", str(k))
             assert_parity(run_gpu(ils, f), want)
         monkeypatch.delenv("ILS_COL_IMPL")
