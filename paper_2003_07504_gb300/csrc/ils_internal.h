@@ -154,6 +154,7 @@ struct Geometry {
   int threads_col, ept_col;
   size_t smem_fwd, smem_inv, smem_col;  // dynamic shared memory bytes
   int warp_row;      // index of a warp-per-row kernel for M = W/2, or -1
+  int warp_adj;      // the warp-per-row kernel of the adjoint's row pass, or -1
   int fixed_row;     // index of a compile-time row plan for M = W/2, or -1 (generic kernels)
   int fixed_col;     // index of a compile-time column plan for H, or -1
 };

@@ -430,7 +430,13 @@ bool pick_geometry(int H, int W, Geometry* g) {
     if (pick < 0 || pick >= nw) pick = 0;
   }
   g->warp_row = nw > 0 ? wv[pick] : -1;
+  g->warp_adj = g->warp_row;
   g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
+  // 256-wide rows (M = 128): the block-per-strip plan by default.  A warp-per-row transform of
+  // 4 points per lane runs its 32-point stage on 4 of the 32 lanes; measured on a 48 x 256 x 256
+  // call: 158 us per call against 181 us (row pass 27.5 against 34.8 us, final inverse 12.4
+  // against 18.3 us).  The adjoint keeps its warp-per-row kernel.
+  if (impl == nullptr && M == 128 && g->fixed_row >= 0) g->warp_row = -1;
   // ILS_ROW_IMPL=fixed<k>: the k-th compile-time row plan of the length
   if (!no_fixed && impl != nullptr && impl[0] == 'f' && impl[1] == 'i' && impl[2] == 'x' && impl[3] == 'e' &&
       impl[4] == 'd' && impl[5] >= '0' && impl[5] <= '9') {
@@ -545,8 +551,8 @@ cudaError_t launch_row_adjoint(const ImageDesc& d, const Geometry& g, const Tabl
                                const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                                bool last, float2* spec_out, cudaStream_t stream) {
   if (mp.pen == 2) return cudaErrorInvalidValue;  // no adjoint for half-quadratic splitting
-  if (g.warp_row >= 0)
-    return warp_row_adjoint(g.warp_row, d, t, mp, spec_in, u_n, fbar, fbar_first, gu0, last, spec_out, stream);
+  if (g.warp_adj >= 0)
+    return warp_row_adjoint(g.warp_adj, d, t, mp, spec_in, u_n, fbar, fbar_first, gu0, last, spec_out, stream);
   dim3 grid((d.H + g.rows_fwd - 1) / g.rows_fwd, d.C);
   auto fn = mp.pen == 1 ? (g.ept_row == 16 ? row_adjoint_kernel<16, 1> : row_adjoint_kernel<32, 1>)
                       : (g.ept_row == 16 ? row_adjoint_kernel<16, 0> : row_adjoint_kernel<32, 0>);

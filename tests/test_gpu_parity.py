@@ -307,17 +307,20 @@ def test_row_plan_variants_agree(ils, monkeypatch, H, W):
 
 # -------------------------------------------------------------- ILS with the Welsch penalty (Sec. 5)
 
-@pytest.mark.parametrize("H,W,C,lam,gamma,N", [
-    (256, 256, 1, 20.0, 10 / 255, 10),   # warp-per-row kernels, L = 4; the paper's clip-art setting
-    (60, 80, 3, 30.0, 5 / 255, 10),      # generic row kernels (M = 40)
-    (45, 640, 1, 20.0, 10 / 255, 4),     # warp L = 10
-    (40, 1920, 1, 30.0, 10 / 255, 15),   # warp L = 30; texture-smoothing iteration count
-    (16, 3840, 1, 20.0, 10 / 255, 3),    # fixed-plan 1920-point rows
-    (27, 250, 1, 5.0, 0.1, 4),           # odd column length, generic rows
-    (1080, 40, 1, 20.0, 10 / 255, 2),    # 1080-point column plan
+@pytest.mark.parametrize("H,W,C,lam,gamma,N,impl", [
+    (256, 256, 1, 20.0, 10 / 255, 10, None),  # fixed-plan 128-point rows; the paper's clip-art setting
+    (64, 256, 1, 20.0, 10 / 255, 10, "warp0"),  # warp-per-row kernels, L = 4
+    (60, 80, 3, 30.0, 5 / 255, 10, None),    # generic row kernels (M = 40)
+    (45, 640, 1, 20.0, 10 / 255, 4, None),   # warp L = 10
+    (40, 1920, 1, 30.0, 10 / 255, 15, None),  # warp L = 30; texture-smoothing iteration count
+    (16, 3840, 1, 20.0, 10 / 255, 3, None),  # fixed-plan 1920-point rows
+    (27, 250, 1, 5.0, 0.1, 4, None),         # odd column length, generic rows
+    (1080, 40, 1, 20.0, 10 / 255, 2, None),  # 1080-point column plan
 ])
-def test_welsch_parity(ils, H, W, C, lam, gamma, N):
+def test_welsch_parity(ils, monkeypatch, H, W, C, lam, gamma, N, impl):
     import torch
+    if impl is not None:
+        monkeypatch.setenv("ILS_ROW_IMPL", impl)
     f = image(H, W, C, seed=H * 31 + W + C)
     with ils.Plan(H, W, C, lam, N=N, penalty="welsch", gamma=gamma) as plan:
         assert plan.c == 2.0
@@ -518,15 +521,18 @@ def test_tonemap_matches_oracle(ils, H, W):
 
 # -------------------------------------------------------------- half-quadratic splitting (Sec. 3.5, the comparison method)
 
-@pytest.mark.parametrize("H,W,C,lam,N", [
-    (256, 256, 1, 0.25, 4),   # warp kernels; the paper's Fig. 11(c) setting
-    (40, 1920, 3, 0.25, 4),   # warp L = 30
-    (16, 3840, 1, 0.1, 3),    # fixed 1920-point rows
-    (60, 80, 2, 0.25, 6),     # generic rows
-    (1080, 40, 1, 0.25, 2),   # 1080-point column plan
+@pytest.mark.parametrize("H,W,C,lam,N,impl", [
+    (256, 256, 1, 0.25, 4, None),     # fixed 128-point rows; the paper's Fig. 11(c) setting
+    (64, 256, 1, 0.25, 4, "warp0"),   # warp kernels, L = 4
+    (40, 1920, 3, 0.25, 4, None),     # warp L = 30
+    (16, 3840, 1, 0.1, 3, None),      # fixed 1920-point rows
+    (60, 80, 2, 0.25, 6, None),       # generic rows
+    (1080, 40, 1, 0.25, 2, None),     # 1080-point column plan
 ])
-def test_hqs_parity(ils, H, W, C, lam, N):
+def test_hqs_parity(ils, monkeypatch, H, W, C, lam, N, impl):
     import torch
+    if impl is not None:
+        monkeypatch.setenv("ILS_ROW_IMPL", impl)
     f = image(H, W, C, seed=13 * H + W + C)
     with ils.Plan(H, W, C, lam, N=N, penalty="hqs") as plan:
         u = plan.smooth(torch.from_numpy(np.ascontiguousarray(f)).cuda()).cpu().numpy()
