@@ -327,15 +327,18 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 //   B: a ring of dY rows (row r in slot r mod WG_RING) with slots 0 and 1 mirrored after the
 //      ring, so rows yq - 1, yq, yq + 1 always sit in three consecutive 8 KB blocks (LBO).
 // Each CTA takes a contiguous range of the batch's tiles, ordered by (image, 128-pixel column,
-// input row); within a column a tile needs one new dY row.  The copies run WG_AHEAD tiles
-// ahead of the MMAs (a new column starts after the MMAs in flight are done).  Out-of-image
+// input row); within a column a tile needs one new dY row.  One thread issues the copies, up
+// to WG_XSLOTS tiles ahead: a slot is refilled once the MMAs of its previous tile are done
+// (they also were the last to read the dY ring slot the new row takes), and a new column
+// starts after every MMA issued is done.  Another thread issues the MMAs of each tile once its
+// copies have landed; the two meet only at the mbarriers (with one thread doing both, a
+// launch took 48-52 us on the 16 x 256^2 training batch, bound by that thread).  Out-of-image
 // pixels come from TMA's zero fill; the input rows -1 and H, which only zero padding would
 // pair with, are never walked.  The CTA accumulates its tiles in tensor memory and adds the
-// result to dW and db with FP32 atomics at the end.  One thread issues the copies and the
-// MMAs; every wait is bounded (error flag, drain, free), and no mbarrier ever has more than
-// one phase pending.
+// result to dW and db with FP32 atomics at the end.  Every wait is bounded (error flag,
+// drain, free), and no mbarrier ever has more than one phase pending.
 constexpr int WG_TILE = 128;
-constexpr int WG_AHEAD = 3;                            // tiles of copies in flight ahead of the MMAs
+constexpr int WG_AHEAD = 3;                            // tiles of copies in flight beyond the current one
 constexpr int WG_XSLOTS = WG_AHEAD + 1;                // input slots (also the number of barrier pairs)
 constexpr int WG_RING = WG_AHEAD + 3;                  // dY ring slots (+2 mirrors)
 constexpr int WG_BLK = WG_TILE * 64;                   // 8192: 128 pixels x 32 BF16 channels
@@ -395,37 +398,40 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
   const int total = a.B * tiles_x * a.H;  // tile g: column g / H, input row g % H
   const int t0 = (int)((long long)total * blockIdx.x / gridDim.x);
   const int t1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-  if (threadIdx.x == 0 && t1 > t0) {
-    // per input slot j (bit j): parity of the next wait on full[j], a copy outstanding on full[j],
-    // parity of the commits made on done[j], a commit not yet waited for
-    uint32_t fullpar = 0, fullout = 0, donebit = 0, donepend = 0;
+  // a tile's position (column col of image b at pixel x0, input row yq), advanced one tile at a
+  // time: a division only when a column ends
+  struct Pos {
+    int col, yq, b, x0;
+  };
+  auto set_col = [&](Pos& p) {
+    p.b = p.col / tiles_x;
+    p.x0 = (p.col - p.b * tiles_x) * WG_TILE;
+  };
+  auto start = [&](int g) {
+    Pos p;
+    p.col = g / a.H;
+    p.yq = g - p.col * a.H;
+    set_col(p);
+    return p;
+  };
+  auto advance = [&](Pos& p) {
+    if (++p.yq == a.H) {
+      p.yq = 0;
+      ++p.col;
+      set_col(p);
+    }
+  };
+  auto full = [&](int j) { return saddr(&bars[j]); };
+  auto done = [&](int j) { return saddr(&bars[WG_XSLOTS + j]); };
+  auto next_slot = [](int j) { return j + 1 == WG_XSLOTS ? 0 : j + 1; };
+  if (warp == 0 && lane == 0 && t1 > t0) {
+    // ---------------- copy thread.  Tile g goes to input slot j = (g - t0) mod WG_XSLOTS once the
+    // MMAs of the slot's previous tile (g - WG_XSLOTS) are done; those also were the last to read
+    // the dY ring slot its new row takes.  A column run starts after every MMA issued is done.
+    // Per slot (bit j): loads so far mod 2, a load whose MMAs this thread has not waited for,
+    // a slot loaded at least once.
+    uint32_t loadpar = 0, outstanding = 0, used = 0;
     bool failed = false;
-    auto full = [&](int j) { return saddr(&bars[j]); };
-    auto done = [&](int j) { return saddr(&bars[WG_XSLOTS + j]); };
-    auto next_slot = [](int j) { return j + 1 == WG_XSLOTS ? 0 : j + 1; };
-    // waits for the last commit on done[j] if it has not been waited for (bounded)
-    auto settle = [&](int j, uint32_t lim) -> bool {
-      if (!((donepend >> j) & 1u)) return true;
-      if (!mbar_wait(done(j), ((donebit >> j) & 1u) ^ 1u, lim)) return false;
-      donepend &= ~(1u << j);
-      return true;
-    };
-    // a tile's position (column col of image b at pixel x0, input row yq), advanced one tile at
-    // a time: a division only when a column ends
-    struct Pos {
-      int col, yq, b, x0;
-    };
-    auto set_col = [&](Pos& p) {
-      p.b = p.col / tiles_x;
-      p.x0 = (p.col - p.b * tiles_x) * WG_TILE;
-    };
-    auto advance = [&](Pos& p) {
-      if (++p.yq == a.H) {
-        p.yq = 0;
-        ++p.col;
-        set_col(p);
-      }
-    };
     // copies for a tile on full[j]: its input row three times, and dY rows yq - 1 .. yq + 1
     // (first tile of a column run) or yq + 1 alone, each into its ring slot and, for slots 0 and
     // 1, the mirror after the ring
@@ -433,7 +439,6 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
       uint32_t bytes = 3 * WG_BLK;
       for (int r = first ? p.yq - 1 : p.yq + 1; r <= p.yq + 1; ++r) bytes += (wg_ring(r) < 2 ? 2 : 1) * WG_BLK;
       mbar_expect_tx(full(j), bytes);
-      fullout |= 1u << j;
       for (int dx = 0; dx < 3; ++dx)
         tma_load_4d(saddr(sX + j * WG_XSLOT + dx * WG_BLK), &x_map, 0, p.x0 - 1 + dx, p.yq, p.b, full(j));
       for (int r = first ? p.yq - 1 : p.yq + 1; r <= p.yq + 1; ++r) {
@@ -442,33 +447,45 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
         if (sl < 2) tma_load_4d(saddr(sD + (WG_RING + sl) * WG_BLK), &dy_map, 0, p.x0, r, p.b, full(j));
       }
     };
-    Pos cur, ld;  // the tile being multiplied, the next tile to load
-    cur.col = t0 / a.H;
-    cur.yq = t0 - cur.col * a.H;
-    set_col(cur);
-    ld = cur;
-    int loaded = t0, lj = 0;  // next tile to load and its input slot
-    int j = 0;                // input slot of tile g: (g - t0) mod WG_XSLOTS
+    Pos ld = start(t0);
+    int lj = 0;
     for (int g = t0; g < t1 && !failed; ++g) {
-      const int col_end = (cur.col + 1) * a.H;  // first tile of the next column
-      if (g == t0 || cur.yq == 0) {
-        // a new column run: every MMA in flight must be done before its rows take the slots
-        for (int sl = 0; sl < WG_XSLOTS; ++sl)
-          if (!settle(sl, a.spin)) failed = true;
-        if (failed) break;
-        ld = cur;
-        lj = j;
-        load_tile(ld, lj, true);
-        for (loaded = g + 1, advance(ld), lj = next_slot(lj); loaded < t1 && loaded < col_end && loaded < g + WG_AHEAD;
-             ++loaded, advance(ld), lj = next_slot(lj))
-          load_tile(ld, lj, false);
+      const bool first = g == t0 || ld.yq == 0;
+      const uint32_t need = first ? outstanding : (outstanding & (1u << lj));
+      for (int sl = 0; sl < WG_XSLOTS; ++sl)
+        if ((need >> sl) & 1u) {
+          if (!mbar_wait(done(sl), ((loadpar >> sl) & 1u) ^ 1u, a.spin)) {
+            failed = true;
+            break;
+          }
+          outstanding &= ~(1u << sl);
+        }
+      if (failed) break;
+      load_tile(ld, lj, first);
+      loadpar ^= 1u << lj;
+      outstanding |= 1u << lj;
+      used |= 1u << lj;
+      advance(ld);
+      lj = next_slot(lj);
+    }
+    // every copy issued must have landed before the CTA may end (bounded): the last phase of
+    // each slot's full barrier
+    for (int sl = 0; sl < WG_XSLOTS; ++sl)
+      if (((used >> sl) & 1u) && !mbar_wait(full(sl), ((loadpar >> sl) & 1u) ^ 1u)) failed = true;
+    if (failed) failed_s = 1;
+  } else if (warp == 1 && lane == 0 && t1 > t0) {
+    // ---------------- MMA thread: tile g from input slot j once its copies have landed
+    uint32_t fullpar = 0, donebit = 0;
+    int lastj = -1;
+    bool failed = false;
+    Pos cur = start(t0);
+    int j = 0;
+    for (int g = t0; g < t1; ++g) {
+      if (!mbar_wait(full(j), (fullpar >> j) & 1u, a.spin)) {
+        failed = true;
+        break;
       }
-      // this tile's operands
-      if (!mbar_wait(full(j), (fullpar >> j) & 1u, a.spin)) { failed = true; break; }
       fullpar ^= 1u << j;
-      fullout &= ~(1u << j);
-      // the barrier about to be committed to must have no phase pending (tile g - WG_XSLOTS)
-      if (!settle(j, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t xa = saddr(sX) + (uint32_t)(j * WG_XSLOT);
       const uint32_t da0 = saddr(sD) + (uint32_t)(wg_ring(cur.yq - 1) * WG_BLK);
@@ -481,24 +498,12 @@ conv32_wgrad_tc_kernel(const __grid_constant__ CUtensorMap x_map, const __grid_c
       }
       mma_commit(done(j));
       donebit ^= 1u << j;
-      donepend |= 1u << j;
-      // with this tile's MMAs queued, prefetch tile g + WG_AHEAD: it takes the input slot and the
-      // dY ring slot of tile g - 1, so wait for tile g - 1's MMAs first
-      if (loaded < t1 && loaded < col_end && loaded == g + WG_AHEAD) {
-        if (!settle(j == 0 ? WG_XSLOTS - 1 : j - 1, a.spin)) { failed = true; break; }
-        load_tile(ld, lj, false);
-        ++loaded;
-        advance(ld);
-        lj = next_slot(lj);
-      }
+      lastj = j;
       advance(cur);
       j = next_slot(j);
     }
-    // drain (bounded): copies still in flight, then every MMA issued
-    for (int sl = 0; sl < WG_XSLOTS; ++sl)
-      if (((fullout >> sl) & 1u) && !mbar_wait(full(sl), (fullpar >> sl) & 1u)) failed = true;
-    for (int sl = 0; sl < WG_XSLOTS; ++sl)
-      if (!settle(sl, tc::kSpinLimit)) failed = true;
+    // the accumulator is complete once the last commit's phase is (MMAs complete in order)
+    if (lastj >= 0 && !mbar_wait(done(lastj), ((donebit >> lastj) & 1u) ^ 1u)) failed = true;
     if (failed) failed_s = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
