@@ -517,6 +517,9 @@ struct ils_cnn {
   bf16* gact[2];           // gradient ping-pong, NHWC BF16
   bf16* pk8;               // a 3-channel plane set as NHWC rows of 8 BF16 (dL/du0 in the backward)
   bf16* pkf;               // f as NHWC rows of 8 BF16, written by the forward (layer 0's input)
+  // f and dL/du0 as NHWC rows of 32 BF16 whose channels 3-31 stay zero (zeroed once): the
+  // weight gradients read whole 64-byte pixels instead of TMA's zero fill of 8-channel rows
+  bf16* pk32[2];
   int step;
   bool packed;
   int* err;    // device flag raised by a tensor-core kernel whose bounded wait gave up
@@ -541,13 +544,16 @@ void cnn_free(ils_cnn* n) {
   cudaFree(n->gact[1]);
   cudaFree(n->pk8);
   cudaFree(n->pkf);
+  cudaFree(n->pk32[0]);
+  cudaFree(n->pk32[1]);
   cudaFree(n->err);
   delete n;
 }
 
 // planar FP32 [B][3][H][W] -> NHWC BF16 rows of 8 channels (3 values, then 5 zeros), the
 // layout the tensor-core weight gradient reads a 3-channel side in
-__global__ void planar3_to_nhwc8_kernel(const float* __restrict__ in, size_t hw, size_t n_px, bf16* __restrict__ out) {
+__global__ void planar3_to_nhwc8_kernel(const float* __restrict__ in, size_t hw, size_t n_px, bf16* __restrict__ out,
+                                        bf16* __restrict__ out32) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_px; i += (size_t)gridDim.x * blockDim.x) {
     const size_t b = i / hw, r = i - b * hw;
     const float* src = in + b * 3 * hw + r;
@@ -558,14 +564,17 @@ __global__ void planar3_to_nhwc8_kernel(const float* __restrict__ in, size_t hw,
     v.y = *reinterpret_cast<uint32_t*>(&c2z);
     v.z = 0u;
     v.w = 0u;
-    reinterpret_cast<uint4*>(out)[i] = v;
+    if (out != nullptr) reinterpret_cast<uint4*>(out)[i] = v;
+    if (out32 != nullptr) reinterpret_cast<uint4*>(out32)[4 * i] = v;  // channels 8-31 stay zero
   }
 }
 
-void planar3_to_nhwc8(const float* in, int B, int H, int W, bf16* out, cudaStream_t st) {
+// out (or null): rows of 8 channels; out32 (or null): the same 16 bytes at the start of rows of
+// 32 channels whose other 48 bytes are zero
+void planar3_to_nhwc8(const float* in, int B, int H, int W, bf16* out, cudaStream_t st, bf16* out32 = nullptr) {
   const size_t hw = (size_t)H * W, n_px = (size_t)B * hw;
   const size_t blocks = (n_px + 255) / 256;
-  planar3_to_nhwc8_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(in, hw, n_px, out);
+  planar3_to_nhwc8_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(in, hw, n_px, out, out32);
 }
 
 cudaError_t cnn_pack(ils_cnn* n, cudaStream_t st) {
@@ -647,6 +656,9 @@ ils_status ils_cnn_create(long long max_pixels, ils_cnn** out) {
   if (e == cudaSuccess && n->tc) e = ils::warm_fused_set_attributes();
   if (e == cudaSuccess && n->tc) e = cudaMalloc((void**)&n->pk8, n->max_px * 8 * sizeof(bf16));
   if (e == cudaSuccess && n->tc) e = cudaMalloc((void**)&n->pkf, n->max_px * 8 * sizeof(bf16));
+  for (int i = 0; i < 2 && e == cudaSuccess && n->tc; ++i)
+    if ((e = cudaMalloc((void**)&n->pk32[i], n->max_px * 32 * sizeof(bf16))) == cudaSuccess)
+      e = cudaMemset(n->pk32[i], 0, n->max_px * 32 * sizeof(bf16));
   if (e == cudaSuccess) {
     cudaFuncSetAttribute(conv_fwd_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)conv_smem(false, 4));
@@ -890,17 +902,21 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
     w.B = B; w.H = H; w.W = W; w.dy_nhwc = dy_nhwc; w.dy_planar = dy_planar;
     w.dw = n->gw[l]; w.db = n->gb[l]; w.cout = kCout[l]; w.tiles_x = grid.x; w.tiles_y = grid.y;
     if (n->tc) {
-      // every layer on tcgen05; a 3-channel side (f for layer 0, dL/du0 for layer 5) is
-      // packed into NHWC rows of 8 channels, rounded to BF16 as the mma.sync path stages it
+      // every layer on tcgen05; a 3-channel side (f for layer 0, dL/du0 for layer 5) is packed
+      // into NHWC rows of 32 channels (channels 3-31 zero), rounded to BF16 as the mma.sync path
+      // stages it; dL/du0 also into rows of 8 for layer 5's input gradient below
       cudaError_t e;
-      if (l == 0) {  // f as the forward packed it (the activations are the forward's too)
-        e = ils::launch_wgrad_tc(B, H, W, n->pkf, 3, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
-      } else if (dy_planar != nullptr) {
-        planar3_to_nhwc8(dy_planar, B, H, W, n->pk8, st);
-        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, n->pk8, kCout[l], n->gw[l], kpad(l), n->gb[l], n->err,
+      if (l == 0) {
+        planar3_to_nhwc8(f, B, H, W, nullptr, st, n->pk32[0]);
+        e = ils::launch_wgrad_tc(B, H, W, n->pk32[0], 32, 3, dy_nhwc, 32, 32, n->gw[l], kpad(l), n->gb[l], n->err,
                                  st);
+      } else if (dy_planar != nullptr) {
+        planar3_to_nhwc8(dy_planar, B, H, W, n->pk8, st, n->pk32[1]);
+        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, 32, n->pk32[1], 32, kCout[l], n->gw[l], kpad(l),
+                                 n->gb[l], n->err, st);
       } else {
-        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, dy_nhwc, 32, n->gw[l], kpad(l), n->gb[l], n->err, st);
+        e = ils::launch_wgrad_tc(B, H, W, n->act[l - 1], 32, 32, dy_nhwc, 32, 32, n->gw[l], kpad(l), n->gb[l], n->err,
+                                 st);
       }
       if (e != cudaSuccess && tc_err == cudaSuccess) tc_err = e;
     } else if (l == 0) {

@@ -624,16 +624,17 @@ cudaError_t conv32_tc_set_attributes() {
 }
 
 // dW += weight gradient, db += bias gradient of a conv3x3 from its NHWC BF16 input x and
-// output gradient dy (B x H x W x 32, or x 8 for a 3-channel side packed with zeros in
-// channels 3-7); dw is [co_n][kpad] FP32 with column (3 dy + dx) ci_n + ci, db [co_n] FP32.
-cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int ci_n, const void* dy, int co_n, float* dw,
-                            int kpad, float* db, int* error, cudaStream_t st) {
+// output gradient dy (B x H x W x x_ch / dy_ch, 32 or 8; channels beyond ci_n / co_n zero); dw
+// is [co_n][kpad] FP32 with column (3 dy + dx) ci_n + ci, db [co_n] FP32.  Rows of 8 channels
+// are widened to 32 by TMA's zero fill, which costs: a 3-channel side is cheaper in rows of 32
+// channels whose channels 3-31 are zero.
+cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int x_ch, int ci_n, const void* dy, int dy_ch, int co_n,
+                            float* dw, int kpad, float* db, int* error, cudaStream_t st) {
   using namespace cnn_tc;
   if (encode_fn() == nullptr) return cudaErrorNotSupported;
-  if (ci_n < 1 || ci_n > 32 || co_n < 1 || co_n > 32 || kpad < 9 * ci_n) return cudaErrorInvalidValue;
+  if (ci_n < 1 || ci_n > x_ch || co_n < 1 || co_n > dy_ch || kpad < 9 * ci_n) return cudaErrorInvalidValue;
   CUtensorMap xm, dm;
-  if (!make_nhwc32_map_sw64(&xm, x, B, H, W, WG_TILE, ci_n <= 8 ? 8 : 32) ||
-      !make_nhwc32_map_sw64(&dm, dy, B, H, W, WG_TILE, co_n <= 8 ? 8 : 32))
+  if (!make_nhwc32_map_sw64(&xm, x, B, H, W, WG_TILE, x_ch) || !make_nhwc32_map_sw64(&dm, dy, B, H, W, WG_TILE, dy_ch))
     return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -241,8 +241,9 @@ cudaError_t launch_conv3_tc(int B, int H, int W, const void* in8, const void* wt
 // weight and bias gradients of a conv3x3 with ci_n, co_n <= 32 on tcgen05, accumulated into
 // dw [co_n][kpad] (column (3 dy + dx) ci_n + ci) and db [co_n]; x and dy are NHWC BF16 rows of
 // 32 channels, or of 8 (channels beyond ci_n / co_n zero) for a side with at most 8
-cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int ci_n, const void* dy, int co_n, float* dw,
-                            int kpad, float* db, int* error, cudaStream_t st);
+// (x_ch, dy_ch: channels per NHWC row of x and dy, 8 or 32)
+cudaError_t launch_wgrad_tc(int B, int H, int W, const void* x, int x_ch, int ci_n, const void* dy, int dy_ch, int co_n,
+                            float* dw, int kpad, float* db, int* error, cudaStream_t st);
 // warm-start network inference as two fused tcgen05 kernels (ils_cnn_fused.cu)
 cudaError_t warm_fused_set_attributes();
 cudaError_t launch_warm_fused(int B, int H, int W, const float* f, void* act, float* u0, const void* const* w,
