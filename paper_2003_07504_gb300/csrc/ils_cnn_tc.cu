@@ -22,7 +22,8 @@
 // of 8-byte elements (1-KB rows instead of 130 rows of 16 bytes).
 //
 // The kernel is a persistent pipeline: one warp issues the TMA copies into a ring of input
-// stages, one issues the MMAs into two tensor-memory accumulators, four drain them.
+// stages, one issues the MMAs into two tensor-memory accumulators, eight drain them (two per
+// tensor-memory lane quarter, 16 output channels each).
 // Every wait on an mbarrier is bounded; on timeout the kernel raises a flag, waits (also
 // bounded) for its own copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda.h>
@@ -79,7 +80,7 @@ constexpr int RB = 9216;                                // bytes per row buffer 
 constexpr int A32_BYTES = 3 * RB;                       // 27648
 constexpr int STAGES = 3;                               // input tiles in flight
 constexpr int SMEM_PIPE = 1024 + STAGES * A32_BYTES + B_BYTES + 128 + 128;
-constexpr int NTHR = 192;                               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int NTHR = 320;                               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 
 // The 3-channel variant (IN8): the input is an NHWC row of 8 channels (3 values, 5 zeros), one
 // chunk plane per stage.  A tap is then half a K = 16 step, so step j pairs taps 2j and 2j + 1:
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf(b), 1);
-      mbar_init(acce(b), 128);
+      mbar_init(acce(b), 256);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -248,22 +249,20 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
     for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
       if (!mbar_wait(accf(i & 1), (i >> 1) & 1)) failed = true;
   } else if (warp >= 2) {
-    // ---------------- epilogue: thread -> pixel (tensor-memory lane) 32 * (warp % 4) + lane
-    const int q = warp & 3;
+    // ---------------- epilogue: thread -> pixel (tensor-memory lane) 32 * (warp % 4) + lane and
+    // output channels 16 h .. 16 h + 15 (warps 2-5: h = 0, warps 6-9: h = 1)
+    const int q = warp & 3, h16 = (warp - 2) >> 2;
     const int px = q * 32 + lane;
     for (int i = 0; i < my_tiles; ++i) {
       const int acc = i & 1;
       if (!mbar_wait(accf(acc), (i >> 1) & 1, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t r[32];
-      const uint32_t taddr = tmem + acc * 32 + ((uint32_t)(q * 32) << 16);
+      uint32_t r[16];
+      const uint32_t taddr = tmem + acc * 32 + h16 * 16 + ((uint32_t)(q * 32) << 16);
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -274,15 +273,16 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       const int y = rr / tiles_x, x = (rr - y * tiles_x) * TILE + px;
       if (x < a.W) {
         const size_t pix = ((size_t)b * a.H + y) * a.W + x;
-        uint4 mk[4];
+        uint4 mk[2];
         if (a.mask != nullptr)
 #pragma unroll
-          for (int t = 0; t < 4; ++t) mk[t] = reinterpret_cast<const uint4*>(a.mask + pix * 32)[t];
-        uint4 o[4];
+          for (int t = 0; t < 2; ++t) mk[t] = reinterpret_cast<const uint4*>(a.mask + pix * 32 + h16 * 16)[t];
+        uint4 o[2];
         uint32_t* ow = reinterpret_cast<uint32_t*>(o);
 #pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          float v0 = __uint_as_float(r[c]) + sbias[c], v1 = __uint_as_float(r[c + 1]) + sbias[c + 1];
+        for (int c = 0; c < 16; c += 2) {
+          const int ch = h16 * 16 + c;
+          float v0 = __uint_as_float(r[c]) + sbias[ch], v1 = __uint_as_float(r[c + 1]) + sbias[ch + 1];
           if (a.relu) {
             v0 = fmaxf(v0, 0.0f);
             v1 = fmaxf(v1, 0.0f);
@@ -292,11 +292,11 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
             if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
             if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
           }
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          ow[c >> 1] = *reinterpret_cast<uint32_t*>(&h);
+          __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
+          ow[c >> 1] = *reinterpret_cast<uint32_t*>(&hv);
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) reinterpret_cast<uint4*>(a.out + pix * 32)[t] = o[t];
+        for (int t = 0; t < 2; ++t) reinterpret_cast<uint4*>(a.out + pix * 32 + h16 * 16)[t] = o[t];
       }
     }
   }
