@@ -306,6 +306,212 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
+// ---------------------------------------------------------------- 32-channel input, row ring
+// The same convolution with each CTA walking a contiguous range of tiles down its columns
+// (tile g: column g / H, output row g % H), so that consecutive tiles share input rows: a ring
+// of CR_RING row buffers (row r in buffer r mod CR_RING, 130 pixels x 64 bytes with the 64-byte
+// swizzle) holds rows y - 1 .. y + 1 of the tiles in flight, and a tile needs one new row (three
+// at the start of a column run).  Tap (dy, dx) of output row y is the operand at pixel dx of the
+// buffer of row y - 1 + dy.  One thread issues the copies: tile g takes barrier slot j =
+// (g - t0) mod CR_NT once the MMAs of the slot's previous tile (g - CR_NT) are done, which also
+// were the last to read the ring buffer its new row takes (CR_RING = CR_NT + 2); a column run
+// starts after every MMA issued is done.  One thread issues the MMAs into two accumulators,
+// eight warps drain them as in conv32_tc_kernel.
+constexpr int CR_NT = 4;
+constexpr int CR_RING = CR_NT + 2;
+constexpr int CR_ROWS_BYTES = CR_RING * RB;                               // 55296
+constexpr int SMEM_RING = 1024 + CR_ROWS_BYTES + B_BYTES + 128 + 128;
+
+__device__ __forceinline__ int cr_ring(int r) { return ((r % CR_RING) + CR_RING) % CR_RING; }
+
+__global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* rows = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
+  unsigned char* sB = rows + CR_ROWS_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + B_BYTES);
+  float* sbias = reinterpret_cast<float*>(sB + B_BYTES + 128);
+  __shared__ uint32_t tmem_base_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int j) { return saddr(&bars[j]); };
+  auto empty = [&](int j) { return saddr(&bars[CR_NT + j]); };
+  auto accf = [&](int b) { return saddr(&bars[2 * CR_NT + b]); };
+  auto acce = [&](int b) { return saddr(&bars[2 * CR_NT + 2 + b]); };
+  auto next_slot = [](int j) { return j + 1 == CR_NT ? 0 : j + 1; };
+
+  for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
+    const int kc = q >> 5, co = q & 31;
+    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
+  }
+  if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias != nullptr ? a.bias[threadIdx.x] : 0.0f;
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < CR_NT; ++j) {
+      mbar_init(full(j), 1);
+      mbar_init(empty(j), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf(b), 1);
+      mbar_init(acce(b), 256);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+
+  const int tiles_x = (a.W + TILE - 1) / TILE;
+  const int total = a.B * tiles_x * a.H;
+  const int t0 = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int t1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  // a tile's position (column col of image b at pixel x0, output row y), advanced one tile at a
+  // time: a division only when a column ends
+  struct Pos {
+    int col, y, b, x0;
+  };
+  auto set_col = [&](Pos& p) {
+    p.b = p.col / tiles_x;
+    p.x0 = (p.col - p.b * tiles_x) * TILE;
+  };
+  auto start = [&](int g) {
+    Pos p;
+    p.col = g / a.H;
+    p.y = g - p.col * a.H;
+    set_col(p);
+    return p;
+  };
+  auto advance = [&](Pos& p) {
+    if (++p.y == a.H) {
+      p.y = 0;
+      ++p.col;
+      set_col(p);
+    }
+  };
+  bool failed = false;
+
+  if (warp == 0 && lane == 0 && t1 > t0) {
+    // ---------------- copy thread.  Per slot (bit j): loads so far mod 2, a load whose MMAs
+    // this thread has not waited for, a slot loaded at least once.
+    uint32_t loadpar = 0, outstanding = 0, used = 0;
+    Pos ld = start(t0);
+    int lj = 0;
+    for (int g = t0; g < t1 && !failed; ++g) {
+      const bool first = g == t0 || ld.y == 0;
+      const uint32_t need = first ? outstanding : (outstanding & (1u << lj));
+      for (int j = 0; j < CR_NT; ++j)
+        if ((need >> j) & 1u) {
+          if (!mbar_wait(empty(j), ((loadpar >> j) & 1u) ^ 1u, a.spin)) {
+            failed = true;
+            break;
+          }
+          outstanding &= ~(1u << j);
+        }
+      if (failed) break;
+      mbar_expect_tx(full(lj), (first ? 3 : 1) * HALO_W * 64);
+      for (int r = first ? ld.y - 1 : ld.y + 1; r <= ld.y + 1; ++r)
+        tma_load_4d(saddr(rows + cr_ring(r) * RB), &in_map, 0, ld.x0 - 1, r, ld.b, full(lj));
+      loadpar ^= 1u << lj;
+      outstanding |= 1u << lj;
+      used |= 1u << lj;
+      advance(ld);
+      lj = next_slot(lj);
+    }
+    // every copy issued must have landed before the CTA may end (bounded)
+    for (int j = 0; j < CR_NT; ++j)
+      if (((used >> j) & 1u) && !mbar_wait(full(j), ((loadpar >> j) & 1u) ^ 1u)) failed = true;
+  } else if (warp == 1 && lane == 0 && t1 > t0) {
+    // ---------------- MMA thread
+    const uint32_t b0 = saddr(sB), rows0 = saddr(rows);
+    uint64_t db[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) db[q] = smem_desc(b0 + (uint32_t)(((q >> 1) * 4 + (q & 1) * 2) * 512), 512, 128);
+    uint32_t fullpar = 0;
+    Pos cur = start(t0);
+    int j = 0, issued = 0;
+    for (int i = 0; i < t1 - t0; ++i) {
+      const int acc = i & 1;
+      if (!mbar_wait(full(j), (fullpar >> j) & 1u, a.spin)) { failed = true; break; }
+      fullpar ^= 1u << j;
+      if (i >= 2 && !mbar_wait(acce(acc), ((i >> 1) & 1) ^ 1, a.spin)) { failed = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + acc * 32;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const uint64_t da0 = smem_desc_sw64(rows0 + (uint32_t)(cr_ring(cur.y - 1 + dy) * RB), 16, 512);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {  // (dx, channel half) of tap (dy, dx)
+          const int dx = q >> 1, kk = q & 1;
+          mma_f16(d, da0 + (uint64_t)((dx * 64 + kk * 32) >> 4), db[dy * 6 + q], (dy | q) ? 1u : 0u);
+        }
+      }
+      mma_commit(empty(j));
+      mma_commit(accf(acc));
+      issued = i + 1;
+      advance(cur);
+      j = next_slot(j);
+    }
+    // the MMAs issued must complete before tensor memory is freed (bounded)
+    for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+      if (!mbar_wait(accf(i & 1), (i >> 1) & 1)) failed = true;
+  } else if (warp >= 2 && t1 > t0) {
+    // ---------------- epilogue: thread -> pixel 32 * (warp % 4) + lane, channels 16 h .. + 15
+    const int q = warp & 3, h16 = (warp - 2) >> 2;
+    const int px = q * 32 + lane;
+    Pos cur = start(t0);
+    for (int i = 0; i < t1 - t0; ++i, advance(cur)) {
+      const int acc = i & 1;
+      if (!mbar_wait(accf(acc), (i >> 1) & 1, a.spin)) { failed = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r[16];
+      const uint32_t taddr = tmem + acc * 32 + h16 * 16 + ((uint32_t)(q * 32) << 16);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce(acc));
+      const int x = cur.x0 + px;
+      if (x < a.W) {
+        const size_t pix = ((size_t)cur.b * a.H + cur.y) * a.W + x;
+        uint4 mk[2];
+        if (a.mask != nullptr)
+#pragma unroll
+          for (int t = 0; t < 2; ++t) mk[t] = reinterpret_cast<const uint4*>(a.mask + pix * 32 + h16 * 16)[t];
+        uint4 o[2];
+        uint32_t* ow = reinterpret_cast<uint32_t*>(o);
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+          const int ch = h16 * 16 + c;
+          float v0 = __uint_as_float(r[c]) + sbias[ch], v1 = __uint_as_float(r[c + 1]) + sbias[ch + 1];
+          if (a.relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          if (a.mask != nullptr) {
+            const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mk)[c >> 1];
+            if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+            if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+          }
+          __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
+          ow[c >> 1] = *reinterpret_cast<uint32_t*>(&hv);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) reinterpret_cast<uint4*>(a.out + pix * 32 + h16 * 16)[t] = o[t];
+      }
+    }
+  }
+  if (failed) atomicExch(a.error, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
 // ---------------------------------------------------------------- weight gradient
 // dW[co][(3 dy + dx) ci_n + ci] += sum_p dY[p][co] X[p + (dy - 1, dx - 1)][ci] and db[co] +=
 // sum_p dY[p][co] over every pixel p of the batch: the weight gradient of a conv3x3 with
@@ -616,6 +822,9 @@ cudaError_t conv32_tc_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cnn_tc::SMEM_PIPE);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           cnn_tc::SMEM_RING);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            cnn_tc::SMEM_PIPE_IN8);
   if (e != cudaSuccess) return e;
@@ -684,7 +893,7 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
   if (in8)
     conv32_tc_kernel<true><<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, map2, a);
   else
-    conv32_tc_kernel<false><<<grid, NTHR, SMEM_PIPE, st>>>(map, map2, a);
+    conv32_ring_tc_kernel<<<grid, NTHR, SMEM_RING, st>>>(map, a);
   return cudaGetLastError();
 }
 
