@@ -1,31 +1,33 @@
-// 32 -> 32 channel 3x3 convolution (the four middle layers of the warm-start network, and
-// their input gradients) on the 5th-generation tensor cores: TMA -> shared memory ->
-// tcgen05.mma (accumulator in tensor memory) -> tcgen05.ld epilogue.
+// 3x3 convolutions of the warm-start network on the 5th-generation tensor cores (TMA -> shared
+// memory -> tcgen05.mma, accumulator in tensor memory -> tcgen05.ld epilogue): the 32 -> 32
+// layers and their input gradients (conv32_ring_tc_kernel), the 3 -> 32 layer and the input
+// gradient of the 32 -> 3 layer (conv3_tc_kernel), and the weight gradients of every layer
+// (conv32_wgrad_tc_kernel).
 //
-// GEMM view per tile: M = 128 consecutive output pixels of one image row, N = 32 output
-// channels, K = 9 taps x 32 input channels, issued as 18 MMAs of K = 16 (BF16 in, FP32
-// accumulate).  The input rows y-1, y, y+1 over pixels x0-1 .. x0+128 arrive as three TMA
-// copies of 130 pixels x 64 bytes (all 32 channels of a pixel in one 64-byte row) with the
-// 64-byte swizzle, each into its own 1024-byte-aligned row buffer.  That is the canonical
-// 64-byte-swizzled K-major operand (8-pixel groups 512 bytes apart): tap (dy, dx) starts at
-// pixel dx of row buffer dy and the second K half 32 bytes further.  The hardware applies the
-// swizzle to the absolute shared-memory address on both sides (TMA write, MMA read), so a
-// start inside the 512-byte pattern needs no base offset in the descriptor (measured: the
-// offset (start >> 7) & 7 gives wrong results, 0 gives the mma.sync kernels' results).  Four
-// copies of 16-byte channel chunks into a chunk-major layout (the no-swizzle form) moved the
-// same bytes as 1,560 16-byte rows per tile with twice the sectors; on the 16 x 256 x 256
-// training batch a launch took 67 us that way and the training step 1.31 ms, against 1.11 ms
-// now.  Out-of-image pixels come from TMA's zero fill (the convolution's zero padding).  The
-// weights, [K-chunk][output channel][8] (no swizzle), stay in shared memory for all tiles of a
-// persistent CTA.  A 3-channel input (IN8) keeps the chunk-major form (one 8-channel plane, 16
-// bytes per pixel, rows 136 pixels apart), each image row loaded as copies of 64 and 66 pixels
-// of 8-byte elements (1-KB rows instead of 130 rows of 16 bytes).
+// GEMM view of a convolution tile: M = 128 consecutive output pixels of one image row, N = 32
+// output channels, K = 9 taps x input channels in MMAs of K = 16 (BF16 in, FP32 accumulate).
+// With 32 input channels a row of pixels x0-1 .. x0+128 is one TMA copy of 130 pixels x 64
+// bytes (all 32 channels of a pixel in one 64-byte row) with the 64-byte swizzle into a
+// 1024-byte-aligned row buffer.  That is the canonical 64-byte-swizzled K-major operand
+// (8-pixel groups 512 bytes apart): tap (dy, dx) starts at pixel dx of the buffer of row
+// y - 1 + dy and the second K half 32 bytes further.  The hardware applies the swizzle to the
+// absolute shared-memory address on both sides (TMA write, MMA read), so a start inside the
+// 512-byte pattern needs no base offset in the descriptor (measured: the offset
+// (start >> 7) & 7 gives wrong results, 0 gives the mma.sync kernels' results).  Four copies of
+// 16-byte channel chunks into a chunk-major layout (the no-swizzle form) moved the same bytes
+// as 1,560 16-byte rows per tile with twice the sectors: 67 us per launch on the 16 x 256 x 256
+// training batch that way, 38 us with the swizzled rows, 36 us with the row ring.  Out-of-image
+// pixels come from TMA's zero fill (the convolution's zero padding).  The weights,
+// [K-chunk][output channel][8] (no swizzle), stay in shared memory for all tiles of a
+// persistent CTA.  A 3-channel input keeps the chunk-major form (one 8-channel plane, 16 bytes
+// per pixel, rows 136 pixels apart), each image row loaded as copies of 64 and 66 pixels of
+// 8-byte elements (1-KB rows instead of 130 rows of 16 bytes).
 //
-// The kernel is a persistent pipeline: one warp issues the TMA copies into a ring of input
-// stages, one issues the MMAs into two tensor-memory accumulators, eight drain them (two per
-// tensor-memory lane quarter, 16 output channels each).
-// Every wait on an mbarrier is bounded; on timeout the kernel raises a flag, waits (also
-// bounded) for its own copies and MMAs in flight, frees its tensor memory and returns.
+// The convolution kernels are persistent pipelines: one warp issues the TMA copies, one the
+// MMAs into two tensor-memory accumulators, eight drain them (two per tensor-memory lane
+// quarter, 16 output channels each).  Every wait on an mbarrier is bounded; on timeout the
+// kernel raises a flag, waits (also bounded) for its own copies and MMAs in flight, frees its
+// tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,7 +44,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TILE = 128;                  // pixels per tile (M)
 constexpr int HALO_W = TILE + 2;           // 130
-constexpr int TMA_BYTES = 3 * HALO_W * 64;      // 24960 bytes delivered per tile
 constexpr int B_CHUNKS = 36;               // K = 288 = 36 chunks of 8
 constexpr int B_BYTES = B_CHUNKS * 32 * 16;  // 18432
 using tc::kSpinLimit;
@@ -74,12 +75,9 @@ struct TcArgs {
   uint32_t spin;      // poll limit of the per-tile waits (a test sets it tiny to exercise the timeout path)
 };
 
-// 32-channel input: the rows y-1, y, y+1 over pixels x0-1 .. x0+128 as three TMA copies of
-// 130 pixels x 64 bytes with the 64-byte swizzle, one 1024-byte-aligned buffer per row
+// 32-channel input: a row of pixels x0-1 .. x0+128 as one TMA copy of 130 pixels x 64 bytes
+// with the 64-byte swizzle, in a 1024-byte-aligned buffer
 constexpr int RB = 9216;                                // bytes per row buffer (130 x 64 = 8320 used)
-constexpr int A32_BYTES = 3 * RB;                       // 27648
-constexpr int STAGES = 3;                               // input tiles in flight
-constexpr int SMEM_PIPE = 1024 + STAGES * A32_BYTES + B_BYTES + 128 + 128;
 constexpr int NTHR = 320;                               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 
 // The 3-channel variant (IN8): the input is an NHWC row of 8 channels (3 values, 5 zeros), one
@@ -100,16 +98,16 @@ constexpr int SMEM_PIPE_IN8 = 1024 + IN8_STAGES * IN8_A_BYTES + IN8_B_BYTES + 12
 
 __host__ __device__ constexpr int in8_tap(int chunk) { return chunk < 8 ? chunk : (chunk == 8 ? -1 : 8); }
 
-// Persistent, warp-specialized pipeline.  Tile i uses input stage i % STAGES and
-// accumulator i % 2 (32 tensor-memory columns each).  Barriers (phase parity from the
+// The 3-channel convolution (IN8 input): a persistent, warp-specialized pipeline.  Tile i
+// (output row y, pixels x0 .. x0 + 127; tiles strided over the CTAs) uses input stage
+// i % IN8_STAGES and accumulator i % 2 (32 tensor-memory columns each).  Barriers (phase parity from the
 // use count): full[s] TMA -> MMA, empty[s] MMA -> TMA (tcgen05.commit), accf[b] MMA ->
 // epilogue, acce[b] epilogue -> MMA (128 arrivals).
-template <bool IN8>
-__global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap in_map,
-                                                            const __grid_constant__ CUtensorMap in_map2, TcArgs a) {
-  constexpr int NST = IN8 ? IN8_STAGES : STAGES;
-  constexpr int ABYTES = IN8 ? IN8_A_BYTES : A32_BYTES;
-  constexpr int BBYTES = IN8 ? IN8_B_BYTES : B_BYTES;
+__global__ void __launch_bounds__(NTHR, 1) conv3_tc_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                           const __grid_constant__ CUtensorMap in_map2, TcArgs a) {
+  constexpr int NST = IN8_STAGES;
+  constexpr int ABYTES = IN8_A_BYTES;
+  constexpr int BBYTES = IN8_B_BYTES;
   extern __shared__ __align__(128) unsigned char smraw[];
   // stages on a 1024-byte boundary: the 64-byte swizzle pattern repeats every 512 bytes
   unsigned char* sm = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);
@@ -123,27 +121,20 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
   auto accf = [&](int b) { return saddr(&bars[2 * NST + b]); };
   auto acce = [&](int b) { return saddr(&bars[2 * NST + 2 + b]); };
 
-  if (IN8) {
-    for (int q = threadIdx.x; q < IN8_CHUNKS * 32; q += blockDim.x) {
-      const int kc = q >> 5, co = q & 31, tap = in8_tap(kc);
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      if (tap >= 0) {
-        const bf16* src = a.wt + co * 32 + tap * 3;
-        __nv_bfloat162 c01, c2z;
-        c01.x = src[0];
-        c01.y = src[1];
-        c2z.x = src[2];
-        c2z.y = __float2bfloat16_rn(0.0f);
-        w[0] = *reinterpret_cast<uint32_t*>(&c01);
-        w[1] = *reinterpret_cast<uint32_t*>(&c2z);
-      }
-      *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+  for (int q = threadIdx.x; q < IN8_CHUNKS * 32; q += blockDim.x) {
+    const int kc = q >> 5, co = q & 31, tap = in8_tap(kc);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (tap >= 0) {
+      const bf16* src = a.wt + co * 32 + tap * 3;
+      __nv_bfloat162 c01, c2z;
+      c01.x = src[0];
+      c01.y = src[1];
+      c2z.x = src[2];
+      c2z.y = __float2bfloat16_rn(0.0f);
+      w[0] = *reinterpret_cast<uint32_t*>(&c01);
+      w[1] = *reinterpret_cast<uint32_t*>(&c2z);
     }
-  } else {
-    for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
-      const int kc = q >> 5, co = q & 31;
-      *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
-    }
+    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias != nullptr ? a.bias[threadIdx.x] : 0.0f;
   if (threadIdx.x == 0) {
@@ -182,15 +173,13 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       const int y = rr / tiles_x, x0 = (rr - y * tiles_x) * TILE;
       const int s = i % NST;
       if (i >= NST && !mbar_wait(empty(s), ((i / NST) & 1) ^ 1, a.spin)) { failed = true; break; }
-      mbar_expect_tx(full(s), IN8 ? IN8_TMA_BYTES : TMA_BYTES);
-      if (IN8)  // per row a copy of 64 and one of 66 pixels (x in 8-byte units: always even)
-        for (int r = 0; r < 3; ++r) {
-          const uint32_t row = saddr(sm + s * ABYTES + r * IN8_RPX * 16);
-          tc::tma_load_3d(row, &in_map, 2 * (x0 - 1), y - 1 + r, b, full(s));
-          tc::tma_load_3d(row + IN8_C0 * 16, &in_map2, 2 * (x0 - 1 + IN8_C0), y - 1 + r, b, full(s));
-        }
-      else
-        for (int r = 0; r < 3; ++r) tma_load_4d(saddr(sm + s * ABYTES + r * RB), &in_map, 0, x0 - 1, y - 1 + r, b, full(s));
+      mbar_expect_tx(full(s), IN8_TMA_BYTES);
+      // per row a copy of 64 and one of 66 pixels (x in 8-byte units: always even)
+      for (int r = 0; r < 3; ++r) {
+        const uint32_t row = saddr(sm + s * ABYTES + r * IN8_RPX * 16);
+        tc::tma_load_3d(row, &in_map, 2 * (x0 - 1), y - 1 + r, b, full(s));
+        tc::tma_load_3d(row + IN8_C0 * 16, &in_map2, 2 * (x0 - 1 + IN8_C0), y - 1 + r, b, full(s));
+      }
       issued = i + 1;
     }
     // before the CTA may end, every copy issued must have landed (bounded)
@@ -202,13 +191,10 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
     // from its first one only in the start-address field (address >> 4, 14 bits; every address
     // here is below 256 KB, so adding a tap's offset >> 4 never carries out of the field): one
     // 64-bit add per MMA instead of a descriptor build.
-    constexpr int NMMA = IN8 ? IN8_STEPS : 18;
     const uint32_t b0 = saddr(sB);
-    uint64_t db[NMMA];
+    uint64_t db[IN8_STEPS];
 #pragma unroll
-    for (int q = 0; q < NMMA; ++q)
-      db[q] = IN8 ? smem_desc(b0 + (uint32_t)(2 * q * 512), 512, 128)
-                  : smem_desc(b0 + (uint32_t)(((q >> 1) * 4 + (q & 1) * 2) * 512), 512, 128);
+    for (int q = 0; q < IN8_STEPS; ++q) db[q] = smem_desc(b0 + (uint32_t)(2 * q * 512), 512, 128);
     int issued = 0, s = 0, sphase = 0;  // stage of tile i and the parity of its full barrier
     for (int i = 0; i < my_tiles; ++i) {
       const int acc = i & 1;
@@ -216,26 +202,15 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
       if (i >= 2 && !mbar_wait(acce(acc), ((i >> 1) & 1) ^ 1, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = saddr(sm + s * ABYTES), d = tmem + acc * 32;
-      if (IN8) {
-        const uint64_t da0 = smem_desc(a0, 16, 128);
+      const uint64_t da0 = smem_desc(a0, 16, 128);
 #pragma unroll
-        for (int j = 0; j < IN8_STEPS; ++j) {
-          // taps t0 (K half 0) and t1 (K half 1) of this step; byte offset of tap t's pixel 0
-          const int t0 = j < 4 ? 2 * j : 7, t1 = j < 4 ? 2 * j + 1 : 8;
-          const int o0 = ((t0 / 3) * IN8_RPX + t0 % 3) * 16, o1 = ((t1 / 3) * IN8_RPX + t1 % 3) * 16;
-          // the K stride (LBO, bits 16-29) is the distance between the two taps
-          const uint64_t da = (da0 & ~(0x3FFFull << 16)) + (uint64_t)(o0 >> 4) + ((uint64_t)((o1 - o0) >> 4) << 16);
-          mma_f16(d, da, db[j], j ? 1u : 0u);
-        }
-      } else {
-        const uint64_t da0 = smem_desc_sw64(a0, 16, 512);
-#pragma unroll
-        for (int q = 0; q < 18; ++q) {
-          // tap q / 2 = (dy, dx): pixel dx of row buffer dy; channels 16 (q % 2) .. + 15
-          const int tap = q >> 1, dy = tap / 3, dx = tap % 3, kk = q & 1;
-          const uint64_t da = da0 + (uint64_t)((dy * RB + dx * 64 + kk * 32) >> 4);
-          mma_f16(d, da, db[q], q ? 1u : 0u);
-        }
+      for (int j = 0; j < IN8_STEPS; ++j) {
+        // taps t0 (K half 0) and t1 (K half 1) of this step; byte offset of tap t's pixel 0
+        const int t0 = j < 4 ? 2 * j : 7, t1 = j < 4 ? 2 * j + 1 : 8;
+        const int o0 = ((t0 / 3) * IN8_RPX + t0 % 3) * 16, o1 = ((t1 / 3) * IN8_RPX + t1 % 3) * 16;
+        // the K stride (LBO, bits 16-29) is the distance between the two taps
+        const uint64_t da = (da0 & ~(0x3FFFull << 16)) + (uint64_t)(o0 >> 4) + ((uint64_t)((o1 - o0) >> 4) << 16);
+        mma_f16(d, da, db[j], j ? 1u : 0u);
       }
       mma_commit(empty(s));
       mma_commit(accf(acc));
@@ -316,7 +291,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_tc_kernel(const __grid_constan
 // (g - t0) mod CR_NT once the MMAs of the slot's previous tile (g - CR_NT) are done, which also
 // were the last to read the ring buffer its new row takes (CR_RING = CR_NT + 2); a column run
 // starts after every MMA issued is done.  One thread issues the MMAs into two accumulators,
-// eight warps drain them as in conv32_tc_kernel.
+// eight warps drain them as in conv3_tc_kernel.
 constexpr int CR_NT = 4;
 constexpr int CR_RING = CR_NT + 2;
 constexpr int CR_ROWS_BYTES = CR_RING * RB;                               // 55296
@@ -819,14 +794,10 @@ bool make_nhwc8_row_map(CUtensorMap* map, const void* act, int B, int H, int W, 
 }
 
 cudaError_t conv32_tc_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       cnn_tc::SMEM_PIPE);
+  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       cnn_tc::SMEM_RING);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           cnn_tc::SMEM_RING);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(cnn_tc::conv32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           cnn_tc::SMEM_PIPE_IN8);
+  e = cudaFuncSetAttribute(cnn_tc::conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cnn_tc::SMEM_PIPE_IN8);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(cnn_tc::conv32_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               cnn_tc::WG_SMEM);
@@ -891,7 +862,7 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
   const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
   a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
   if (in8)
-    conv32_tc_kernel<true><<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, map2, a);
+    conv3_tc_kernel<<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, map2, a);
   else
     conv32_ring_tc_kernel<<<grid, NTHR, SMEM_RING, st>>>(map, a);
   return cudaGetLastError();
