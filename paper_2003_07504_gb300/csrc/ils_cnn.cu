@@ -16,10 +16,10 @@
 // flipped in space and transposed in channels (kernels dgrad_*); the weight gradient is
 // a GEMM over pixels (dW = sum_p dY(p)^T im2col(X)(p)) computed with the same MMA and
 // reduced into FP32 with atomics.  ReLU masks use the stored post-ReLU activations.
-// With tcgen05 available, the 32 -> 32 layers' forward and input gradients and every
-// layer's weight gradient run on the tcgen05 kernels of ils_cnn_tc.cu (a 3-channel side
-// packed into 8-channel NHWC rows first); these kernels remain for the forward and input
-// gradient of the 3-channel first and last layers (and as the whole network without tcgen05).
+// With tcgen05 available, every layer's forward, input gradient and weight gradient runs on
+// the tcgen05 kernels of ils_cnn_tc.cu (a 3-channel side packed into NHWC rows first); these
+// kernels remain as the whole network without tcgen05 (ILS_CNN_TC=0), the reference the
+// tensor-core kernels are tested against.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -838,10 +838,16 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
     m.out_nhwc = n->act[l]; m.relu = 1; m.cout = 32;
     conv_fwd_kernel<false, 4, false><<<grid, NTHREADS, conv_smem(false, 4), st>>>(m);
   }
-  ConvArgs z{};
-  z.B = B; z.H = H; z.W = W; z.in_nhwc = n->act[kLayers - 2]; z.wt = n->wf[kLayers - 1]; z.bias = n->b[kLayers - 1];
-  z.out_planar = u0; z.resid = f; z.cout = 3;
-  conv_fwd_kernel<false, 1, true><<<grid, NTHREADS, conv_smem(false, 1), st>>>(z);
+  if (n->tc) {  // layer 5: 32 -> 3 plus the residual f
+    cudaError_t e = ils::launch_conv_last_tc(B, H, W, n->act[kLayers - 2], n->wf[kLayers - 1], n->b[kLayers - 1], f,
+                                             u0, n->err, st);
+    if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
+  } else {
+    ConvArgs z{};
+    z.B = B; z.H = H; z.W = W; z.in_nhwc = n->act[kLayers - 2]; z.wt = n->wf[kLayers - 1]; z.bias = n->b[kLayers - 1];
+    z.out_planar = u0; z.resid = f; z.cout = 3;
+    conv_fwd_kernel<false, 1, true><<<grid, NTHREADS, conv_smem(false, 1), st>>>(z);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ILS_OK : cnn_fail(e, "cnn forward launch");
 }

@@ -70,6 +70,8 @@ struct TcArgs {
   const float* bias;  // [32] or null
   bf16* out;          // NHWC BF16
   const bf16* mask;   // NHWC BF16, or null: output zeroed where mask <= 0
+  float* out_planar;  // LAST (32 -> 3): B x 3 x H x W FP32 output, out_planar = resid + conv + bias
+  const float* resid;
   int relu;
   int* error;         // set to 1 when a bounded wait gave up
   uint32_t spin;      // poll limit of the per-tile waits (a test sets it tiny to exercise the timeout path)
@@ -299,6 +301,9 @@ constexpr int SMEM_RING = 1024 + CR_ROWS_BYTES + B_BYTES + 128 + 128;
 
 __device__ __forceinline__ int cr_ring(int r) { return ((r % CR_RING) + CR_RING) % CR_RING; }
 
+// LAST: the 32 -> 3 last layer with the residual, N = 16 (output channels 3-15 zero weights) and
+// a planar FP32 epilogue; weights [8 padded rows][288] as the forward GEMM rows of that layer.
+template <bool LAST>
 __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
   unsigned char* rows = smraw + ((1024u - (saddr(smraw) & 1023u)) & 1023u);  // 1024-byte aligned
@@ -313,11 +318,13 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_co
   auto acce = [&](int b) { return saddr(&bars[2 * CR_NT + 2 + b]); };
   auto next_slot = [](int j) { return j + 1 == CR_NT ? 0 : j + 1; };
 
-  for (int q = threadIdx.x; q < B_CHUNKS * 32; q += blockDim.x) {
-    const int kc = q >> 5, co = q & 31;
-    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc];
+  constexpr int NCO = LAST ? 16 : 32;  // N of the MMAs: rows of the weight chunks
+  for (int q = threadIdx.x; q < B_CHUNKS * NCO; q += blockDim.x) {
+    const int kc = q / NCO, co = q % NCO;
+    *reinterpret_cast<uint4*>(sB + (size_t)q * 16) =
+        (!LAST || co < 8) ? reinterpret_cast<const uint4*>(a.wt)[co * B_CHUNKS + kc] : make_uint4(0u, 0u, 0u, 0u);
   }
-  if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias != nullptr ? a.bias[threadIdx.x] : 0.0f;
+  if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias != nullptr && (!LAST || threadIdx.x < 3) ? a.bias[threadIdx.x] : 0.0f;
   if (threadIdx.x == 0) {
     for (int j = 0; j < CR_NT; ++j) {
       mbar_init(full(j), 1);
@@ -403,7 +410,9 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_co
     const uint32_t b0 = saddr(sB), rows0 = saddr(rows);
     uint64_t db[18];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) db[q] = smem_desc(b0 + (uint32_t)(((q >> 1) * 4 + (q & 1) * 2) * 512), 512, 128);
+    for (int q = 0; q < 18; ++q)
+      db[q] = smem_desc(b0 + (uint32_t)(((q >> 1) * 4 + (q & 1) * 2) * NCO * 16), NCO * 16, 128);
+    constexpr uint32_t idesc = tc::idesc_bf16(128, NCO);
     uint32_t fullpar = 0;
     Pos cur = start(t0);
     int j = 0, issued = 0;
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_co
 #pragma unroll
         for (int q = 0; q < 6; ++q) {  // (dx, channel half) of tap (dy, dx)
           const int dx = q >> 1, kk = q & 1;
-          mma_f16(d, da0 + (uint64_t)((dx * 64 + kk * 32) >> 4), db[dy * 6 + q], (dy | q) ? 1u : 0u);
+          tc::mma_f16(d, da0 + (uint64_t)((dx * 64 + kk * 32) >> 4), db[dy * 6 + q], idesc, (dy | q) ? 1u : 0u);
         }
       }
       mma_commit(empty(j));
@@ -439,6 +448,12 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_co
     Pos cur = start(t0);
     for (int i = 0; i < t1 - t0; ++i, advance(cur)) {
       const int acc = i & 1;
+      // LAST: the residual does not depend on the accumulator: its loads overlap the MMAs
+      float res[3] = {0.0f, 0.0f, 0.0f};
+      const size_t hw = (size_t)a.H * a.W, off = (size_t)cur.y * a.W + cur.x0 + px;
+      if (LAST && h16 == 0 && cur.x0 + px < a.W)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = a.resid[((size_t)cur.b * 3 + c) * hw + off];
       if (!mbar_wait(accf(acc), (i >> 1) & 1, a.spin)) { failed = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint32_t r[16];
@@ -452,6 +467,13 @@ __global__ void __launch_bounds__(NTHR, 1) conv32_ring_tc_kernel(const __grid_co
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(acce(acc));
       const int x = cur.x0 + px;
+      if (LAST) {  // channels 0-2 of the first half: u0 = f + conv + bias, planar FP32
+        if (h16 == 0 && x < a.W)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            a.out_planar[((size_t)cur.b * 3 + c) * hw + off] = (__uint_as_float(r[c]) + sbias[c]) + res[c];
+        continue;
+      }
       if (x < a.W) {
         const size_t pix = ((size_t)cur.b * a.H + cur.y) * a.W + x;
         uint4 mk[2];
@@ -794,8 +816,11 @@ bool make_nhwc8_row_map(CUtensorMap* map, const void* act, int B, int H, int W, 
 }
 
 cudaError_t conv32_tc_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cnn_tc::SMEM_RING);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(cnn_tc::conv32_ring_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           cnn_tc::SMEM_RING);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(cnn_tc::conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cnn_tc::SMEM_PIPE_IN8);
   if (e != cudaSuccess) return e;
@@ -864,11 +889,37 @@ cudaError_t launch_conv_tc(bool in8, int B, int H, int W, const void* in, const 
   if (in8)
     conv3_tc_kernel<<<grid, NTHR, SMEM_PIPE_IN8, st>>>(map, map2, a);
   else
-    conv32_ring_tc_kernel<<<grid, NTHR, SMEM_RING, st>>>(map, a);
+    conv32_ring_tc_kernel<false><<<grid, NTHR, SMEM_RING, st>>>(map, a);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// u0 = f + conv3x3_{32->3}(in) + bias: in NHWC BF16 B x H x W x 32, wt [8][288] BF16 (rows 3-7
+// zero), f and u0 planar FP32 B x 3 x H x W.
+cudaError_t launch_conv_last_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, const float* f,
+                                float* u0, int* error, cudaStream_t st) {
+  using namespace cnn_tc;
+  if (encode_fn() == nullptr) return cudaErrorNotSupported;
+  CUtensorMap map;
+  if (!make_nhwc32_map_sw64(&map, in, B, H, W, HALO_W, 32)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = B * H * ((W + TILE - 1) / TILE);
+  const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+  TcArgs a{};
+  a.B = B; a.H = H; a.W = W;
+  a.wt = static_cast<const bf16*>(wt);
+  a.bias = bias;
+  a.out_planar = u0;
+  a.resid = f;
+  a.error = error;
+  const char* spin = getenv("ILS_TEST_TC_SPIN");   // test hook: tiny poll limit -> timeout path
+  a.spin = (spin != nullptr && spin[0] != 0) ? (uint32_t)atoi(spin) : kSpinLimit;
+  conv32_ring_tc_kernel<true><<<grid, NTHR, SMEM_RING, st>>>(map, a);
+  return cudaGetLastError();
+}
 
 // out = conv3x3_{32->32}(in) (+bias, ReLU | mask) on NHWC BF16 tensors of B x H x W x 32.
 cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, void* out,

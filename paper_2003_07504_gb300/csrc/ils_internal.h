@@ -236,6 +236,9 @@ cudaError_t launch_conv32_tc(int B, int H, int W, const void* in, const void* wt
                              const void* mask, int relu, int* error, cudaStream_t st);
 // 3->32 channel conv3x3 on tcgen05: in is NHWC BF16 rows of 8 channels (3 values, then zeros),
 // wt [32][32] BF16 with column tap * 3 + ci (k < 27)
+// u0 = f + conv3x3_{32->3}(in) + bias on tcgen05 (the warm-start network's last layer)
+cudaError_t launch_conv_last_tc(int B, int H, int W, const void* in, const void* wt, const float* bias, const float* f,
+                                float* u0, int* error, cudaStream_t st);
 cudaError_t launch_conv3_tc(int B, int H, int W, const void* in8, const void* wt, const float* bias, void* out,
                             const void* mask, int relu, int* error, cudaStream_t st);
 // weight and bias gradients of a conv3x3 with ci_n, co_n <= 32 on tcgen05, accumulated into
