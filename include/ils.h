@@ -352,12 +352,13 @@ ils_status ils_cnn_set_adam(ils_cnn* net, const float* m, const float* v, long l
 /* u0 = f + net(f) (f, u0 device, non-overlapping).  Keeps the activations for backward. */
 ils_status ils_cnn_forward(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);
 
-/* u0 = f + net(f) for inference (no activations kept; the last forward's activations are
- * overwritten).  With the tcgen05 kernels in use it runs as two fused kernels, layers 1-3
- * and 4-6, whose hidden activations stay on chip except the one 32-channel map between
- * them; otherwise it is ils_cnn_forward.  Same numerics as ils_cnn_forward (BF16 inputs,
- * weights and hidden activations, FP32 accumulation); results agree up to FP32
- * accumulation order.  f, u0: device B x 3 x H x W FP32, non-overlapping. */
+/* u0 = f + net(f) for inference (the last forward's activations are overwritten).  It runs
+ * the layer-by-layer kernels of ils_cnn_forward (with tcgen05: 0.40 ms for a 1920 x 1080 RGB
+ * frame); with ILS_CNN_FUSED=1 in the environment and the tcgen05 kernels in use, two fused
+ * kernels instead, layers 1-3 and 4-6, whose hidden activations stay on chip except the one
+ * 32-channel map between them (0.50 ms).  Same numerics either way (BF16 inputs, weights and
+ * hidden activations, FP32 accumulation); results agree up to FP32 accumulation order.
+ * f, u0: device B x 3 x H x W FP32, non-overlapping. */
 ils_status ils_cnn_infer(ils_cnn* net, int B, int H, int W, const float* f, float* u0, void* stream);
 
 /* Accumulate dL/dparams given dL/du0 (device, B x 3 x H x W), using the activations of
@@ -365,10 +366,10 @@ ils_status ils_cnn_infer(ils_cnn* net, int B, int H, int W, const float* f, floa
 ils_status ils_cnn_backward(ils_cnn* net, int B, int H, int W, const float* f, const float* grad_u0, void* stream);
 ils_status ils_cnn_zero_grad(ils_cnn* net, void* stream);
 
-/* The four 32 -> 32 layers (and their input gradients) run on the tcgen05 tensor cores
- * (TMA loads, tensor-memory accumulators) when the driver offers tensor-map encoding,
- * else on the mma.sync kernels; ILS_CNN_TC=0 in the environment at creation forces the
- * latter.  Returns 1 when the tcgen05 kernels are in use. */
+/* Every layer's forward, input gradient and weight gradient runs on the tcgen05 tensor cores
+ * (TMA loads, tensor-memory accumulators) when the driver offers tensor-map encoding, else on
+ * the mma.sync kernels; ILS_CNN_TC=0 in the environment at creation forces the latter.
+ * Returns 1 when the tcgen05 kernels are in use. */
 int ils_cnn_uses_tcgen05(const ils_cnn* net);
 
 /* Waits for the device; returns ILS_ERR_TIMEOUT (and clears it) if a tensor-core kernel's

@@ -242,10 +242,11 @@ def test_tcgen05_bounded_wait_reports_timeout(ws, monkeypatch):
 
 
 @pytest.mark.parametrize("B,H,W", [(1, 12, 122), (1, 25, 250), (2, 40, 300), (1, 13, 5), (1, 1, 130)])
-def test_fused_inference_matches_oracle(ws, B, H, W):
+def test_fused_inference_matches_oracle(ws, monkeypatch, B, H, W):
     # two fused tcgen05 kernels (layers 1-3, 4-6): one tile, ragged tiles in x and y, several
     # images, a single narrow tile, a single row
     import torch
+    monkeypatch.setenv("ILS_CNN_FUSED", "1")
     p = random_params(ws, 11)
     f = synth.preset_image(H, W, 3 * B, "small", 7 * H + W).reshape(B, 3, H, W)
     net = ws.WarmStartNet(B * H * W, p)
@@ -257,11 +258,12 @@ def test_fused_inference_matches_oracle(ws, B, H, W):
     net.close()
 
 
-def test_fused_inference_matches_layer_kernels_at_1080p(ws):
+def test_fused_inference_matches_layer_kernels_at_1080p(ws, monkeypatch):
     # full-size frame: fused inference against the layer-by-layer forward (same BF16 rounding
     # points, FP32 accumulation in another order) with the trained weights when present
     import os
     import torch
+    monkeypatch.setenv("ILS_CNN_FUSED", "1")
     H, W = 1080, 1920
     p = ws.load_params(ws.DEFAULT_WEIGHTS) if os.path.exists(ws.DEFAULT_WEIGHTS) else random_params(ws, 12)
     f = torch.from_numpy(synth.preset_image(H, W, 3, "hd", 31).reshape(1, 3, H, W)).cuda()
@@ -291,6 +293,7 @@ def test_fused_inference_matches_layer_kernels_at_1080p(ws):
 
 def test_fused_inference_bounded_wait_reports_timeout(ws, monkeypatch):
     import torch
+    monkeypatch.setenv("ILS_CNN_FUSED", "1")
     H, W = 30, 260
     p = random_params(ws, 13)
     f = torch.from_numpy(synth.preset_image(H, W, 3, "small", 2).reshape(1, 3, H, W)).cuda()
