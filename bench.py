@@ -620,7 +620,7 @@ def warm_leg(torch, dev, steps, flush):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
     out["network"] = {"ms": net_ms, "flop_per_px": CNN_FLOP_PER_PX, "tflops": tflops,
                       "frac_of_bf16_peak": tflops / float(peaks["bf16_tflops"]),
-                      "kernels": "two fused tcgen05 kernels (layers 1-3, 4-6)" if net.uses_tcgen05 else "mma.sync"}
+                      "kernels": "six tcgen05 convolution launches (layer by layer; ILS_CNN_FUSED=1: two fused kernels)" if net.uses_tcgen05 else "mma.sync"}
     with ils.Plan(H, W, C, LAM, P, EPS, N_ITERS) as p4:
         errs = [rms(p4.smooth(fk), k) for k, fk in enumerate(frames)]
         u4 = torch.empty_like(f)
