@@ -462,8 +462,16 @@ __global__ void mse_kernel(const float* u0, const float* target, float* grad, si
     grad[i] = 2.0f * d * scale;
     s += d * d;
   }
+  // one atomic per block (one per warp on the single loss word serialized ~30 k atomics)
+  __shared__ float ws[32];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * scale);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) atomicAdd(loss, t * scale);
+  }
 }
 
 }  // namespace cnn
@@ -820,7 +828,7 @@ ils_status ils_cnn_forward(ils_cnn* n, int B, int H, int W, const float* f, floa
   a.B = B; a.H = H; a.W = W;
   // layer 0: planar 3 -> 32, ReLU (tcgen05: f packed into 8-channel NHWC rows first)
   if (n->tc) {
-    planar3_to_nhwc8(f, B, H, W, n->pkf, st);
+    planar3_to_nhwc8(f, B, H, W, n->pkf, st, n->pk32[0]);  // pk32[0]: layer 0's weight gradient
     cudaError_t e = ils::launch_conv3_tc(B, H, W, n->pkf, n->wf[0], n->b[0], n->act[0], nullptr, 1, n->err, st);
     if (e != cudaSuccess) return cnn_fail(e, "tensor-core conv launch");
   } else {
@@ -915,8 +923,7 @@ ils_status ils_cnn_backward(ils_cnn* n, int B, int H, int W, const float* f, con
       // into NHWC rows of 32 channels (channels 3-31 zero), rounded to BF16 as the mma.sync path
       // stages it; dL/du0 also into rows of 8 for layer 5's input gradient below
       cudaError_t e;
-      if (l == 0) {
-        planar3_to_nhwc8(f, B, H, W, nullptr, st, n->pk32[0]);
+      if (l == 0) {  // f as the forward packed it (the activations are the forward's too)
         e = ils::launch_wgrad_tc(B, H, W, n->pk32[0], 32, 3, dy_nhwc, 32, 32, n->gw[l], kpad(l), n->gb[l], n->err,
                                  st);
       } else if (dy_planar != nullptr) {
