@@ -438,8 +438,9 @@ std::vector<float2> row_twiddles(int W) {
   const int M = W / 2;
   std::vector<float2> v = unit_roots(W);
   v.resize(row_twiddle_count(W), make_float2(0.0f, 0.0f));
+  const int S = four_step_lanes(M);
   for (int t = 0; t < M; ++t) {
-    const int k2 = t / 32, n1 = t % 32;
+    const int k2 = t / S, n1 = t % S;
     v[(size_t)W + t] = v[(size_t)(2 * n1 * k2) % W];  // exp(-2 pi i n1 k2 / M)
   }
   return v;

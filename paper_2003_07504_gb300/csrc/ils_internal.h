@@ -159,12 +159,16 @@ struct Geometry {
   int fixed_col;     // index of a compile-time column plan for H, or -1
 };
 
+// Lanes that share one packed row of M complex points in the warp-per-row transforms: 32
+// (one warp, M = 32 L), or 64 (a warp pair, M = 64 L) for rows longer than 1024 points.
+__host__ __device__ constexpr int four_step_lanes(int M) { return M > 1024 ? 64 : 32; }
+
 // Device tables for one (H, W, lambda, c).
 struct Tables {
   // exp(-2 pi i t / W) for t < W, then the W/2 four-step twiddles of the warp-per-row
-  // transforms, k2-major so that a warp's 32 lanes read 32 consecutive entries:
-  // twW[W + 32 k2 + n1] = exp(-2 pi i n1 k2 / (W/2)) (row_twiddles), then stage tables
-  // (row_twiddle_count)
+  // transforms, k2-major so that the lanes of a row read consecutive entries:
+  // twW[W + S k2 + n1] = exp(-2 pi i n1 k2 / (W/2)) with S = four_step_lanes(W/2)
+  // (row_twiddles), then stage tables (row_twiddle_count)
   float2* twW;
   float2* twH;   // exp(-2 pi i t / H) for t < H, then stage tables (col_twiddle_count)
   float* ax;     // M+1 entries: lambda c (1 - cos(2 pi k / W)),  k = 0..M
@@ -276,6 +280,8 @@ cudaError_t build_row_twiddles(int W, float2* twW, cudaStream_t st);
 
 // Warp-per-row kernels (ils_rows_warp.cu).
 int warp_row_variants(int M, int* idx, int max);
+// whether warp-per-row entry idx has an adjoint row kernel (the warp-pair entries have none)
+bool warp_row_has_adjoint(int idx);
 cudaError_t warp_set_attributes();
 cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp, const float* f,
                              const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,

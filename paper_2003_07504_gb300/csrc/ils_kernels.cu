@@ -430,7 +430,7 @@ bool pick_geometry(int H, int W, Geometry* g) {
     if (pick < 0 || pick >= nw) pick = 0;
   }
   g->warp_row = nw > 0 ? wv[pick] : -1;
-  g->warp_adj = g->warp_row;
+  g->warp_adj = g->warp_row >= 0 && warp_row_has_adjoint(g->warp_row) ? g->warp_row : -1;
   g->fixed_row = no_fixed ? -1 : fixed_row_index(M);
   // 256-wide rows (M = 128): the block-per-strip plan by default.  A warp-per-row transform of
   // 4 points per lane runs its 32-point stage on 4 of the 32 lanes; measured on a 48 x 256 x 256

@@ -116,7 +116,7 @@ __global__ void noalloc_tables_kernel(int H, int W, double lc, float2* twW, floa
       twW[i] = make_float2((float)c, (float)s);
     }
     if (i < M) {  // the four-step entries (layout of Tables::twW): the same values as twW[2 n1 k2 mod W]
-      const int k2 = i / 32, n1 = i % 32;
+      const int S = four_step_lanes(M), k2 = i / S, n1 = i % S;
       sincospi(-2.0 * (double)((2 * n1 * k2) % W) / (double)W, &s, &c);
       twW[W + i] = make_float2((float)c, (float)s);
     }

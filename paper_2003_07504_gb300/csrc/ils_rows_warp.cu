@@ -1,4 +1,5 @@
-// Row passes with one warp per image row, for row lengths W = 64 L (M = W/2 = 32 L complex).
+// Row passes with one warp per image row, for row lengths W = 64 L (M = W/2 = 32 L complex),
+// and with a warp pair per row for W = 128 L (PairRow below).
 //
 // A warp transforms one packed complex row of M = 32 L points as a 32 x L four-step FFT:
 // lane n1 holds x[n1 + 32 n2] (n2 = 0..L-1, a coalesced row load), runs the L-point DFT
@@ -523,12 +524,301 @@ row_warp_adj_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
   if (out_live) WR::forward_row_to_global(v, spec_out + ch * plane + (size_t)(y0 + o) * M, buf, lane, tw);
 }
 
+// ---------------------------------------------------------------- two warps per row
+//
+// Rows of M = 64 L complex points (W = 128 L; W = 3840: L = 30) are transformed by a warp
+// pair, so that a lane holds L values, as in the one-warp transform of a row half as long.
+// Lane g = lane + 32 h of the pair (h: the pair's warp) holds x[g + 64 n2], n2 < L, runs the
+// L-point DFT over its registers and multiplies by w_M^{g k2}; the pair transposes through
+// the row's buffer (line stride 65, conflict free); lane k2 < L of warp h then runs the
+// 32-point DFT Z_h of the stride-2 subsequence y[h + 2 b] of the 64 values of index k2, and
+// one radix-2 step joins the halves of the 64-point DFT: Y[k + 32 c] = Z_0[k] + (-1)^c
+// w_64^k Z_1[k], warp h forming c = h after the two warps swap their Z through the buffer.
+// X[k2 + L k1] lands in register k1 - 32 h of lane k2 of warp h.  The pair synchronizes with
+// its own named barrier (bar.sync 1 + pair, 64 threads), four times per transform.  The ids
+// are immediates (one switch case per pair of the CTA) so that a CTA reserves only NP + 1
+// hardware barriers; a register id would reserve all 16.
+#define ILS_PAIR_BAR(k) \
+  case k - 1:           \
+    if constexpr (NP >= k) asm volatile("bar.sync " #k ", 64;" ::: "memory"); \
+    break;
+template <int L, int NP>
+struct PairRow {
+  static constexpr int M = 64 * L;
+  static constexpr int STRIDE = 65;  // complex per transposed line
+  static constexpr int BUF = (L * STRIDE > M ? L * STRIDE : M);
+  static_assert(L <= 32 && L % 2 == 0, "one 32-point transform per lane; 16-byte row copies");
+  static_assert(2 * 32 * L <= BUF, "the Z exchange fits the row buffer");
+
+  static_assert(NP >= 1 && NP <= 15, "one named barrier per pair (ids 1..15)");
+  // the pair barrier of pair p < NP
+  __device__ __forceinline__ static void bar(int p) {
+    switch (p) {
+      ILS_PAIR_BAR(1) ILS_PAIR_BAR(2) ILS_PAIR_BAR(3) ILS_PAIR_BAR(4) ILS_PAIR_BAR(5)
+      ILS_PAIR_BAR(6) ILS_PAIR_BAR(7) ILS_PAIR_BAR(8) ILS_PAIR_BAR(9) ILS_PAIR_BAR(10)
+      ILS_PAIR_BAR(11) ILS_PAIR_BAR(12) ILS_PAIR_BAR(13) ILS_PAIR_BAR(14) ILS_PAIR_BAR(15)
+      default: break;
+    }
+  }
+
+  // v: lane g holds x[g + 64 n2]; out[k] (lane k2 < L of warp h): X[k2 + L (k + 32 h)].
+  // buf: the pair's row buffer, free on entry and on return.
+  template <bool INV>
+  __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[32], float2* buf, int g, int h, int lane,
+                                             int pr, const TwRef& tw) {
+    dft_reg<L, INV>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < L; ++k2) {
+      float2 w = tw.ft[64 * k2 + g];  // w_M^{g k2}
+      if (INV) w.y = -w.y;
+      v[k2] = cmul(v[k2], w);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < L; ++k2) buf[k2 * STRIDE + g] = v[k2];
+    bar(pr);
+    const bool act = lane < L;  // lane = k2
+    if (act) {
+#pragma unroll
+      for (int b = 0; b < 32; ++b) out[b] = buf[lane * STRIDE + h + 2 * b];
+      dft_reg<32, INV>(out);
+      if (h == 1) {
+        constexpr Roots<64> w64{};
+#pragma unroll
+        for (int k = 1; k < 32; ++k) out[k] = twiddle_const<64, INV>(out[k], k, w64);
+      }
+    }
+    bar(pr);  // every lane has read its line
+    if (act) {
+      float2* mine = buf + h * (32 * L);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) mine[k * L + lane] = out[k];
+    }
+    bar(pr);
+    if (act) {
+      const float2* other = buf + (1 - h) * (32 * L);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float2 z = other[k * L + lane];
+        out[k] = h == 0 ? cadd(out[k], z) : csub(z, out[k]);
+      }
+    }
+    bar(pr);  // the exchange is read: buf is free
+  }
+
+  // 16-byte asynchronous copy of the packed spectrum row X into buf (the caller waits).
+  __device__ __forceinline__ static void stage_row(const float2* __restrict__ X, float2* buf, int g) {
+#pragma unroll
+    for (int q = 0; q < L / 2; ++q) cp_async16(buf + 2 * (g + 64 * q), X + 2 * (g + 64 * q));
+  }
+
+  // Hermitian unpacking of the packed half spectrum for the inverse real transform (the
+  // formula of WarpRow::load_c2r), v[n2] = Z[g + 64 n2]; X global, or staged in buf (then the
+  // pair has read buf on return).
+  template <bool STAGED>
+  __device__ __forceinline__ static void load_c2r(const float2* __restrict__ X, float2 (&v)[L], const float2* buf,
+                                                  int g, int pr, const TwRef& tw) {
+    const float2* src = STAGED ? buf : X;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int k = g + 64 * n2;
+      if (k == 0) {
+        const float2 x = src[0];
+        v[n2] = c2(x.x + x.y, x.x - x.y);
+      } else {
+        const float2 a = src[k], b = cconj(src[M - k]);
+        const float2 s = cadd(a, b), d = csub(a, b);
+        const float2 t = cmul(cconj(tw.rt[k]), d);
+        v[n2] = c2(s.x - t.y, s.y + t.x);
+      }
+    }
+    if (STAGED) bar(pr);
+  }
+
+  // Inverse real transform of X into buf in natural order (pairs of pixels, unnormalized);
+  // the caller synchronizes before other warps read buf.
+  __device__ __forceinline__ static void inverse_row_to_buf(const float2* __restrict__ X, float2* buf, int g, int h,
+                                                            int lane, int pr, const TwRef& tw) {
+    float2 v[L];
+    load_c2r<false>(X, v, buf, g, pr, tw);
+    float2 out[32];
+    fft<true>(v, out, buf, g, h, lane, pr, tw);
+    if (lane < L) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) buf[lane + L * (k + 32 * h)] = out[k];
+    }
+  }
+
+  // Inverse real transform of X (global, or staged in buf) straight to the output through
+  // the epilogue (pair index rowoff + m of the output image).
+  template <int EPI, bool STAGED>
+  __device__ __forceinline__ static void inverse_row_to_global(const float2* __restrict__ X, float2* out,
+                                                               size_t rowoff, const Epilogue& epi, float2* buf, int g,
+                                                               int h, int lane, int pr, const TwRef& tw) {
+    float2 v[L];
+    load_c2r<STAGED>(X, v, buf, g, pr, tw);
+    float2 res[32];
+    fft<true>(v, res, buf, g, h, lane, pr, tw);
+    float dm = 0.0f;
+    if (lane < L) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        dm = fmaxf(dm, epi.template store<EPI>(out, rowoff + lane + L * (k + 32 * h), res[k]));
+    }
+    epi.template finish<EPI>(dm);
+  }
+
+  // Forward real transform of r (lane g holds the r-pairs m = g + 64 n2) to the packed half
+  // spectrum in dst; buf must be free for the pair (no other reader left).
+  __device__ __forceinline__ static void forward_row_to_global(float2 (&v)[L], float2* dst, float2* buf, int g, int h,
+                                                               int lane, int pr, const TwRef& tw) {
+    float2 out[32];
+    fft<false>(v, out, buf, g, h, lane, pr, tw);
+    if (lane < L) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) buf[lane + L * (k + 32 * h)] = out[k];
+    }
+    bar(pr);
+    // buf holds Z = FFT_M(r[2m] + i r[2m+1]): the packed half spectrum, pairs (k, M-k)
+#pragma unroll
+    for (int q = 0; q < (M / 2 + 1 + 63) / 64; ++q) {
+      const int k = g + 64 * q;
+      if (k > M / 2) continue;
+      if (k == 0) {
+        const float2 z = buf[0];
+        dst[0] = c2(z.x + z.y, z.x - z.y);
+      } else {
+        const float2 a = buf[k], b = buf[M - k];
+        const float2 fa = cscale(cadd(a, cconj(b)), 0.5f), fo = cscale(csub(a, cconj(b)), 0.5f);
+        dst[k] = cadd(fa, cmul(tw.rt[k], c2(fo.y, -fo.x)));
+        if (M - k != k) {
+          const float2 fb = cscale(cadd(b, cconj(a)), 0.5f), fq = cscale(csub(b, cconj(a)), 0.5f);
+          dst[M - k] = cadd(fb, cmul(tw.rt[M - k], c2(fq.y, -fq.x)));
+        }
+      }
+    }
+  }
+};
+
+// Fused row pass with a warp pair per strip row: CTA = ROWS + 2 pairs over rows y0-1 ..
+// y0+ROWS (periodic); pair p holds strip row p in buffer p.  FIRST: u^0 rows are copied from
+// u0 (or f); otherwise rebuilt by the inverse transform of spec_in.  Pair o+1 then forms r of
+// output row o with the per-pair stencil of row_warp_fwd_kernel (mu of the pair's three x
+// gradients and four y gradients; the x gradient left of a pair is the left lane's right
+// one, lane 0 evaluating its own) and forward-transforms it.
+template <int L, int ROWS, bool FIRST, int PEN, int MINB>
+__global__ void __launch_bounds__((ROWS + 2) * 64, MINB)
+row_pair_fwd_kernel(int H, const float2* __restrict__ twW, MuParams mp, const float* __restrict__ f,
+                    const float* __restrict__ u0, const float2* __restrict__ spec_in, float2* __restrict__ spec_out,
+                    float* __restrict__ u_ckpt) {
+  griddep_launch();
+  using PR = PairRow<L, ROWS + 2>;
+  constexpr int M = PR::M;
+  extern __shared__ float2 sm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, p = w >> 1, h = w & 1, g = lane + 32 * h;
+  const int strips = (H + ROWS - 1) / ROWS;
+  const int ch = blockIdx.x / strips;
+  const int y0 = (blockIdx.x - ch * strips) * ROWS;
+  const int nout = min(ROWS, H - y0);
+  const size_t plane = (size_t)H * M;
+  float2* buf = sm + p * PR::BUF;
+  auto U = [&](int row, int m) -> float2 { return sm[row * PR::BUF + m]; };
+  const int o = p - 1;  // output row of this pair
+  const bool out_live = o >= 0 && o < nout;
+  const bool f_is_u = FIRST && (u0 == nullptr || u0 == f);
+  const size_t orow = ch * plane + (size_t)(y0 + max(o, 0)) * M;
+  float2* tws = sm + (ROWS + 2) * PR::BUF;
+  const TwRef tw{tws, tws + M};
+  stage_row_twiddles<M>(tws, twW);  // constant tables: before the wait on the previous grid
+  griddep_wait();
+  const int yy = wrap_row(y0 - 1 + p, H);
+  if (FIRST && p < nout + 2) {
+    const float2* src = reinterpret_cast<const float2*>(u0 != nullptr ? u0 : f) + ch * plane + (size_t)yy * M;
+    if ((reinterpret_cast<size_t>(src) & 15) == 0) {
+      PR::stage_row(src, buf, g);
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) buf[g + 64 * n2] = src[g + 64 * n2];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (!FIRST && p < nout + 2) PR::inverse_row_to_buf(spec_in + ch * plane + (size_t)yy * M, buf, g, h, lane, p, tw);
+  __syncthreads();
+  float2 v[L];
+  if (mp.half_lambda == 0.0f) {  // lambda = 0 (or a plain row FFT): r = f
+    if (out_live) {
+      const float2* fr = reinterpret_cast<const float2*>(f) + orow;
+#pragma unroll
+      for (int n2 = 0; n2 < L; ++n2) {
+        const int m = g + 64 * n2;
+        v[n2] = fr[m];
+        if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[orow + m] = U(p, m);
+      }
+      PR::bar(p);  // both warps have read their row before the transform writes buf
+      PR::forward_row_to_global(v, spec_out + orow, buf, g, h, lane, p, tw);
+    }
+    return;
+  }
+  if (out_live) {
+    const float2* fr = reinterpret_cast<const float2*>(f) + orow;
+#pragma unroll
+    for (int n2 = 0; n2 < L; ++n2) {
+      const int m = g + 64 * n2;
+      const float2 c = U(p, m);
+      const float ur = U(p, m == M - 1 ? 0 : m + 1).x;
+      const float2 up = U(p - 1, m);
+      const float2 dn = U(p + 1, m);
+      const float2 fv = f_is_u ? c : fr[m];
+      const float mx_c = mu_pen<PEN>(c.y - c.x, mp);
+      const float mx_r = mu_pen<PEN>(ur - c.y, mp);
+      float mx_l = __shfl_up_sync(kFull, mx_r, 1);
+      if (lane == 0) mx_l = mu_pen<PEN>(c.x - U(p, m == 0 ? M - 1 : m - 1).y, mp);
+      const float my0u = mu_pen<PEN>(c.x - up.x, mp);
+      const float my0d = mu_pen<PEN>(dn.x - c.x, mp);
+      const float my1u = mu_pen<PEN>(c.y - up.y, mp);
+      const float my1d = mu_pen<PEN>(dn.y - c.y, mp);
+      v[n2] = c2(fmaf(mp.half_lambda, (mx_l - mx_c) + (my0u - my0d), fv.x),
+                 fmaf(mp.half_lambda, (mx_c - mx_r) + (my1u - my1d), fv.y));
+      if (u_ckpt != nullptr) reinterpret_cast<float2*>(u_ckpt)[orow + m] = c;
+    }
+  }
+  __syncthreads();  // every pair has read the strip rows: buffer p becomes pair p's scratch
+  if (out_live) PR::forward_row_to_global(v, spec_out + orow, buf, g, h, lane, p, tw);
+}
+
+// Final inverse row pass with a warp pair per row, ROWS rows per CTA; EPI: the epilogue mode.
+template <int L, int ROWS, int EPI, bool SPEC>
+__global__ void __launch_bounds__(ROWS * 64)
+row_pair_inv_kernel(int H, const float2* __restrict__ twW, const float2* __restrict__ spec, float* __restrict__ u,
+                    Epilogue epi) {
+  griddep_launch();
+  using PR = PairRow<L, ROWS>;
+  constexpr int M = PR::M;
+  extern __shared__ float2 sm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, p = w >> 1, h = w & 1, g = lane + 32 * h;
+  const int strips = (H + ROWS - 1) / ROWS;
+  const int ch = blockIdx.x / strips;
+  const int y = (blockIdx.x - ch * strips) * ROWS + p;
+  const size_t off = ch * (size_t)H * M + (size_t)min(y, H - 1) * M;
+  float2* tws = sm + ROWS * PR::BUF;
+  stage_row_twiddles<M>(tws, twW);
+  griddep_wait();
+  if (SPEC && y < H) PR::stage_row(spec + off, sm + p * PR::BUF, g);
+  cp_async_wait_all();
+  __syncthreads();
+  if (y >= H) return;  // pair-uniform; no CTA barrier below
+  PR::template inverse_row_to_global<EPI, SPEC>(spec + off, reinterpret_cast<float2*>(u), off, epi,
+                                                sm + p * PR::BUF, g, h, lane, p, TwRef{tws, tws + M});
+}
+
 using FwdFn = void (*)(int, const float2*, MuParams, const float*, const float*, const float2*, float2*, float*);
 using AdjFn = void (*)(int, const float2*, MuParams, const float2*, const float*, float*, int, float*, int, float2*);
 using InvFn = void (*)(int, const float2*, const float2*, float*, Epilogue);
 
 struct WarpRowEntry {
   int M, rows_fwd, rows_inv, buf, stage;
+  int P;                     // warps per row: 1 (WarpRow) or 2 (PairRow)
+  int rows_first;            // output rows per CTA of the first row pass (no inverse transforms)
   FwdFn first[kPenalties], later[kPenalties];  // per penalty (MuParams::pen)
   InvFn inv[kEpilogues];     // per epilogue mode
   AdjFn adj[2];              // per penalty with an adjoint (Eq. 7, Welsch)
@@ -547,6 +837,8 @@ constexpr WarpRowEntry warp_entry() {
                       RI,
                       WarpRow<L>::BUF,
                       STAGE ? RF * 32 * L : 0,
+                      1,
+                      RF,
                       {row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 0, MINB, SPEC>,
                        row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 1, MINB, SPEC>,
                        row_warp_fwd_kernel<L, RF, true, STAGE, SHARED, 2, MINB, SPEC>},
@@ -557,6 +849,29 @@ constexpr WarpRowEntry warp_entry() {
                        row_warp_inv_kernel<L, RI, 2, SPEC_I>, row_warp_inv_kernel<L, RI, 3, SPEC_I>,
                        row_warp_inv_kernel<L, RI, 4, SPEC_I>, row_warp_inv_kernel<L, RI, 5, SPEC_I>},
                       {row_warp_adj_kernel<L, RF, 0, MINB>, row_warp_adj_kernel<L, RF, 1, MINB>}};
+}
+
+// Warp-pair rows (M = 64 L): RF output rows per CTA of the later row passes ((RF + 2) pairs,
+// MINB CTAs per SM), RF1 (MINB1) in the first row pass, whose strips only copy their rows (no
+// repeated inverse transforms of halo rows, so short strips at more CTAs per SM win there), RI
+// rows per final-inverse CTA (SPEC_I: staged spectrum rows); no adjoint kernel.
+template <int L, int RF1, int MINB1, int RF, int MINB, int RI, bool SPEC_I>
+constexpr WarpRowEntry pair_entry() {
+  return WarpRowEntry{64 * L,
+                      RF,
+                      RI,
+                      PairRow<L, 1>::BUF,
+                      0,
+                      2,
+                      RF1,
+                      {row_pair_fwd_kernel<L, RF1, true, 0, MINB1>, row_pair_fwd_kernel<L, RF1, true, 1, MINB1>,
+                       row_pair_fwd_kernel<L, RF1, true, 2, MINB1>},
+                      {row_pair_fwd_kernel<L, RF, false, 0, MINB>, row_pair_fwd_kernel<L, RF, false, 1, MINB>,
+                       row_pair_fwd_kernel<L, RF, false, 2, MINB>},
+                      {row_pair_inv_kernel<L, RI, 0, SPEC_I>, row_pair_inv_kernel<L, RI, 1, SPEC_I>,
+                       row_pair_inv_kernel<L, RI, 2, SPEC_I>, row_pair_inv_kernel<L, RI, 3, SPEC_I>,
+                       row_pair_inv_kernel<L, RI, 4, SPEC_I>, row_pair_inv_kernel<L, RI, 5, SPEC_I>},
+                      {nullptr, nullptr}};
 }
 
 // The first entry of a length is its default; the others are autotune alternatives.  Every
@@ -576,6 +891,7 @@ const WarpRowEntry kWarpRows[] = {
     warp_entry<20, 6, 8, false, false>(),    // W = 1280, per-pair stencil
     warp_entry<32, 6, 8, false, false>(),    // W = 2048, per-pair stencil
     warp_entry<4, 14, 16, true, true>(),     // W = 256, 16-warp CTAs, one per SM (89 registers)
+    pair_entry<30, 3, 2, 6, 1, 4, true>(),   // W = 3840: first pass 10-warp CTAs two per SM, later 16-warp
 };
 
 }  // namespace
@@ -587,19 +903,22 @@ int warp_row_variants(int M, int* idx, int max) {
   return n;
 }
 
+bool warp_row_has_adjoint(int idx) { return kWarpRows[idx].adj[0] != nullptr; }
+
 cudaError_t warp_set_attributes() {
   cudaError_t e;
   for (const WarpRowEntry& r : kWarpRows) {
     const int sf = ((r.rows_fwd + 2) * r.buf + r.stage + 2 * r.M) * (int)sizeof(float2);
+    const int s1 = ((r.rows_first + 2) * r.buf + r.stage + 2 * r.M) * (int)sizeof(float2);
     const int si = (r.rows_inv * r.buf + 2 * r.M) * (int)sizeof(float2);
     for (int pen = 0; pen < kPenalties; ++pen) {
-      if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
+      if ((e = cudaFuncSetAttribute(r.first[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, s1))) return e;
       if ((e = cudaFuncSetAttribute(r.later[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sf))) return e;
     }
     for (int m = 0; m < kEpilogues; ++m)
       if ((e = cudaFuncSetAttribute(r.inv[m], cudaFuncAttributeMaxDynamicSharedMemorySize, si))) return e;
     const int sa = ((r.rows_fwd + 2) * r.buf + 2 * r.M) * (int)sizeof(float2);
-    for (int pen = 0; pen < 2; ++pen)
+    for (int pen = 0; pen < 2 && r.adj[0] != nullptr; ++pen)
       if ((e = cudaFuncSetAttribute(r.adj[pen], cudaFuncAttributeMaxDynamicSharedMemorySize, sa))) return e;
   }
   return cudaSuccess;
@@ -609,18 +928,20 @@ cudaError_t warp_row_forward(int idx, const ImageDesc& d, const Tables& t, const
                              const float* u0, const float2* spec_in, float2* spec_out, float* u_ckpt,
                              cudaStream_t stream) {
   const WarpRowEntry& r = kWarpRows[idx];
-  const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
-  const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + r.stage + 2 * r.M) * sizeof(float2);
+  const int rows = spec_in == nullptr ? r.rows_first : r.rows_fwd;
+  const int blocks = (d.H + rows - 1) / rows * d.C;
+  const size_t smem = ((size_t)(rows + 2) * r.buf + r.stage + 2 * r.M) * sizeof(float2);
   const int pen = mp.pen;
   FwdFn fn = spec_in == nullptr ? r.first[pen] : r.later[pen];
-  return launch_k(d.pdl, fn, blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out, u_ckpt);
+  return launch_k(d.pdl, fn, blocks, (rows + 2) * 32 * r.P, smem, stream, d.H, t.twW, mp, f, u0, spec_in, spec_out,
+                  u_ckpt);
 }
 
 cudaError_t warp_row_adjoint(int idx, const ImageDesc& d, const Tables& t, const MuParams& mp,
                              const float2* spec_in, const float* u_n, float* fbar, bool fbar_first, float* gu0,
                              bool last, float2* spec_out, cudaStream_t stream) {
   const WarpRowEntry& r = kWarpRows[idx];
-  if (mp.pen != 0 && mp.pen != 1) return cudaErrorInvalidValue;
+  if ((mp.pen != 0 && mp.pen != 1) || r.adj[0] == nullptr) return cudaErrorInvalidValue;
   const int blocks = (d.H + r.rows_fwd - 1) / r.rows_fwd * d.C;
   const size_t smem = ((size_t)(r.rows_fwd + 2) * r.buf + 2 * r.M) * sizeof(float2);
   return launch_k(d.pdl, r.adj[mp.pen], blocks, (r.rows_fwd + 2) * 32, smem, stream, d.H, t.twW, mp, spec_in, u_n,
@@ -632,7 +953,7 @@ cudaError_t warp_row_inverse(int idx, const ImageDesc& d, const Tables& t, const
   const WarpRowEntry& r = kWarpRows[idx];
   const int blocks = (d.H + r.rows_inv - 1) / r.rows_inv * d.C;
   const size_t smem = ((size_t)r.rows_inv * r.buf + 2 * r.M) * sizeof(float2);
-  return launch_k(d.pdl, r.inv[epi.mode], blocks, r.rows_inv * 32, smem, stream, d.H, t.twW, spec, u, epi);
+  return launch_k(d.pdl, r.inv[epi.mode], blocks, r.rows_inv * 32 * r.P, smem, stream, d.H, t.twW, spec, u, epi);
 }
 
 }  // namespace ils

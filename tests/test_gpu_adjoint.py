@@ -53,6 +53,8 @@ def gpu_grad(ils, f, w, lam=1.0, p=0.8, N=4, u0=None, separate=False):
     # warp-per-row adjoint kernels: L = 8, 10, 20, 30, 32 (ragged last strip: H not a multiple of 6)
     (20, 512, 1, 1.0, 0.8, 3), (15, 640, 2, 1.0, 0.8, 2), (16, 1280, 1, 2.0, 0.8, 2), (25, 1920, 1, 1.0, 0.8, 2),
     (9, 2048, 1, 1.0, 1.0, 2),
+    # 3840-wide rows: warp-pair forward kernels, generic adjoint row kernel
+    (9, 3840, 1, 1.0, 0.8, 2),
 ])
 def test_adjoint_matches_fp64_reverse_mode(ils, H, W, C, lam, p, N):
     f = synth.preset_image(H, W, C, "small", H + W + C)

@@ -294,10 +294,12 @@ def test_column_plan_variants_agree(ils, monkeypatch, H, W):
             assert_parity(frames[0][1].cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("H,W", [(12, 1920), (40, 1920), (10, 1280), (15, 640), (6, 3840), (16, 512), (20, 256)])
+@pytest.mark.parametrize("H,W", [(12, 1920), (40, 1920), (10, 1280), (15, 640), (6, 3840), (20, 3840), (16, 512),
+                                 (20, 256)])
 def test_row_plan_variants_agree(ils, monkeypatch, H, W):
-    # every warp-per-row and fixed-plan row variant of the length against the oracle (40 x 1920:
-    # seven 6-row strips, the last one ragged)
+    # every warp-per-row (warp-pair at W = 3840) and fixed-plan row variant of the length
+    # against the oracle (40 x 1920: seven 6-row strips, the last one ragged; 20 x 3840: 3-row
+    # strips in the first row pass and 6-row strips in the later ones, each with a 2-row tail)
     f = image(H, W, 2, seed=W + H, preset="hd")
     want = O.ils_smooth(f.astype(np.float64), 1.0, 0.8, 1e-4, 4)
     for impl in [f"warp{k}" for k in range(8)] + [f"fixed{k}" for k in range(3)]:
@@ -313,7 +315,7 @@ def test_row_plan_variants_agree(ils, monkeypatch, H, W):
     (60, 80, 3, 30.0, 5 / 255, 10, None),    # generic row kernels (M = 40)
     (45, 640, 1, 20.0, 10 / 255, 4, None),   # warp L = 10
     (40, 1920, 1, 30.0, 10 / 255, 15, None),  # warp L = 30; texture-smoothing iteration count
-    (16, 3840, 1, 20.0, 10 / 255, 3, None),  # fixed-plan 1920-point rows
+    (16, 3840, 1, 20.0, 10 / 255, 3, None),  # warp-pair 1920-point rows
     (27, 250, 1, 5.0, 0.1, 4, None),         # odd column length, generic rows
     (1080, 40, 1, 20.0, 10 / 255, 2, None),  # 1080-point column plan
 ])
@@ -525,7 +527,8 @@ def test_tonemap_matches_oracle(ils, H, W):
     (256, 256, 1, 0.25, 4, None),     # fixed 128-point rows; the paper's Fig. 11(c) setting
     (64, 256, 1, 0.25, 4, "warp0"),   # warp kernels, L = 4
     (40, 1920, 3, 0.25, 4, None),     # warp L = 30
-    (16, 3840, 1, 0.1, 3, None),      # fixed 1920-point rows
+    (16, 3840, 1, 0.1, 3, None),      # warp-pair 1920-point rows
+    (16, 3840, 1, 0.1, 3, "fixed"),   # fixed 1920-point rows
     (60, 80, 2, 0.25, 6, None),       # generic rows
     (1080, 40, 1, 0.25, 2, None),     # 1080-point column plan
 ])

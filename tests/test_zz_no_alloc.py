@@ -5,7 +5,7 @@ device synchronization, a plugin whose host owns all device memory) get the
 same smoothing with the workspace in the library's fixed static device array.
 Checked through the C ABI against the plan-based ils_smooth, within the parity
 tolerance, on two calls in a row (the second call reuses the array the first
-one left behind), against the FP64 oracle on a small RGB image, and for the
+one left behind), against the FP64 oracle on a small RGB image and a 3840-wide strip, and for the
 property that defines it: a call leaves the device's free memory unchanged.
 This file is collected last on purpose.
 """
@@ -54,9 +54,10 @@ def test_noalloc_matches_plan_path_on_two_calls(env):
         assert mx <= MAX_ABS_TOL and rms <= RMS_TOL, (C, H, W, mx, rms)
 
 
-def test_noalloc_matches_oracle(env):
+@pytest.mark.parametrize("C,H,W", [(3, 240, 320), (1, 16, 3840)])   # second: warp-pair rows
+def test_noalloc_matches_oracle(env, C, H, W):
     torch, _lib, ils = env
-    f = synth.preset_image(240, 320, 3, "hd", 43)
+    f = synth.preset_image(H, W, C, "hd", 43)
     fd = torch.from_numpy(f).cuda()
     u = torch.empty_like(fd)
     assert _noalloc(torch, _lib, fd, u) == 0
