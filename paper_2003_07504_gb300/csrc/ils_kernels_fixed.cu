@@ -542,14 +542,17 @@ const RowEntry kRows[] = {
 // 640x480, 1280x720, 1920x1080, 2048x1536 and 3840x2160 RGB.  One default per length, whatever
 // the channel count, so that a channel's result does not depend on the other channels of
 // the call (at 1080 rows: 36 x 30 with 8 columns per CTA, 1920 x 1080 RGB 265 us per frame
-// against 270 for 12 x 10 x 9 and 272-276 for 4 columns per CTA; gray 178 against 173 / 176).
+// against 270 for 12 x 10 x 9 and 272-276 for 4 columns per CTA; gray 178 against 173 / 176;
+// at 2160 rows: 45 x 48 with 8 columns per CTA, one CTA per SM at 168 registers, 3840 x 2160
+// RGB column pass 106 us per launch and 1078 us per N = 4 frame against 112 / 1156 us with 4
+// columns at two CTAs per SM and 139 / 1219 us with 6 columns at one).
 const ColEntry kCols[] = {
     col_entry<FixedPlan<256, 16, 16>, 16>(),
     col_entry<FixedPlan<480, 8, 6, 10>, 4, 2>(),
     col_entry<FixedPlan<720, 8, 9, 10>, 4, 2>(),
     col_entry<FixedPlan<1080, 36, 30>, 8, 2>(),
     col_entry<FixedPlan<1536, 32, 48>, 4, 2>(),
-    col_entry<FixedPlan<2160, 45, 48>, 4, 2>(),
+    col_entry<FixedPlan<2160, 45, 48>, 8>(),
     col_entry<FixedPlan<512, 16, 32>, 4, 3>(),
     // alternatives for the autotuner
     col_entry<FixedPlan<1080, 12, 10, 9>, 4, 2>(),
@@ -562,6 +565,10 @@ const ColEntry kCols[] = {
     col_entry<FixedPlan<1536, 16, 12, 8>, 4>(),
     col_entry<FixedPlan<2160, 12, 12, 15>, 4>(),
     col_entry<FixedPlan<512, 8, 8, 8>, 4, 2>(),
+    col_entry<FixedPlan<2160, 45, 48>, 4, 2>(),
+    col_entry<FixedPlan<1536, 32, 48>, 8>(),
+    col_entry<FixedPlan<720, 24, 30>, 8, 2>(),
+    col_entry<FixedPlan<480, 20, 24>, 8, 2>(),
 };
 
 }  // namespace
