@@ -535,7 +535,7 @@ row_warp_adj_kernel(int H, const float2* __restrict__ twW, MuParams mp, const fl
 // one radix-2 step joins the halves of the 64-point DFT: Y[k + 32 c] = Z_0[k] + (-1)^c
 // w_64^k Z_1[k], warp h forming c = h after the two warps swap their Z through the buffer.
 // X[k2 + L k1] lands in register k1 - 32 h of lane k2 of warp h.  The pair synchronizes with
-// its own named barrier (bar.sync 1 + pair, 64 threads), four times per transform.  The ids
+// its own named barrier (bar.sync 1 + pair, 64 threads), three times per transform.  The ids
 // are immediates (one switch case per pair of the CTA) so that a CTA reserves only NP + 1
 // hardware barriers; a register id would reserve all 16.
 #define ILS_PAIR_BAR(k) \
@@ -562,7 +562,8 @@ struct PairRow {
   }
 
   // v: lane g holds x[g + 64 n2]; out[k] (lane k2 < L of warp h): X[k2 + L (k + 32 h)].
-  // buf: the pair's row buffer, free on entry and on return.
+  // buf: the pair's row buffer, free on entry; on return lane k2 of warp h may write the slots
+  // k2 + L (k + 32 h) (its outputs' natural-order slots), the rest only after a pair barrier.
   template <bool INV>
   __device__ __forceinline__ static void fft(float2 (&v)[L], float2 (&out)[32], float2* buf, int g, int h, int lane,
                                              int pr, const TwRef& tw) {
@@ -588,21 +589,23 @@ struct PairRow {
       }
     }
     bar(pr);  // every lane has read its line
+    // Z_h goes to the other warp's output region (natural-order slots k2 + L (k + 32 (1 - h))),
+    // so that after the barrier each lane reads, and its caller overwrites, only its own
+    // warp's region: no barrier is needed before the outputs are stored.
     if (act) {
-      float2* mine = buf + h * (32 * L);
+      float2* other = buf + (1 - h) * (32 * L);
 #pragma unroll
-      for (int k = 0; k < 32; ++k) mine[k * L + lane] = out[k];
+      for (int k = 0; k < 32; ++k) other[k * L + lane] = out[k];
     }
     bar(pr);
     if (act) {
-      const float2* other = buf + (1 - h) * (32 * L);
+      const float2* mine = buf + h * (32 * L);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        const float2 z = other[k * L + lane];
+        const float2 z = mine[k * L + lane];
         out[k] = h == 0 ? cadd(out[k], z) : csub(z, out[k]);
       }
     }
-    bar(pr);  // the exchange is read: buf is free
   }
 
   // 16-byte asynchronous copy of the packed spectrum row X into buf (the caller waits).
