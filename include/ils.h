@@ -314,7 +314,7 @@ ils_status ils_batch_destroy(ils_batch* batch);
 /*
  * Introspection for tools and tests: the branch a frame runs on (return value, or -1
  * for a bad argument) and the kernel variants its class uses: row variant 1000 + w for
- * warp-per-row kernel entry w, otherwise an index into the table of block-per-strip
+ * warp-per-row (or warp-pair) kernel entry w, otherwise an index into the table of block-per-strip
  * plans; column variant an index into the table of column plans; -1 = generic kernels.
  */
 int ils_batch_kernel_choice(const ils_batch* batch, int frame, int* row_variant, int* col_variant);
